@@ -1,0 +1,386 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test names what it pins and why a plausible mistake in the oracle (a
+dropped term, a wrong sign, a transposed operand, a wrong scaling, a wrong
+corner rule) would fail it.  No value here comes from the CUDA path.
+"""
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle import hps_oracle as O
+from paper_1307_2665_gb300 import inputs as I
+
+UNIT = (0.0, 1.0, 0.0, 1.0)
+SKEW = (-0.3, 0.9, 0.1, 1.7)  # hx != hy on every grid below
+
+
+# --------------------------------------------------------------- 1-D constants
+@pytest.mark.parametrize("p", [3, 5, 9, 16, 21])
+def test_cheb_diff_is_exact_on_polynomials(p):
+    """Section 3.1: D differentiates every polynomial of degree < p exactly."""
+    t = O.cheb_points(p)
+    D = O.cheb_diff(p)
+    assert t[0] == -1.0 and t[-1] == 1.0 and np.all(np.diff(t) > 0)
+    for k in range(p):
+        err = np.max(np.abs(D @ t ** k - k * t ** max(k - 1, 0) * (k > 0)))
+        assert err <= 1e-12 * p * p * max(1, k), (k, err)
+
+
+@pytest.mark.parametrize("q", [1, 2, 7, 14, 21])
+def test_gauss_rule_exact(q):
+    """Gauss-Legendre: q points integrate degree <= 2q-1 exactly on [-1,1]."""
+    x, w = O.gauss_points(q)
+    assert np.all(np.diff(x) > 0)
+    for k in range(2 * q):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(w, x ** k) - exact) <= 1e-14 * 2 * q
+    if 2 <= q <= 7:  # and not degree 2q (the defect shrinks fast with q)
+        assert abs(np.dot(w, x ** (2 * q)) - 2.0 / (2 * q + 1)) > 1e-6
+
+
+def test_interp_matrix_exact_and_cardinal():
+    """Steps 1 and 4: interpolation reproduces polynomials of degree < n and is
+    the identity on its own nodes; extrapolation to the side ends included."""
+    g, _ = O.gauss_points(14)
+    t = O.cheb_points(16)
+    P = O.interp_matrix(g, t)
+    for k in range(14):
+        assert np.max(np.abs(P @ g ** k - t ** k)) < 1e-12
+    assert np.max(np.abs(O.interp_matrix(t, t) - np.eye(16))) < 1e-12
+    Q = O.interp_matrix(t, g)
+    for k in range(16):
+        assert np.max(np.abs(Q @ t ** k - g ** k)) < 1e-12
+
+
+# ---------------------------------------------------------------- P7 counting
+def test_node_counts_match_tables():
+    """Tables 1 and 3 print N and N_tot for q = p = 21; N = 2n(n+1)q and
+    N_tot = N + (n(p-1)+1)^2 reproduce every pair."""
+    rows = [(16, 11424, 114465), (32, 44352, 455233), (64, 174720, 1815681),
+            (128, 693504, 7252225), (256, 2763264, 28987905), (512, 11031552, 115909633)]
+    for n, N, Ntot in rows:
+        assert O.gauss_count(n, 21) == N
+        assert O.total_count(n, 21, 21) == Ntot
+    # the oracle's own numbering agrees with the formula
+    pr = O.Problem(UNIT, 5, 5, 21, 21, {})
+    assert O.EdgeNumbering(pr).N == O.gauss_count(5, 21)
+
+
+# ---------------------------------------------------------------- P1 harmonic
+@pytest.mark.parametrize("nx,ny,p,q", [(1, 1, 16, 14), (2, 2, 16, 14), (8, 8, 12, 10),
+                                       (3, 2, 10, 10)])
+def test_harmonic_polynomials_reproduced(nx, ny, p, q):
+    """P1: for Laplace every harmonic polynomial of degree <= q-1 is reproduced
+    to rounding: side data are interpolated exactly (degree <= q-1), D is exact
+    (degree <= p-1), so the exact values satisfy E1 and E2.  A wrong flux
+    direction, a lost scaling 2/h or a wrong corner rule breaks this."""
+    prob = O.make_problem(SKEW, nx, ny, p, q, I.laplace)
+    bxy = O.boundary_points(prob)
+    xy = O.cheb_grid(SKEW, nx, ny, p)
+    ks = [(k, part) for k in range(0, q) for part in ("re", "im") if not (k == 0 and part == "im")]
+    f = np.stack([I.harmonic_poly(k, part, bxy[:, 0], bxy[:, 1]) for k, part in ks], axis=1)
+    sol, _, _ = O.solve_global(prob, f)
+    for r, (k, part) in enumerate(ks):
+        ex = I.harmonic_poly(k, part, xy[..., 0], xy[..., 1])
+        err = np.max(np.abs(sol.w[r] - ex)) / max(1.0, np.max(np.abs(ex)))
+        assert err < 1e-11, (k, part, err)
+
+
+def test_harmonic_degree_q_not_exact_on_one_leaf():
+    """Sharpness of P1: degree q is NOT exact for one leaf (the Gauss side
+    interpolant has degree q-1), so the test above is not vacuous."""
+    q = 8
+    prob = O.make_problem(UNIT, 1, 1, 12, q, I.laplace)
+    bxy = O.boundary_points(prob)
+    xy = O.cheb_grid(UNIT, 1, 1, 12)
+    f = I.harmonic_poly(q + 1, "re", bxy[:, 0], bxy[:, 1])
+    sol, _, _ = O.solve_global(prob, f)
+    ex = I.harmonic_poly(q + 1, "re", xy[..., 0], xy[..., 1])
+    assert np.max(np.abs(sol.w[0] - ex)) > 1e-8
+
+
+# ---------------------------------------------- general operator with body load
+class _Poly:
+    """A random polynomial of total degree <= deg and its derivatives."""
+
+    def __init__(self, seed, deg):
+        rng = np.random.default_rng(seed)
+        self.terms = [(i, j, rng.standard_normal()) for i in range(deg + 1)
+                      for j in range(deg + 1) if i + j <= deg]
+
+    def __call__(self, x, y, dx=0, dy=0):
+        out = np.zeros(np.broadcast(x, y).shape)
+        for i, j, c in self.terms:
+            if i < dx or j < dy:
+                continue
+            fi = np.prod(np.arange(i - dx + 1, i + 1)) if dx else 1
+            fj = np.prod(np.arange(j - dy + 1, j + 1)) if dy else 1
+            out = out + c * fi * fj * x ** (i - dx) * y ** (j - dy)
+        return out
+
+
+def _varcoef(x, y):
+    return {"c11": 1 + 0.3 * np.sin(x + 2 * y), "c12": 0.2 * np.cos(3 * x - y),
+            "c22": 1.2 + 0.1 * x * y, "c1": 5 * np.cos(x), "c2": -4 * np.sin(2 * y),
+            "c": 7 * np.exp(x * y)}
+
+
+def _apply_A(cf, ux, uy, uxx, uxy, uyy, u):
+    """eq. (1.2) applied to analytic derivatives (written independently of the
+    oracle's matrices: pointwise products of exact derivatives)."""
+    return (-cf["c11"] * uxx - 2 * cf["c12"] * uxy - cf["c22"] * uyy
+            + cf["c1"] * ux + cf["c2"] * uy + cf["c"] * u)
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 2), (3, 2)])
+@pytest.mark.parametrize("solver", ["global", "condensed"])
+def test_polynomial_solution_with_body_load(nx, ny, solver):
+    """Every coefficient term and sign of eq. (1.2) (the factor -2 on c12, +c1,
+    +c2, +c), the 2/hx and 2/hy scalings (hx != hy): a polynomial u of degree
+    <= q-1 with body load F = A u evaluated analytically is reproduced exactly."""
+    p, q = 12, 10
+    P = _Poly(1, 6)
+    prob = O.make_problem(SKEW, nx, ny, p, q, _varcoef)
+    xy = O.cheb_grid(SKEW, nx, ny, p)
+    x, y = xy[..., 0], xy[..., 1]
+    Au = _apply_A(_varcoef(x, y), P(x, y, 1, 0), P(x, y, 0, 1), P(x, y, 2, 0), P(x, y, 1, 1),
+                  P(x, y, 0, 2), P(x, y))
+    ops = O.LeafOps(p, q, prob.hx, prob.hy)
+    F = Au.reshape(prob.n_leaves, p * p)[:, ops.Ji][..., None]
+    bxy = O.boundary_points(prob)
+    f = P(bxy[:, 0], bxy[:, 1])
+    if solver == "global":
+        sol, _, _ = O.solve_global(prob, f, F=F)
+    else:
+        sol = O.solve_condensed(prob, f, F=F)
+    ex = P(x, y)
+    assert np.max(np.abs(sol.w[0] - ex)) / np.max(np.abs(ex)) < 1e-12
+
+
+@pytest.mark.parametrize("solver", ["global", "condensed"])
+def test_flux_jump_right_hand_side(solver):
+    """E2 with a right-hand side: u = P + s (x - xe)_+ + t (y - ye)_+ is a
+    polynomial on every leaf and continuous, with d/dx jumping by s across
+    x = xe and d/dy by t across y = ye.  With G = flux^alpha - flux^beta =
+    -s (resp. -t) on those edges the oracle must return u exactly; a flux taken
+    in the outward instead of the global direction, or alpha/beta swapped, fails."""
+    p, q, nx, ny = 10, 8, 3, 3
+    P = _Poly(2, 4)
+    s, t = 0.7, -1.3
+    prob = O.make_problem(SKEW, nx, ny, p, q, _varcoef)
+    xe = SKEW[0] + 1 * prob.hx
+    ye = SKEW[2] + 2 * prob.hy
+
+    def U(x, y, dx=0, dy=0):
+        out = P(x, y, dx, dy)
+        rx = (x > xe + 1e-12) | ((np.abs(x - xe) <= 1e-12) & (dx == 0))
+        ry = (y > ye + 1e-12) | ((np.abs(y - ye) <= 1e-12) & (dy == 0))
+        if dx == 0 and dy == 0:
+            out = out + s * np.where(rx, x - xe, 0) + t * np.where(ry, y - ye, 0)
+        elif dx == 1 and dy == 0:
+            out = out + s * np.where(x > xe, 1.0, 0.0)
+        elif dx == 0 and dy == 1:
+            out = out + t * np.where(y > ye, 1.0, 0.0)
+        return out
+
+    xy = O.cheb_grid(SKEW, nx, ny, p)
+    ops = O.LeafOps(p, q, prob.hx, prob.hy)
+    F = np.zeros((prob.n_leaves, (p - 2) ** 2, 1))
+    for l in range(prob.n_leaves):
+        x, y = xy[l, ..., 0], xy[l, ..., 1]
+        cx, cy = x.mean(), y.mean()  # which side of the kinks this leaf is on
+        ux = P(x, y, 1, 0) + s * (cx > xe)
+        uy = P(x, y, 0, 1) + t * (cy > ye)
+        Au = _apply_A(_varcoef(x, y), ux, uy, P(x, y, 2, 0), P(x, y, 1, 1), P(x, y, 0, 2),
+                      U(x, y))
+        F[l, :, 0] = Au.reshape(p * p)[ops.Ji]
+    en = O.EdgeNumbering(prob)
+    exy = en.coords()
+    G = np.zeros((en.N, 1))
+    onx = np.abs(exy[:, 0] - xe) < 1e-12
+    ony = np.abs(exy[:, 1] - ye) < 1e-12
+    vert = np.arange(en.N) >= en.NH
+    G[onx & vert, 0] = -s
+    G[ony & ~vert, 0] = -t
+    bxy = O.boundary_points(prob)
+    f = U(bxy[:, 0], bxy[:, 1])
+    if solver == "global":
+        sol, _, _ = O.solve_global(prob, f, F=F, G=G)
+    else:
+        sol = O.solve_condensed(prob, f, F=F, G=G)
+    ex = np.stack([U(xy[l, ..., 0], xy[l, ..., 1]) for l in range(prob.n_leaves)])
+    assert np.max(np.abs(sol.w[0] - ex)) / np.max(np.abs(ex)) < 1e-11
+
+
+# --------------------------------------------------------------- P2 constants
+def test_constants_are_solutions_when_c_is_zero():
+    """P2: with c = 0 every operator kills constants: u = 1 for f = 1, and the
+    leaf DtN annihilates the constant vector (T 1 = 0)."""
+    def co(x, y):
+        d = _varcoef(x, y)
+        d["c"] = None
+        return d
+    prob = O.make_problem(SKEW, 3, 2, 12, 10, co)
+    bxy = O.boundary_points(prob)
+    sol, _, _ = O.solve_global(prob, np.ones(len(bxy)))
+    assert np.max(np.abs(sol.w[0] - 1.0)) < 1e-12
+    T, _ = O.leaf_dtn(prob, 4)
+    assert np.max(np.abs(T @ np.ones(T.shape[1]))) < 1e-10 * np.max(np.abs(T))
+
+
+# ------------------------------------------------------------- P3 symmetry
+def test_dtn_green_symmetry_on_harmonic_data():
+    """P3: Green's second identity: for harmonic u, v, the boundary integral of
+    u dv/dn equals that of v du/dn.  With W the Gauss weights and Sigma the
+    outward sign (-1 on south and west sides, where the global-direction flux
+    points inward), B^T (W Sigma T) B is symmetric for harmonic polynomial data
+    B of degree <= q-1 (Gauss is exact to degree 2q-1).  The full W Sigma T is
+    not symmetric (corner effects), which the test also records."""
+    p, q = 16, 14
+    prob = O.make_problem(SKEW, 1, 1, p, q, I.laplace)
+    T, _ = O.leaf_dtn(prob, 0)
+    g, w = O.gauss_points(q)
+    hx, hy = prob.hx, prob.hy
+    Wd = np.concatenate([w * hx / 2, w * hy / 2, w * hx / 2, w * hy / 2])
+    sig = np.concatenate([-np.ones(q), np.ones(q), np.ones(q), -np.ones(q)])
+    M = (Wd * sig)[:, None] * T
+    x0, _, y0, _ = SKEW
+    t = (g + 1) / 2
+    bx = np.concatenate([x0 + t * hx, np.full(q, x0 + hx), x0 + t * hx, np.full(q, x0)])
+    by = np.concatenate([np.full(q, y0), y0 + t * hy, np.full(q, y0 + hy), y0 + t * hy])
+    B = np.stack([I.harmonic_poly(k, part, bx, by) for k in range(1, q)
+                  for part in ("re", "im")], axis=1)
+    S = B.T @ M @ B
+    assert np.max(np.abs(S - S.T)) <= 1e-10 * np.max(np.abs(S))
+    assert np.max(np.abs(M - M.T)) > 1e-3 * np.max(np.abs(M))
+
+
+# -------------------------------------------------- P4 spectral convergence
+def _geometric(e, drop, floor=1e-12):
+    """Each refinement lowers the error by more than `drop` decades until the
+    error reaches the rounding floor."""
+    le = np.log10(e)
+    for a, b in zip(le[:-1], le[1:]):
+        if 10 ** a > floor:
+            assert b < a - drop or 10 ** b < floor, e
+    return True
+
+
+def _conv_errors(fn_exact, coef_fn, ps, n=2, dom=UNIT):
+    errs = []
+    for p in ps:
+        prob = O.make_problem(dom, n, n, p, p - 2, coef_fn)
+        bxy = O.boundary_points(prob)
+        xy = O.cheb_grid(dom, n, n, p)
+        sol = O.solve_condensed(prob, fn_exact(bxy[:, 0], bxy[:, 1]))
+        ex = fn_exact(xy[..., 0], xy[..., 1])
+        errs.append(np.max(np.abs(sol.w[0] - ex)) / np.max(np.abs(ex)))
+    return np.array(errs)
+
+
+def test_spectral_convergence_exp_sin():
+    """P4: u = e^x sin y (harmonic): error falls geometrically with p."""
+    e = _conv_errors(I.exp_sin, I.laplace, [6, 8, 10, 12, 14])
+    _geometric(e, 1.0)
+    assert e[-1] < 1e-12
+
+
+def test_spectral_convergence_log_source():
+    """P4: u = log|x - (-2, 0)| (Section 8.1, Laplace)."""
+    e = _conv_errors(I.log_source, I.laplace, [6, 8, 10, 12, 16])
+    _geometric(e, 0.5)
+    assert e[-1] < 1e-10
+
+
+def test_spectral_convergence_helmholtz_y0():
+    """P4: u = Y0(kappa |x - (-2, 0)|) solves -Lap u - kappa^2 u = 0 (Section
+    8.1, Helmholtz); kappa = 40 on 4 x 4 leaves of [0, 1]^2."""
+    kappa = 40.0
+
+    def exact(x, y):
+        return scipy.special.y0(kappa * np.hypot(x + 2.0, y))
+
+    def co(x, y):
+        return I.constant_helmholtz(x, y, kappa)
+
+    e = _conv_errors(exact, co, [10, 14, 18, 22], n=4)
+    _geometric(e, 0.7)
+    assert e[-1] < 1e-9
+
+
+# ------------------------------------------------------------ P6 brute force
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 2)])
+def test_sparse_equals_dense_solve(nx, ny):
+    """P6: the sparse LU and a dense solve of the same assembled system agree."""
+    prob = O.make_problem(SKEW, nx, ny, 10, 8, _varcoef)
+    f = np.random.default_rng(5).standard_normal(len(O.boundary_points(prob)))
+    a, A, _ = O.solve_global(prob, f)
+    b, _, _ = O.solve_global(prob, f, dense=True)
+    assert np.max(np.abs(a.w - b.w)) < 1e-12 * np.max(np.abs(a.w))
+    assert np.linalg.cond(A.toarray()) < 1e12
+
+
+def test_leaf_formula_matches_one_leaf_solve():
+    """P6: on one leaf, w_i = Y u_e (eq. leaf_solve) with Y from leaf_dtn, and
+    the boundary values are L1 u_e, equal the assembled solve."""
+    prob = O.make_problem(SKEW, 1, 1, 12, 10, _varcoef)
+    f = np.random.default_rng(6).standard_normal(4 * 10)
+    sol, _, _ = O.solve_global(prob, f)
+    _, Y = O.leaf_dtn(prob, 0)
+    en = O.EdgeNumbering(prob)
+    Ug = np.zeros(en.N)
+    Ug[en.gamma_order()] = f
+    ue = Ug[en.leaf_sides(0, 0)]
+    ops = O.LeafOps(12, 10, prob.hx, prob.hy)
+    full = ops.L1 @ ue
+    full[ops.Ji] = Y @ ue
+    assert np.max(np.abs(full - sol.w[0, 0].ravel())) < 1e-12 * np.max(np.abs(full))
+
+
+def test_condensed_equals_global_with_loads():
+    """The static condensation is the same elimination: identical solutions,
+    including body load F and flux jump G right-hand sides."""
+    prob = O.make_problem(SKEW, 3, 2, 10, 8, _varcoef)
+    rng = np.random.default_rng(7)
+    en = O.EdgeNumbering(prob)
+    f = rng.standard_normal((len(O.boundary_points(prob)), 2))
+    F = rng.standard_normal((prob.n_leaves, 64, 2))
+    G = rng.standard_normal((en.N, 2))
+    a, _, _ = O.solve_global(prob, f, F=F, G=G)
+    b = O.solve_condensed(prob, f, F=F, G=G)
+    assert np.max(np.abs(a.w - b.w)) < 1e-11 * np.max(np.abs(a.w))
+
+
+# ---------------------------------------------------------------- residual
+def test_residual_zero_at_solution_and_linear():
+    """The matrix-free residual vanishes at the solution and equals b - A x of
+    the assembled system at a perturbed candidate (same sign conventions)."""
+    prob = O.make_problem(SKEW, 3, 2, 10, 8, _varcoef)
+    rng = np.random.default_rng(8)
+    en = O.EdgeNumbering(prob)
+    f = rng.standard_normal(len(O.boundary_points(prob)))
+    F = rng.standard_normal((prob.n_leaves, 64, 1))
+    G = rng.standard_normal((en.N, 1))
+    sol, A, rhs = O.solve_global(prob, f, F=F, G=G)
+    r1, r2 = O.residual(prob, sol, f, F=F, G=G)
+    scale = np.max(np.abs(rhs))
+    assert max(np.max(np.abs(r1)), np.max(np.abs(r2))) < 1e-9 * scale
+    # perturb interior edge values and interior nodes, compare with b - A x
+    isb = en.is_boundary()
+    inner = np.nonzero(~isb)[0]
+    du = rng.standard_normal(len(inner)) * 1e-3
+    ops = O.LeafOps(10, 8, prob.hx, prob.hy)
+    dw = rng.standard_normal((prob.n_leaves, 64)) * 1e-3
+    Ug = sol.u_gauss.copy()
+    Ug[inner, 0] += du
+    w = sol.w.copy().reshape(1, prob.n_leaves, 100)
+    w[0][:, ops.Ji] += dw
+    cand = O.Solution(w=w.reshape(sol.w.shape), u_gauss=Ug)
+    r1, r2 = O.residual(prob, cand, f, F=F, G=G)
+    dx = np.concatenate([du, dw.ravel()])
+    ref = -(A @ dx)
+    nu = len(inner)
+    got = np.concatenate([r2[inner, 0], r1[:, :, 0].ravel()])
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+    assert nu > 0
