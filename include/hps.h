@@ -1,0 +1,140 @@
+/*
+ * hps.h -- C ABI of a GB300 (sm_103a) direct solver for variable-coefficient
+ * elliptic PDEs on a rectangle, discretised by the composite spectral
+ * collocation method of Gillman & Martinsson, "A direct solver with O(N)
+ * complexity for variable coefficient elliptic PDEs discretized via a
+ * high-order composite spectral collocation method" (arXiv:1307.2665).
+ *
+ * Problem (Section 1.1, eq. 1.1-1.2): on Omega = [x0,x1] x [y0,y1],
+ *     A u = 0 in Omega,  u = f on the boundary Gamma, with
+ *     A u = -c11 u_xx - 2 c12 u_xy - c22 u_yy + c1 u_x + c2 u_y + c u.
+ *
+ * Discretisation (Sections 2-3): Omega is split into nx-by-ny equal leaves.
+ * Each leaf carries a p x p tensor grid of Chebyshev extreme points (the
+ * collocation nodes) and q Gauss-Legendre points on each edge (the nodes of
+ * the global unknowns).  hps_build runs Algorithm 1 (leaf DtN maps, Section 3;
+ * Schur-complement merges, Section 4, eqs. U_parent and merge); hps_solve runs
+ * Algorithm 2 (downward pass) and the leaf post-processing of Section 4.3, and
+ * returns u at every leaf's p x p Chebyshev grid.
+ *
+ * Conventions shared by every entry point:
+ *   - Leaf l = iy*nx + ix (ix along x).  Within a leaf, node (a, b) has index
+ *     a*p + b with a the y index and b the x index, both increasing with the
+ *     coordinate ("iy-major").
+ *   - Coefficient arrays hold nx*ny*p*p doubles sampled at hps_cheb_nodes().
+ *     A NULL coefficient pointer means that coefficient is identically zero.
+ *   - Dirichlet data f holds, per right-hand side, the values at the
+ *     nbnd = 2*(nx+ny)*q Gauss nodes of Gamma in counter-clockwise order from
+ *     (x0, y0): south side (x increasing), east (y increasing), north
+ *     (x decreasing), west (y decreasing).  hps_boundary_nodes() returns them.
+ *     Layout: f[r*nbnd + i] for right-hand side r.
+ *   - The solution u holds u[(r*nx*ny + l)*p*p + a*p + b].
+ *   - Every array argument is a HOST pointer unless options.device_ptrs is 1,
+ *     in which case coefficient, f and u pointers passed to hps_build /
+ *     hps_solve are device pointers on the current CUDA device.
+ *   - The caller owns every buffer it passes.  The library copies what it
+ *     needs; the handle owns its device memory until hps_free().
+ *   - Return value: HPS_OK (0) or a negative status (below).  All argument
+ *     validation happens before any device work; on error no handle is
+ *     returned and nothing is left allocated.
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPS_OK 0
+#define HPS_EINVAL (-1)         /* bad sizes, p < 3, q < 1, q > p, NULL required pointer */
+#define HPS_ENOMEM (-2)         /* device or host allocation failed, or over the memory budget */
+#define HPS_ESINGULAR (-3)      /* zero or non-finite pivot in a leaf or merge factorisation */
+#define HPS_ENOTCONVERGED (-4)  /* iterative refinement did not reach the tolerance */
+#define HPS_EDEVICE (-5)        /* CUDA error */
+
+#define HPS_FP64 0   /* every stage in double precision */
+#define HPS_MIXED 1  /* FP32 leaves and lower merges, FP64 top merges, FP64 refinement */
+
+typedef struct hps_handle_s* hps_handle;
+
+typedef struct {
+  double x0, x1, y0, y1;
+} hps_domain;
+
+typedef struct {
+  int precision;          /* HPS_FP64 or HPS_MIXED */
+  double refine_tol;      /* mixed mode: stop when max|delta| <= tol * max|u| (default 1e-11) */
+  int max_refine;         /* mixed mode: iteration cap (default 10) */
+  int fp64_top_levels;    /* mixed mode: merge levels below the root kept in FP64 (default 2) */
+  int device_ptrs;        /* 1: coefficient / f / u pointers are device pointers */
+  void* stream;           /* cudaStream_t to run on; NULL: the library's own stream */
+  int form_root_dtn;      /* 1: also form the root DtN T^1 (not needed by hps_solve) */
+} hps_options;
+
+typedef struct {
+  int status;             /* HPS_OK or the failing status */
+  int iterations;         /* refinement iterations run (0 in FP64 mode) */
+  double last_update;     /* max|delta| / max|u| of the last correction (mixed mode) */
+  int bad_box;            /* box index of a singular pivot, or -1 */
+} hps_solve_info;
+
+/* Fill *opt with the defaults above (FP64, host pointers, library stream). */
+void hps_default_options(hps_options* opt);
+
+/* Number of Dirichlet nodes on Gamma, 2*(nx+ny)*q. */
+int64_t hps_boundary_count(int nx, int ny, int q);
+
+/* Coordinates of every leaf's Chebyshev grid (Section 3.1: p extreme points
+ * per direction).  xy: host array of nx*ny*p*p*2 doubles, (x, y) pairs in the
+ * node order above. */
+int hps_cheb_nodes(hps_domain d, int nx, int ny, int p, double* xy);
+
+/* Coordinates (x, y) of the Gauss nodes on Gamma in the order of f, computed
+ * without a handle.  xy: host array of 2*nbnd doubles. */
+int hps_boundary_nodes_grid(hps_domain d, int nx, int ny, int q, double* xy);
+
+/* Build stage (Algorithm 1): leaf DtN maps T = L4 L3 L2 L1 (Section 3.2) for
+ * every leaf, then the merges of Section 4 up the binary tree, storing each
+ * merge's solution operator S (eq. U_parent) and each leaf's interior solution
+ * operator Y = -A_ii^{-1} A_ie L1 (eq. leaf_solve, Section 4.3) on the device.
+ * The tree splits a box's longer side at floor(n/2) (ties: x), so any nx, ny
+ * >= 1 is accepted.  Returns HPS_ESINGULAR if a pivot is zero or not finite
+ * (e.g. a Helmholtz box at a Dirichlet resonance, Remark 1.1). */
+int hps_build(hps_domain d, int nx, int ny, int p, int q,
+              const double* c11, const double* c12, const double* c22,
+              const double* c1, const double* c2, const double* c,
+              const hps_options* opt, hps_handle* out);
+
+/* Coordinates of the Gauss nodes on Gamma in the order of f (host array of
+ * 2*nbnd doubles). */
+int hps_boundary_nodes(hps_handle h, double* xy);
+
+/* Solve stage (Algorithm 2 and Section 4.3): given nrhs Dirichlet data sets f,
+ * compute u at every leaf's Chebyshev grid.  In HPS_MIXED mode this runs
+ * iterative refinement against the FP64 residual of the global collocation
+ * system until the tolerance is met (HPS_ENOTCONVERGED otherwise; u then holds
+ * the last iterate).  info may be NULL.  f and u follow options.device_ptrs of
+ * the build. */
+int hps_solve(hps_handle h, const double* f, int nrhs, double* u, hps_solve_info* info);
+
+/* Same as hps_solve with an explicit pointer kind: device_ptrs 0 (host arrays,
+ * copies to and from the device inside the call) or 1 (device arrays). */
+int hps_solve_ex(hps_handle h, const double* f, int nrhs, double* u, int device_ptrs,
+                 hps_solve_info* info);
+
+/* Sizes of a built handle: number of leaves, p, q, nbnd, bytes of device memory
+ * held.  Any output pointer may be NULL. */
+int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_t* device_bytes);
+
+/* Release every resource of the handle (NULL is accepted). */
+int hps_free(hps_handle h);
+
+/* Static text for a status code. */
+const char* hps_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPS_H */

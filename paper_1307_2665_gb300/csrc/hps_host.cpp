@@ -1,0 +1,324 @@
+// Host-side constants and the tree plan of the composite spectral solver.
+//
+// Constants (Section 3.1, 3.2): Chebyshev extreme points with the barycentric
+// differentiation matrix, Gauss-Legendre points by Newton's method on the
+// three-term Legendre recurrence, and Lagrange interpolation matrices in the
+// first ("modified Lagrange") barycentric form, which stays accurate when a side
+// interpolant is evaluated at the side's end points (Step 1 extrapolates the
+// Gauss interpolant to the Chebyshev corners).
+//
+// Plan (Section 2 and Section 4.1): the binary tree over the leaves, each box's
+// exterior ordering, and, per merge geometry, the maps that split the children's
+// exterior nodes into J1, J2, J3 (Algorithm 1, line 6; Figure 3).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <stdexcept>
+#include <tuple>
+
+#include "hps_internal.hpp"
+
+namespace hps {
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// Lagrange basis of nodes x evaluated at t: row-major (nt x n).
+std::vector<double> lagrange_matrix(const std::vector<double>& x, const std::vector<double>& t) {
+  const int n = (int)x.size(), nt = (int)t.size();
+  std::vector<double> w(n);
+  for (int j = 0; j < n; ++j) {
+    double prod = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) prod *= (x[j] - x[k]);
+    w[j] = 1.0 / prod;
+  }
+  std::vector<double> P((size_t)nt * n, 0.0);
+  for (int i = 0; i < nt; ++i) {
+    int hit = -1;
+    for (int j = 0; j < n; ++j)
+      if (t[i] == x[j]) hit = j;
+    if (hit >= 0) {
+      P[(size_t)i * n + hit] = 1.0;
+      continue;
+    }
+    double ell = 1.0;  // node polynomial prod_k (t - x_k)
+    for (int k = 0; k < n; ++k) ell *= (t[i] - x[k]);
+    for (int j = 0; j < n; ++j) P[(size_t)i * n + j] = ell * w[j] / (t[i] - x[j]);
+  }
+  return P;
+}
+
+}  // namespace
+
+Consts make_consts(int p, int q) {
+  Consts c;
+  c.p = p;
+  c.q = q;
+  // Chebyshev extreme points, increasing: t_j = -cos(pi j/(p-1)), written as a
+  // sine so that the set is exactly antisymmetric about 0.
+  c.t.resize(p);
+  for (int j = 0; j < p; ++j) c.t[j] = std::sin(kPi * (2.0 * j - (p - 1)) / (2.0 * (p - 1)));
+  // Barycentric weights of the extreme points: (-1)^j, halved at both ends.
+  std::vector<double> bw(p);
+  for (int j = 0; j < p; ++j) bw[j] = ((j % 2) ? -1.0 : 1.0) * ((j == 0 || j == p - 1) ? 0.5 : 1.0);
+  c.D.assign((size_t)p * p, 0.0);
+  for (int i = 0; i < p; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < p; ++j) {
+      if (j == i) continue;
+      double v = (bw[j] / bw[i]) / (c.t[i] - c.t[j]);
+      c.D[(size_t)i * p + j] = v;
+      diag -= v;  // rows of D annihilate constants
+    }
+    c.D[(size_t)i * p + i] = diag;
+  }
+  // Gauss-Legendre points: Newton iteration on P_q from Chebyshev-like guesses.
+  c.g.resize(q);
+  c.gw.resize(q);
+  for (int k = 0; k < q; ++k) {
+    double x = -std::cos(kPi * (k + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int n = 2; n <= q; ++n) {
+        double pn = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+        p0 = p1;
+        p1 = pn;
+      }
+      double pq = (q == 1) ? x : p1;
+      double pqm1 = (q == 1) ? 1.0 : p0;
+      dp = q * (x * pq - pqm1) / (x * x - 1.0);
+      double dx = pq / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    // recompute the derivative at the converged point for the weight
+    double p0 = 1.0, p1 = x;
+    for (int n = 2; n <= q; ++n) {
+      double pn = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+      p0 = p1;
+      p1 = pn;
+    }
+    double pq = (q == 1) ? x : p1, pqm1 = (q == 1) ? 1.0 : p0;
+    dp = q * (x * pq - pqm1) / (x * x - 1.0);
+    c.g[k] = x;
+    c.gw[k] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  std::sort(c.g.begin(), c.g.end());
+  // weights follow the sorted order (the rule is symmetric, recompute to be safe)
+  for (int k = 0; k < q; ++k) {
+    double x = c.g[k], p0 = 1.0, p1 = x;
+    for (int n = 2; n <= q; ++n) {
+      double pn = ((2.0 * n - 1.0) * x * p1 - (n - 1.0) * p0) / n;
+      p0 = p1;
+      p1 = pn;
+    }
+    double pq = (q == 1) ? x : p1, pqm1 = (q == 1) ? 1.0 : p0;
+    double dp = q * (x * pq - pqm1) / (x * x - 1.0);
+    c.gw[k] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  c.Pg2c = lagrange_matrix(c.g, c.t);  // Step 1 (per side)
+  c.Pc2g = lagrange_matrix(c.t, c.g);  // Step 4 (per side)
+  return c;
+}
+
+// ------------------------------------------------------------------ the plan
+namespace {
+
+// Side offsets of a box's exterior ordering: S, E, N, W.
+struct Sides {
+  int S, E, N, W, n;
+  Sides(int bx, int by, int q) {
+    S = 0;
+    E = bx * q;
+    N = (bx + by) * q;
+    W = (2 * bx + by) * q;
+    n = 2 * (bx + by) * q;
+  }
+};
+
+MergeShape make_shape(int split, int abx, int aby, int bbx, int bby, int q) {
+  MergeShape s;
+  s.split = split;
+  Sides A(abx, aby, q), B(bbx, bby, q);
+  int pbx = split == 0 ? abx + bbx : abx;
+  int pby = split == 0 ? aby : aby + bby;
+  Sides P(pbx, pby, q);
+  s.na = A.n;
+  s.nb = B.n;
+  s.ne = P.n;
+  s.src.assign(P.n, 0);
+  auto alpha = [](int i) { return i; };
+  auto beta = [](int i) { return -(i + 1); };
+  if (split == 0) {
+    // west alpha, east beta; J3 = alpha's east side = beta's west side
+    s.m = aby * q;
+    s.j3a = A.E;
+    s.j3b = B.W;
+    for (int k = 0; k < pbx * q; ++k) {
+      s.src[P.S + k] = k < abx * q ? alpha(A.S + k) : beta(B.S + k - abx * q);
+      s.src[P.N + k] = k < abx * q ? alpha(A.N + k) : beta(B.N + k - abx * q);
+    }
+    for (int k = 0; k < pby * q; ++k) {
+      s.src[P.E + k] = beta(B.E + k);
+      s.src[P.W + k] = alpha(A.W + k);
+    }
+  } else {
+    // south alpha, north beta; J3 = alpha's north side = beta's south side
+    s.m = abx * q;
+    s.j3a = A.N;
+    s.j3b = B.S;
+    for (int k = 0; k < pbx * q; ++k) {
+      s.src[P.S + k] = alpha(A.S + k);
+      s.src[P.N + k] = beta(B.N + k);
+    }
+    for (int k = 0; k < pby * q; ++k) {
+      s.src[P.E + k] = k < aby * q ? alpha(A.E + k) : beta(B.E + k - aby * q);
+      s.src[P.W + k] = k < aby * q ? alpha(A.W + k) : beta(B.W + k - aby * q);
+    }
+  }
+  s.cmap_a.assign(s.na, 0);
+  s.cmap_b.assign(s.nb, 0);
+  for (int j = 0; j < s.m; ++j) {
+    s.cmap_a[s.j3a + j] = -(j + 1);
+    s.cmap_b[s.j3b + j] = -(j + 1);
+  }
+  for (int k = 0; k < s.ne; ++k) {
+    int v = s.src[k];
+    if (v >= 0)
+      s.cmap_a[v] = k;
+    else
+      s.cmap_b[-v - 1] = k;
+  }
+  return s;
+}
+
+}  // namespace
+
+Plan make_plan(double x0, double x1, double y0, double y1, int nx, int ny, int p, int q) {
+  Plan pl;
+  pl.x0 = x0;
+  pl.x1 = x1;
+  pl.y0 = y0;
+  pl.y1 = y1;
+  pl.nx = nx;
+  pl.ny = ny;
+  pl.p = p;
+  pl.q = q;
+  pl.leaf_box.assign((size_t)nx * ny, -1);
+  std::map<std::tuple<int, int, int, int, int>, int> shape_ids;
+  // Breadth-first construction keeps parent index < child index (Section 2).
+  Box root;
+  root.ix0 = 0;
+  root.iy0 = 0;
+  root.bx = nx;
+  root.by = ny;
+  pl.boxes.push_back(root);
+  for (size_t b = 0; b < pl.boxes.size(); ++b) {
+    Box cur = pl.boxes[b];
+    if (cur.bx == 1 && cur.by == 1) {
+      pl.boxes[b].leaf = cur.iy0 * nx + cur.ix0;
+      pl.leaf_box[pl.boxes[b].leaf] = (int)b;
+      continue;
+    }
+    Box a, c;
+    int split = (cur.bx >= cur.by) ? 0 : 1;  // split the longer side; ties split x
+    if (split == 0) {
+      int h = cur.bx / 2;
+      a = {cur.ix0, cur.iy0, h, cur.by};
+      c = {cur.ix0 + h, cur.iy0, cur.bx - h, cur.by};
+    } else {
+      int h = cur.by / 2;
+      a = {cur.ix0, cur.iy0, cur.bx, h};
+      c = {cur.ix0, cur.iy0 + h, cur.bx, cur.by - h};
+    }
+    a.parent = c.parent = (int)b;
+    pl.boxes[b].split = split;
+    pl.boxes[b].child[0] = (int)pl.boxes.size();
+    pl.boxes.push_back(a);
+    pl.boxes[b].child[1] = (int)pl.boxes.size();
+    pl.boxes.push_back(c);
+  }
+  // heights bottom-up (children have larger indices)
+  for (int b = (int)pl.boxes.size() - 1; b >= 0; --b) {
+    Box& x = pl.boxes[b];
+    x.ne = 2 * (x.bx + x.by) * q;
+    if (x.child[0] >= 0)
+      x.height = 1 + std::max(pl.boxes[x.child[0]].height, pl.boxes[x.child[1]].height);
+  }
+  pl.height = pl.boxes[0].height;
+  pl.levels.assign(pl.height + 1, {});
+  for (int b = 0; b < (int)pl.boxes.size(); ++b) {
+    Box& x = pl.boxes[b];
+    if (x.child[0] < 0) continue;
+    const Box& A = pl.boxes[x.child[0]];
+    const Box& B = pl.boxes[x.child[1]];
+    auto key = std::make_tuple(x.split, A.bx, A.by, B.bx, B.by);
+    auto it = shape_ids.find(key);
+    if (it == shape_ids.end()) {
+      pl.shapes.push_back(make_shape(x.split, A.bx, A.by, B.bx, B.by, q));
+      it = shape_ids.emplace(key, (int)pl.shapes.size() - 1).first;
+    }
+    x.shape = it->second;
+    pl.levels[x.height].push_back(b);
+  }
+  int64_t off = 0;
+  for (auto& x : pl.boxes) {
+    x.ext_off = off;
+    off += x.ne;
+  }
+  pl.ext_total = off;
+  // root exterior (S, E, N, W increasing) from f (counter-clockwise from (x0,y0))
+  const int nb = 2 * (nx + ny) * q;
+  pl.root_from_f.assign(nb, 0);
+  Sides R(nx, ny, q);
+  for (int k = 0; k < nx * q; ++k) {
+    pl.root_from_f[R.S + k] = k;
+    pl.root_from_f[R.N + k] = (nx + ny) * q + (nx * q - 1 - k);
+  }
+  for (int k = 0; k < ny * q; ++k) {
+    pl.root_from_f[R.E + k] = nx * q + k;
+    pl.root_from_f[R.W + k] = (2 * nx + ny) * q + (ny * q - 1 - k);
+  }
+  return pl;
+}
+
+void cheb_node_coords(double x0, double x1, double y0, double y1, int nx, int ny, int p,
+                      double* xy) {
+  Consts c = make_consts(p, 1);
+  const double hx = (x1 - x0) / nx, hy = (y1 - y0) / ny;
+  for (int iy = 0; iy < ny; ++iy)
+    for (int ix = 0; ix < nx; ++ix) {
+      size_t l = (size_t)iy * nx + ix;
+      for (int a = 0; a < p; ++a)
+        for (int b = 0; b < p; ++b) {
+          size_t n = (l * p + a) * p + b;
+          xy[2 * n] = x0 + ix * hx + 0.5 * (c.t[b] + 1.0) * hx;
+          xy[2 * n + 1] = y0 + iy * hy + 0.5 * (c.t[a] + 1.0) * hy;
+        }
+    }
+}
+
+void boundary_node_coords(double x0, double x1, double y0, double y1, int nx, int ny, int q,
+                          double* xy) {
+  Consts c = make_consts(std::max(q, 2), q);
+  const double hx = (x1 - x0) / nx, hy = (y1 - y0) / ny;
+  size_t n = 0;
+  auto put = [&](double x, double y) {
+    xy[2 * n] = x;
+    xy[2 * n + 1] = y;
+    ++n;
+  };
+  for (int i = 0; i < nx; ++i)
+    for (int k = 0; k < q; ++k) put(x0 + i * hx + 0.5 * (c.g[k] + 1.0) * hx, y0);
+  for (int j = 0; j < ny; ++j)
+    for (int k = 0; k < q; ++k) put(x1, y0 + j * hy + 0.5 * (c.g[k] + 1.0) * hy);
+  for (int i = nx - 1; i >= 0; --i)
+    for (int k = q - 1; k >= 0; --k) put(x0 + i * hx + 0.5 * (c.g[k] + 1.0) * hx, y1);
+  for (int j = ny - 1; j >= 0; --j)
+    for (int k = q - 1; k >= 0; --k) put(x0, y0 + j * hy + 0.5 * (c.g[k] + 1.0) * hy);
+}
+
+}  // namespace hps

@@ -1,0 +1,295 @@
+// Leaf kernels (Section 3 and Section 4.3).
+//
+// On the p x p Chebyshev grid of a leaf the operator of eq. (1.2) is the
+// collocation matrix of Section 3.1,
+//   A = -C11 Dx^2 - 2 C12 Dx Dy - C22 Dy^2 + C1 Dx + C2 Dy + C,
+// with Dx = (2/hx) I (x) D acting along x and Dy = (2/hy) D (x) I along y.  The
+// entries are generated on the fly from D, D^2 and the coefficient samples; no
+// p^2 x p^2 matrix is ever stored.
+//
+//   leaf_assemble : A_ii (interior rows and columns) and B = -A_ie L1, where L1
+//                   (Step 1) extrapolates each side's degree q-1 Gauss
+//                   interpolant to the side's p Chebyshev points and averages
+//                   the two values at a corner.  The batched LU then turns B
+//                   into Y = -A_ii^{-1} A_ie L1 (eq. leaf_solve).
+//   leaf_dtn      : T = L4 L3 W with W = [L1 ; Y] the full-grid potential per
+//                   unit Gauss datum (Steps 3-4: d/dy on horizontal sides, d/dx
+//                   on vertical sides, then evaluation of the side interpolant
+//                   at the q Gauss points).
+//   leaf_post     : w_full = W u_e for the solve (Section 4.3).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hps_kernels.cuh"
+
+namespace hps {
+
+namespace {
+
+struct CoefPtrs {
+  const double* c[6];  // c11, c12, c22, c1, c2, c (null = absent)
+};
+
+}  // namespace
+
+// One CTA per leaf.
+template <typename R>
+__global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q, double sx,
+                                                       double sy, const double* __restrict__ gD,
+                                                       const double* __restrict__ gPg2c,
+                                                       R* __restrict__ Aii, R* __restrict__ Y) {
+  extern __shared__ __align__(16) double sm[];
+  const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
+  double* D = sm;             // p x p
+  double* D2 = D + pp;        // p x p  (D*D)
+  double* Pg = D2 + pp;       // p x q
+  double* G = Pg + p * q;     // p x q : G[b][k] = sum_d D[b][d] w(d) Pg[d][k]
+  double* cf = G + p * q;     // 6 x pp coefficient samples
+  const int l = blockIdx.x;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
+  for (int k = 0; k < 6; ++k)
+    for (int e = threadIdx.x; e < pp; e += blockDim.x)
+      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)l * pp + e] : 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    int i = e / p, j = e % p;
+    double s = 0.0;
+    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + j], s);
+    D2[e] = s;
+  }
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+    int b = e / q, k = e % q;
+    double s = 0.0;
+    for (int d = 0; d < p; ++d) {
+      double w = (d == 0 || d == p - 1) ? 0.5 : 1.0;
+      s = fma(D[b * p + d] * w, Pg[d * q + k], s);
+    }
+    G[e] = s;
+  }
+  __syncthreads();
+  const double* c11 = cf;
+  const double* c12 = cf + pp;
+  const double* c22 = cf + 2 * pp;
+  const double* c1 = cf + 3 * pp;
+  const double* c2 = cf + 4 * pp;
+  const double* c0 = cf + 5 * pp;
+  const bool has12 = cp.c[1] != nullptr;
+  R* Al = Aii + (size_t)l * ni * ni;
+  // A_ii(ri, ci), ri = (a-1)*(p-2) + (b-1), ci = (c-1)*(p-2) + (d-1)
+  for (int e = threadIdx.x; e < ni * ni; e += blockDim.x) {
+    const int ri = e % ni, ci = e / ni;
+    const int a = ri / pi + 1, b = ri % pi + 1, c = ci / pi + 1, d = ci % pi + 1;
+    const int r = a * p + b;
+    double v = 0.0;
+    if (a == c) v += -c11[r] * sx * sx * D2[b * p + d] + c1[r] * sx * D[b * p + d];
+    if (b == d) v += -c22[r] * sy * sy * D2[a * p + c] + c2[r] * sy * D[a * p + c];
+    if (has12) v += -2.0 * c12[r] * sx * sy * D[a * p + c] * D[b * p + d];
+    if (a == c && b == d) v += c0[r];
+    Al[e] = (R)v;
+  }
+  // B = -A_ie L1 (ni x 4q).  For an interior row (a, b) only the boundary nodes
+  // of row a / column b are reached by the pure x / pure y terms; the mixed term
+  // reaches every node of a side, collapsed through G.
+  R* Yl = Y + (size_t)l * ni * nq;
+  for (int e = threadIdx.x; e < ni * nq; e += blockDim.x) {
+    const int ri = e % ni, gcol = e / ni;
+    const int s = gcol / q, k = gcol % q;
+    const int a = ri / pi + 1, b = ri % pi + 1;
+    const int r = a * p + b;
+    double v;
+    if (s == 0 || s == 2) {  // horizontal side: node (c, b) with c = 0 or p-1
+      const int c = (s == 0) ? 0 : p - 1;
+      v = (c22[r] * sy * sy * D2[a * p + c] - c2[r] * sy * D[a * p + c]) * Pg[b * q + k];
+      if (has12) v += 2.0 * c12[r] * sx * sy * D[a * p + c] * G[b * q + k];
+    } else {  // vertical side: node (a, d) with d = p-1 (east) or 0 (west)
+      const int d = (s == 1) ? p - 1 : 0;
+      v = (c11[r] * sx * sx * D2[b * p + d] - c1[r] * sx * D[b * p + d]) * Pg[a * q + k];
+      if (has12) v += 2.0 * c12[r] * sx * sy * D[b * p + d] * G[a * q + k];
+    }
+    Yl[e] = (R)v;
+  }
+}
+
+template <typename R>
+void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double hx, double hy,
+                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, cudaStream_t st) {
+  if (nleaves <= 0) return;
+  CoefPtrs cp;
+  for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
+  size_t smem = (size_t)(2 * p * p + 2 * p * q + 6 * p * p) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_leaf_assemble<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  k_leaf_assemble<R><<<nleaves, 256, smem, st>>>(cp, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, Aii,
+                                                 Y);
+}
+
+// ------------------------------------------------------------------ leaf DtN
+// One CTA per leaf; the 4q columns of W are processed in chunks of CH.
+template <typename R>
+__global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int p, int q, double sx,
+                                                  double sy, const double* __restrict__ gD,
+                                                  const double* __restrict__ gPg2c,
+                                                  const double* __restrict__ gPc2g,
+                                                  R* __restrict__ T) {
+  constexpr int CH = 8;
+  extern __shared__ __align__(16) double sm[];
+  const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
+  double* D = sm;               // p x p
+  double* Pg = D + pp;          // p x q
+  double* Pc = Pg + p * q;      // q x p
+  double* W = Pc + q * p;       // pp x CH
+  double* F = W + pp * CH;      // 4p x CH side fluxes at Chebyshev points
+  const int l = blockIdx.x;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+    Pg[e] = gPg2c[e];
+    Pc[e] = gPc2g[e];
+  }
+  const R* Yl = Y + (size_t)l * ni * nq;
+  R* Tl = T + (size_t)l * nq * nq;
+  for (int g0 = 0; g0 < nq; g0 += CH) {
+    const int nc = min(CH, nq - g0);
+    __syncthreads();
+    // W[:, g] for g in chunk: boundary rows from L1, interior rows from Y
+    for (int e = threadIdx.x; e < pp * nc; e += blockDim.x) {
+      const int node = e % pp, cc = e / pp, g = g0 + cc;
+      const int a = node / p, b = node % p;
+      double v = 0.0;
+      if (a > 0 && a < p - 1 && b > 0 && b < p - 1) {
+        v = (double)Yl[(a - 1) * pi + (b - 1) + (size_t)g * ni];
+      } else {
+        const int s = g / q, k = g % q;
+        // the node lies on side s at position j?
+        int j = -1;
+        if (s == 0 && a == 0) j = b;
+        if (s == 2 && a == p - 1) j = b;
+        if (s == 1 && b == p - 1) j = a;
+        if (s == 3 && b == 0) j = a;
+        if (j >= 0) v = ((j == 0 || j == p - 1) ? 0.5 : 1.0) * Pg[j * q + k];
+      }
+      W[node + cc * pp] = v;
+    }
+    __syncthreads();
+    // Step 3: fluxes at the Chebyshev points of each side
+    for (int e = threadIdx.x; e < 4 * p * nc; e += blockDim.x) {
+      const int sj = e % (4 * p), cc = e / (4 * p);
+      const int s = sj / p, j = sj % p;
+      double acc = 0.0;
+      const double* Wc = W + cc * pp;
+      if (s == 0 || s == 2) {  // d/dy at node (0 or p-1, j)
+        const int row = (s == 0) ? 0 : p - 1;
+        for (int a = 0; a < p; ++a) acc = fma(D[row * p + a], Wc[a * p + j], acc);
+        acc *= sy;
+      } else {  // d/dx at node (j, p-1 or 0)
+        const int col = (s == 1) ? p - 1 : 0;
+        for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], Wc[j * p + b], acc);
+        acc *= sx;
+      }
+      F[sj + cc * 4 * p] = acc;
+    }
+    __syncthreads();
+    // Step 4: Gauss values of each side's flux interpolant
+    for (int e = threadIdx.x; e < nq * nc; e += blockDim.x) {
+      const int row = e % nq, cc = e / nq;
+      const int s = row / q, k = row % q;
+      double acc = 0.0;
+      for (int j = 0; j < p; ++j) acc = fma(Pc[k * p + j], F[s * p + j + cc * 4 * p], acc);
+      Tl[row + (size_t)(g0 + cc) * nq] = (R)acc;
+    }
+  }
+}
+
+template <typename R>
+void leaf_dtn(const R* Y, int nleaves, int p, int q, double hx, double hy, const double* d_D,
+              const double* d_Pg2c, const double* d_Pc2g, R* T, cudaStream_t st) {
+  if (nleaves <= 0) return;
+  size_t smem = (size_t)(p * p + 2 * p * q + p * p * 8 + 4 * p * 8) * sizeof(double);
+  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, d_Pc2g, T);
+}
+
+// ------------------------------------------------------------ post-process
+// u[(r*nl + l)*pp + node] = (W u_e)(node), W = [L1 ; Y], right-hand sides in
+// chunks of RC.
+template <typename R>
+__global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
+                                                   const double* __restrict__ uext,
+                                                   const int64_t* __restrict__ leaf_off,
+                                                   int64_t ext_total, int nl, int p, int q,
+                                                   int nrhs, const double* __restrict__ gPg2c,
+                                                   double* __restrict__ u) {
+  constexpr int RC = 16;
+  extern __shared__ __align__(16) double sm[];
+  const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
+  double* Pg = sm;           // p x q
+  double* ue = Pg + p * q;   // nq x RC
+  const int l = blockIdx.x;
+  const int64_t off = leaf_off[l];
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
+  const R* Yl = Y + (size_t)l * ni * nq;
+  for (int r0 = 0; r0 < nrhs; r0 += RC) {
+    const int nr = min(RC, nrhs - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * RC; e += blockDim.x) {
+      const int g = e % nq, rr = e / nq;
+      ue[g * RC + rr] = rr < nr ? uext[(size_t)(r0 + rr) * ext_total + off + g] : 0.0;
+    }
+    __syncthreads();
+    for (int node = threadIdx.x; node < pp; node += blockDim.x) {
+      const int a = node / p, b = node % p;
+      double acc[RC];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = 0.0;
+      if (a > 0 && a < p - 1 && b > 0 && b < p - 1) {
+        const int ri = (a - 1) * pi + (b - 1);
+        for (int g = 0; g < nq; ++g) {
+          const double y = (double)Yl[ri + (size_t)g * ni];
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(y, ue[g * RC + rr], acc[rr]);
+        }
+      } else {
+        // boundary node: sides containing it, weights halved at corners
+        const int sides[4][2] = {{0, b}, {2, b}, {1, a}, {3, a}};
+        const bool on[4] = {a == 0, a == p - 1, b == p - 1, b == 0};
+        for (int t = 0; t < 4; ++t) {
+          if (!on[t]) continue;
+          const int s = sides[t][0], j = sides[t][1];
+          const double w = (j == 0 || j == p - 1) ? 0.5 : 1.0;
+          for (int k = 0; k < q; ++k) {
+            const double c = w * Pg[j * q + k];
+#pragma unroll
+            for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(c, ue[(s * q + k) * RC + rr], acc[rr]);
+          }
+        }
+      }
+      for (int rr = 0; rr < nr; ++rr) u[((size_t)(r0 + rr) * nl + l) * pp + node] = acc[rr];
+    }
+  }
+}
+
+template <typename R>
+void leaf_post(const R* Y, const double* uext, const int64_t* leaf_ext_off, int64_t ext_total,
+               int nleaves, int p, int q, int nrhs, const double* d_Pg2c, double* u,
+               cudaStream_t st) {
+  if (nleaves <= 0 || nrhs <= 0) return;
+  size_t smem = (size_t)(p * q + 4 * q * 16) * sizeof(double);
+  k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, uext, leaf_ext_off, ext_total, nleaves, p, q,
+                                             nrhs, d_Pg2c, u);
+}
+
+#define HPS_INST_LEAF(R)                                                                        \
+  template void leaf_assemble<R>(const double* const*, int, int, int, double, double,           \
+                                 const double*, const double*, R*, R*, cudaStream_t);           \
+  template void leaf_dtn<R>(const R*, int, int, int, double, double, const double*,             \
+                            const double*, const double*, R*, cudaStream_t);                    \
+  template void leaf_post<R>(const R*, const double*, const int64_t*, int64_t, int, int, int,   \
+                             int, const double*, double*, cudaStream_t);
+HPS_INST_LEAF(double)
+HPS_INST_LEAF(float)
+
+}  // namespace hps

@@ -1,0 +1,468 @@
+// Batched dense linear algebra for the leaf eliminations (eq. leaf_solve) and
+// the merge factorisations (eq. U_parent): right-looking blocked LU with
+// partial pivoting applied to the augmented system [A | B], then blocked
+// backward substitution, and a tiled batched GEMM for every rank-nb update and
+// for the Schur-complement products of eq. merge.
+//
+// Every kernel walks an array of per-problem descriptors, so one launch covers
+// all leaves or all merges of a tree level (of one or of many problems).
+//
+// Panel factorisation: one CTA per matrix; the panel (rows k0..m-1, nb columns)
+// is staged in shared memory when it fits, the pivot search is a warp-shuffle
+// argmax, and the scale + rank-1 update of each column is fused.  Row swaps and
+// the unit-lower triangular solve of the block row run one warp per column with
+// the block row held in registers (lane = row).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "hps_kernels.cuh"
+
+namespace hps {
+
+constexpr int kNB = 32;  // panel width == warp width (lane = row of the block row)
+
+// ------------------------------------------------------------------- GEMM tile
+// C[m0:m0+BM, n0:n0+BN] = beta C + alpha A[m0:, 0:K] B[0:K, n0:].
+// Threads: (BM/TM) x (BN/TN); thread t covers TM consecutive rows and TN
+// consecutive columns, with the column-tile index varying fastest so that one
+// warp owns a contiguous band of rows and a ragged tail of rows idles whole warps.
+template <typename R, int BM_, int BN_, int BK_, int TM_, int TN_>
+struct Tile {
+  static constexpr int BM = BM_, BN = BN_, BK = BK_, TM = TM_, TN = TN_;
+  static constexpr int NTN = BN / TN;
+  static constexpr int NTM = BM / TM;
+  static constexpr int NT = NTN * NTM;
+  static constexpr int SMEM = (BK * BM + BK * BN) * (int)sizeof(R);
+
+  __device__ static void run(int M, int N, int K, R alpha, const R* __restrict__ A, int lda,
+                             const R* __restrict__ B, int ldb, R beta, R* __restrict__ C, int ldc,
+                             int m0, int n0, R* sm) {
+    R* As = sm;            // [BK][BM]
+    R* Bs = sm + BK * BM;  // [BK][BN]
+    const int t = threadIdx.x;
+    const int tn = t % NTN, tm = t / NTN;
+    const int r0 = tm * TM, c0 = tn * TN;
+    // first row of this warp's band; the band is idle when it starts past M
+    const int warp_row0 = (((t / 32) * 32) / NTN) * TM;
+    const bool warp_live = (m0 + warp_row0) < M;
+    R acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = R(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      for (int e = t; e < BM * BK; e += NT) {
+        int i = e % BM, k = e / BM;
+        int gi = m0 + i, gk = k0 + k;
+        As[k * BM + i] = (gi < M && gk < K) ? A[gi + (size_t)gk * lda] : R(0);
+      }
+      for (int e = t; e < BK * BN; e += NT) {
+        int k = e % BK, j = e / BK;
+        int gk = k0 + k, gj = n0 + j;
+        Bs[k * BN + j] = (gk < K && gj < N) ? B[gk + (size_t)gj * ldb] : R(0);
+      }
+      __syncthreads();
+      if (warp_live) {
+#pragma unroll 4
+        for (int k = 0; k < BK; ++k) {
+          R a[TM], b[TN];
+#pragma unroll
+          for (int i = 0; i < TM; ++i) a[i] = As[k * BM + r0 + i];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) b[j] = Bs[k * BN + c0 + j];
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      int gi = m0 + r0 + i;
+      if (gi >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        int gj = n0 + c0 + j;
+        if (gj >= N) continue;
+        R* cp = C + gi + (size_t)gj * ldc;
+        *cp = (beta == R(0)) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *cp);
+      }
+    }
+  }
+};
+
+template <typename R>
+using TileSq = Tile<R, 64, 64, 16, 4, 4>;
+template <typename R>
+using TileNarrow = Tile<R, 128, 16, 16, 4, 4>;
+
+// ------------------------------------------------------------ explicit GEMMs
+template <typename R, class TL>
+__global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<R>* __restrict__ d, int tpm,
+                                                 int tpn, R alpha, R beta) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int per = tpm * tpn;
+  const GemmDesc<R> g = d[blockIdx.x / per];
+  const int tile = blockIdx.x % per;
+  const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
+  if (m0 >= g.M || n0 >= g.N) return;
+  TL::run(g.M, g.N, g.K, alpha, g.A, g.lda, g.B, g.ldb, beta, g.C, g.ldc, m0, n0,
+          reinterpret_cast<R*>(smraw));
+}
+
+template <typename R, class TL>
+static void launch_gemm(const GemmDesc<R>* d, int nd, int max_M, int max_N, R alpha, R beta,
+                        cudaStream_t st) {
+  int tpm = (max_M + TL::BM - 1) / TL::BM, tpn = (max_N + TL::BN - 1) / TL::BN;
+  if (nd <= 0 || tpm <= 0 || tpn <= 0) return;
+  long long blocks = (long long)nd * tpm * tpn;
+  k_gemm<R, TL><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
+}
+
+template <typename R>
+void gemm_batched(const GemmDesc<R>* d_desc, int ndesc, int max_M, int max_N, R alpha, R beta,
+                  cudaStream_t st) {
+  if (max_N <= 16)
+    launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st);
+  else
+    launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st);
+}
+
+// ------------------------------------------------------------ LU: the panel
+// Factor columns k0..k0+nbk-1 (rows k0..m-1) of one matrix per CTA.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lu_panel(const LuDesc<R>* __restrict__ d, int k0,
+                                                  int smem_elems, int* status) {
+  const LuDesc<R> D = d[blockIdx.x];
+  const int m = D.m;
+  if (k0 >= m) return;
+  const int nbk = min(kNB, m - k0);
+  const int rows = m - k0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* sm = reinterpret_cast<R*>(smraw);
+  __shared__ R red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_piv;
+  const bool staged = rows * nbk <= smem_elems;
+  R* A0 = D.A + k0 + (size_t)k0 * D.lda;
+  R* P = staged ? sm : A0;
+  const int ldp = staged ? rows : D.lda;
+  if (staged) {
+    for (int e = threadIdx.x; e < rows * nbk; e += blockDim.x) {
+      int i = e % rows, c = e / rows;
+      P[i + c * ldp] = A0[i + (size_t)c * D.lda];
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int jj = 0; jj < nbk; ++jj) {
+    // pivot search: largest |P(i, jj)| over i >= jj, ties to the smaller row
+    R best = R(-1);
+    int bi = jj;
+    for (int i = jj + threadIdx.x; i < rows; i += blockDim.x) {
+      R v = fabs(P[i + jj * ldp]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      R ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[wid] = best;
+      red_i[wid] = bi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      best = lane < nw ? red_v[lane] : R(-1);
+      bi = lane < nw ? red_i[lane] : jj;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        R ov = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) {
+          best = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_piv = bi;
+        D.ipiv[k0 + jj] = k0 + bi;
+      }
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != jj) {
+      for (int c = threadIdx.x; c < nbk; c += blockDim.x) {
+        R a = P[jj + c * ldp];
+        P[jj + c * ldp] = P[piv + c * ldp];
+        P[piv + c * ldp] = a;
+      }
+      __syncthreads();
+    }
+    const R pv = P[jj + jj * ldp];
+    const bool bad = !(pv != R(0)) || !isfinite(pv);
+    if (bad && threadIdx.x == 0 && status) atomicCAS(status, 0, D.box + 1);
+    const R inv = bad ? R(0) : R(1) / pv;
+    for (int i = jj + 1 + threadIdx.x; i < rows; i += blockDim.x) {
+      R l = P[i + jj * ldp] * inv;
+      P[i + jj * ldp] = l;
+      for (int c = jj + 1; c < nbk; ++c) P[i + c * ldp] = fma(-l, P[jj + c * ldp], P[i + c * ldp]);
+    }
+    __syncthreads();
+  }
+  if (staged) {
+    for (int e = threadIdx.x; e < rows * nbk; e += blockDim.x) {
+      int i = e % rows, c = e / rows;
+      A0[i + (size_t)c * D.lda] = P[i + c * ldp];
+    }
+  }
+}
+
+// ----------------------------------------- LU: swaps + unit-lower block solve
+// For every column outside the panel: apply the panel's row interchanges, then
+// (trailing columns of A and columns of B) solve with the unit-lower L11.
+// One warp per column.  The interchanges of a panel move at most 2*nb rows;
+// their net permutation is computed once per CTA.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restrict__ d, int k0,
+                                                      int chunks, int cols_per_cta,
+                                                      int swap_left) {
+  const LuDesc<R> D = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int m = D.m;
+  if (k0 >= m) return;
+  const int nbk = min(kNB, m - k0);
+  const int nleft = swap_left ? k0 : 0;
+  const int ntr = m - k0 - nbk;
+  const int total = nleft + ntr + D.nrhs;
+  const int cbeg = chunk * cols_per_cta;
+  if (cbeg >= total) return;
+  const int cend = min(total, cbeg + cols_per_cta);
+  __shared__ R L11[kNB * kNB];
+  __shared__ int rows_inv[2 * kNB];  // involved rows (relative to k0)
+  __shared__ int src_of[2 * kNB];    // new value of rows_inv[t] comes from rows_inv[src_of[t]]
+  __shared__ int s_nr;
+  for (int e = threadIdx.x; e < nbk * nbk; e += blockDim.x) {
+    int i = e % nbk, j = e / nbk;
+    L11[i + j * kNB] = D.A[(k0 + i) + (size_t)(k0 + j) * D.lda];
+  }
+  if (threadIdx.x == 0) {
+    // rows 0..nbk-1 plus every pivot row beyond the block
+    int nr = nbk;
+    for (int i = 0; i < nbk; ++i) rows_inv[i] = i;
+    for (int j = 0; j < nbk; ++j) {
+      int pr = D.ipiv[k0 + j] - k0;
+      bool found = false;
+      for (int t = 0; t < nr; ++t) found |= (rows_inv[t] == pr);
+      if (!found) rows_inv[nr++] = pr;
+    }
+    // apply the interchanges to the slot contents
+    int content[2 * kNB];
+    for (int t = 0; t < nr; ++t) content[t] = t;
+    for (int j = 0; j < nbk; ++j) {
+      int pr = D.ipiv[k0 + j] - k0;
+      int tj = j, tp = 0;
+      for (int t = 0; t < nr; ++t)
+        if (rows_inv[t] == pr) tp = t;
+      int c = content[tj];
+      content[tj] = content[tp];
+      content[tp] = c;
+    }
+    for (int t = 0; t < nr; ++t) src_of[t] = content[t];
+    s_nr = nr;
+  }
+  __syncthreads();
+  const int nr = s_nr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int col = cbeg + wid; col < cend; col += nw) {
+    R* x;
+    bool solve;
+    if (col < nleft) {
+      x = D.A + k0 + (size_t)col * D.lda;
+      solve = false;
+    } else if (col < nleft + ntr) {
+      x = D.A + k0 + (size_t)(k0 + nbk + (col - nleft)) * D.lda;
+      solve = true;
+    } else {
+      x = D.B + k0 + (size_t)(col - nleft - ntr) * D.ldb;
+      solve = true;
+    }
+    // gather the involved rows (lane holds slots lane and lane+32)
+    R v0 = lane < nr ? x[rows_inv[lane]] : R(0);
+    R v1 = (lane + 32) < nr ? x[rows_inv[lane + 32]] : R(0);
+    // permuted values: slot t takes the old value of slot src_of[t]
+    int s0 = lane < nr ? src_of[lane] : 0;
+    int s1 = (lane + 32) < nr ? src_of[lane + 32] : 0;
+    R n0a = __shfl_sync(0xffffffffu, v0, s0 & 31);
+    R n0b = __shfl_sync(0xffffffffu, v1, s0 & 31);
+    R n1a = __shfl_sync(0xffffffffu, v0, s1 & 31);
+    R n1b = __shfl_sync(0xffffffffu, v1, s1 & 31);
+    R w0 = s0 < 32 ? n0a : n0b;
+    R w1 = s1 < 32 ? n1a : n1b;
+    if ((lane + 32) < nr) x[rows_inv[lane + 32]] = w1;
+    // w0 of lanes < nbk is the block row; solve with unit-lower L11
+    if (solve) {
+      for (int j = 0; j < nbk - 1; ++j) {
+        R xj = __shfl_sync(0xffffffffu, w0, j);
+        if (lane > j && lane < nbk) w0 = fma(-L11[lane + j * kNB], xj, w0);
+      }
+    }
+    if (lane < nr) x[rows_inv[lane]] = w0;
+  }
+}
+
+// ------------------------------------------------------ LU: trailing update
+// Rows k0+nbk..m-1 of (trailing columns of A, columns of B) -= L21 * U12.
+template <typename R, class TL>
+__global__ void __launch_bounds__(TL::NT) k_lu_update(const LuDesc<R>* __restrict__ d, int k0,
+                                                      int tpm, int tpnA, int tpnB) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int per = tpm * (tpnA + tpnB);
+  const LuDesc<R> D = d[blockIdx.x / per];
+  const int tile = blockIdx.x % per;
+  const int m = D.m;
+  if (k0 >= m) return;
+  const int nbk = min(kNB, m - k0);
+  const int r0 = k0 + nbk;
+  const int M = m - r0;
+  if (M <= 0) return;
+  const int tmi = tile % tpm, tni = tile / tpm;
+  const R* L21 = D.A + r0 + (size_t)k0 * D.lda;
+  if (tni < tpnA) {
+    const int N = m - r0;
+    const int m0 = tmi * TL::BM, n0 = tni * TL::BN;
+    if (m0 >= M || n0 >= N) return;
+    TL::run(M, N, nbk, R(-1), L21, D.lda, D.A + k0 + (size_t)r0 * D.lda, D.lda, R(1),
+            D.A + r0 + (size_t)r0 * D.lda, D.lda, m0, n0, reinterpret_cast<R*>(smraw));
+  } else {
+    const int N = D.nrhs;
+    const int m0 = tmi * TL::BM, n0 = (tni - tpnA) * TL::BN;
+    if (m0 >= M || n0 >= N) return;
+    TL::run(M, N, nbk, R(-1), L21, D.lda, D.B + k0, D.ldb, R(1), D.B + r0, D.ldb, m0, n0,
+            reinterpret_cast<R*>(smraw));
+  }
+}
+
+// ------------------------------------------- back substitution: diagonal block
+// Rows kb0..kb0+nbk-1 of B := U11^{-1} (those rows).  One warp per column.
+template <typename R>
+__global__ void __launch_bounds__(256) k_trsm_upper(const LuDesc<R>* __restrict__ d, int kb0,
+                                                    int chunks, int cols_per_cta) {
+  const LuDesc<R> D = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int m = D.m;
+  if (kb0 >= m) return;
+  const int nbk = min(kNB, m - kb0);
+  const int cbeg = chunk * cols_per_cta;
+  if (cbeg >= D.nrhs) return;
+  const int cend = min(D.nrhs, cbeg + cols_per_cta);
+  __shared__ R U11[kNB * kNB];
+  for (int e = threadIdx.x; e < nbk * nbk; e += blockDim.x) {
+    int i = e % nbk, j = e / nbk;
+    U11[i + j * kNB] = D.A[(kb0 + i) + (size_t)(kb0 + j) * D.lda];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int col = cbeg + wid; col < cend; col += nw) {
+    R* x = D.B + kb0 + (size_t)col * D.ldb;
+    R v = lane < nbk ? x[lane] : R(0);
+    for (int j = nbk - 1; j >= 0; --j) {
+      R dj = U11[j + j * kNB];
+      R xj = __shfl_sync(0xffffffffu, v, j);
+      xj = (dj != R(0)) ? xj / dj : R(0);
+      if (lane == j) v = xj;
+      if (lane < j) v = fma(-U11[lane + j * kNB], xj, v);
+    }
+    if (lane < nbk) x[lane] = v;
+  }
+}
+
+// ---------------------------------------------- back substitution: update
+// Rows 0..kb0-1 of B -= U[0:kb0, kb0:kb0+nbk] * B[kb0:kb0+nbk, :].
+template <typename R, class TL>
+__global__ void __launch_bounds__(TL::NT) k_backsub_update(const LuDesc<R>* __restrict__ d,
+                                                           int kb0, int tpm, int tpn) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int per = tpm * tpn;
+  const LuDesc<R> D = d[blockIdx.x / per];
+  const int tile = blockIdx.x % per;
+  if (kb0 >= D.m || kb0 == 0) return;
+  const int nbk = min(kNB, D.m - kb0);
+  const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
+  if (m0 >= kb0 || n0 >= D.nrhs) return;
+  TL::run(kb0, D.nrhs, nbk, R(-1), D.A + (size_t)kb0 * D.lda, D.lda, D.B + kb0, D.ldb, R(1), D.B,
+          D.ldb, m0, n0, reinterpret_cast<R*>(smraw));
+}
+
+// ------------------------------------------------------------------ driver
+template <typename R>
+void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, bool swap_left,
+                      int* d_status, cudaStream_t st) {
+  if (nd <= 0 || max_m <= 0) return;
+  using TL = TileSq<R>;
+  using TN = TileNarrow<R>;
+  // panel staging budget: keep two CTAs per SM
+  const int smem_bytes = 96 * 1024;
+  const int smem_elems = smem_bytes / (int)sizeof(R);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_lu_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    attr_done = true;
+  }
+  const int cols_per_cta = 64;
+  for (int k0 = 0; k0 < max_m; k0 += kNB) {
+    k_lu_panel<R><<<nd, 256, smem_bytes, st>>>(d_desc, k0, smem_elems, d_status);
+    int total_cols = (swap_left ? k0 : 0) + max_m + max_nrhs;
+    int chunks = (total_cols + cols_per_cta - 1) / cols_per_cta;
+    k_lu_swap_trsm<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(
+        d_desc, k0, chunks, cols_per_cta, swap_left ? 1 : 0);
+    int rem = max_m - k0 - kNB;
+    if (rem > 0) {
+      int tpm = (rem + TL::BM - 1) / TL::BM;
+      int tpnA = (rem + TL::BN - 1) / TL::BN;
+      int tpnB = (max_nrhs + TL::BN - 1) / TL::BN;
+      long long blocks = (long long)nd * tpm * (tpnA + tpnB);
+      k_lu_update<R, TL><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d_desc, k0, tpm, tpnA, tpnB);
+    }
+  }
+  const int last = ((max_m - 1) / kNB) * kNB;
+  for (int kb0 = last; kb0 >= 0; kb0 -= kNB) {
+    int chunks = (max_nrhs + cols_per_cta - 1) / cols_per_cta;
+    k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, kb0, chunks,
+                                                                       cols_per_cta);
+    if (kb0 > 0) {
+      if (max_nrhs <= 16) {
+        int tpm = (kb0 + TN::BM - 1) / TN::BM, tpn = (max_nrhs + TN::BN - 1) / TN::BN;
+        k_backsub_update<R, TN><<<(unsigned)((long long)nd * tpm * tpn), TN::NT, TN::SMEM, st>>>(
+            d_desc, kb0, tpm, tpn);
+      } else {
+        int tpm = (kb0 + TL::BM - 1) / TL::BM, tpn = (max_nrhs + TL::BN - 1) / TL::BN;
+        k_backsub_update<R, TL><<<(unsigned)((long long)nd * tpm * tpn), TL::NT, TL::SMEM, st>>>(
+            d_desc, kb0, tpm, tpn);
+      }
+    }
+  }
+}
+
+template void lu_solve_batched<double>(const LuDesc<double>*, int, int, int, bool, int*,
+                                       cudaStream_t);
+template void lu_solve_batched<float>(const LuDesc<float>*, int, int, int, bool, int*,
+                                      cudaStream_t);
+template void gemm_batched<double>(const GemmDesc<double>*, int, int, int, double, double,
+                                   cudaStream_t);
+template void gemm_batched<float>(const GemmDesc<float>*, int, int, int, float, float,
+                                  cudaStream_t);
+
+}  // namespace hps

@@ -1,0 +1,130 @@
+// Merge gather and downward-pass scatter kernels (Section 4, Algorithms 1-2).
+//
+// A merge of children alpha, beta into tau needs, in the parent's exterior
+// ordering (J1, J2 interleaved as the parent's sides require):
+//   Aw = T33^a - T33^b                       (m x m)
+//   S  = [-T31^a | T32^b]                    (m x ne)   -> Aw^{-1} S by the LU
+//   Cw = [T13^a ; T23^b]                     (ne x m)
+//   Tp = diag(T11^a, T22^b)                  (ne x ne)  -> Tp + Cw S by a GEMM
+// J3 is a contiguous run of each child's exterior (alpha's east or north side,
+// beta's west or south side); src[k] names the child entry of parent position k.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "hps_kernels.cuh"
+
+namespace hps {
+
+template <typename Rin, typename R>
+__global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<Rin, R>* __restrict__ d,
+                                                      int chunks, int64_t per_chunk) {
+  const MergeDesc<Rin, R> g = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int64_t m = g.m, ne = g.ne;
+  const int64_t nA = m * m, nS = m * ne, nC = ne * m, nT = g.Tp ? ne * ne : 0;
+  const int64_t total = nA + nS + nC + nT;
+  const int64_t beg = (int64_t)chunk * per_chunk;
+  const int64_t end = min(total, beg + per_chunk);
+  const int64_t na = g.na, nb = g.nb;
+  for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    if (e < nA) {
+      int64_t i = e % m, j = e / m;
+      g.Aw[e] = (R)g.Ta[(g.j3a + i) + (g.j3a + j) * na] - (R)g.Tb[(g.j3b + i) + (g.j3b + j) * nb];
+    } else if (e < nA + nS) {
+      int64_t x = e - nA, i = x % m, k = x / m;
+      int s = g.src[k];
+      g.S[x] = s >= 0 ? -(R)g.Ta[(g.j3a + i) + (int64_t)s * na]
+                      : (R)g.Tb[(g.j3b + i) + (int64_t)(-s - 1) * nb];
+    } else if (e < nA + nS + nC) {
+      int64_t x = e - nA - nS, k = x % ne, i = x / ne;
+      int s = g.src[k];
+      g.Cw[x] = s >= 0 ? (R)g.Ta[s + (g.j3a + i) * na]
+                       : (R)g.Tb[(int64_t)(-s - 1) + (g.j3b + i) * nb];
+    } else {
+      int64_t x = e - nA - nS - nC, k = x % ne, k2 = x / ne;
+      int s = g.src[k], s2 = g.src[k2];
+      R v = R(0);
+      if (s >= 0 && s2 >= 0)
+        v = (R)g.Ta[s + (int64_t)s2 * na];
+      else if (s < 0 && s2 < 0)
+        v = (R)g.Tb[(int64_t)(-s - 1) + (int64_t)(-s2 - 1) * nb];
+      g.Tp[x] = v;
+    }
+  }
+}
+
+template <typename Rin, typename R>
+void merge_gather(const MergeDesc<Rin, R>* d_desc, int ndesc, int64_t max_work, cudaStream_t st) {
+  if (ndesc <= 0 || max_work <= 0) return;
+  const int64_t per_chunk = 256 * 16;
+  int chunks = (int)((max_work + per_chunk - 1) / per_chunk);
+  k_merge_gather<Rin, R><<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(d_desc, chunks,
+                                                                             per_chunk);
+}
+
+// ----------------------------------------------------------- downward pass
+// Exterior-value pool: uext[r*ext_total + box.ext_off + i] for right-hand side r.
+__global__ void k_root_scatter(const double* __restrict__ f, const int* __restrict__ root_from_f,
+                               int nbnd, int nrhs, double* __restrict__ uext, int64_t root_off,
+                               int64_t ext_total) {
+  int64_t n = (int64_t)nbnd * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int k = (int)(e % nbnd);
+    int64_t r = e / nbnd;
+    uext[r * ext_total + root_off + k] = f[r * nbnd + root_from_f[k]];
+  }
+}
+
+void solve_root_scatter(const double* f, const int* root_from_f, int nbnd, int nrhs,
+                        double* uext, int64_t root_off, int64_t ext_total, cudaStream_t st) {
+  int64_t n = (int64_t)nbnd * nrhs;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (blocks > 0)
+    k_root_scatter<<<blocks, 256, 0, st>>>(f, root_from_f, nbnd, nrhs, uext, root_off, ext_total);
+}
+
+// children's exterior values from the parent's and u3 = S u_parent
+__global__ void k_child_scatter(const SolveScatterDesc* __restrict__ d, int chunks,
+                                const double* __restrict__ u3, int64_t u3_total,
+                                double* __restrict__ uext, int64_t ext_total, int nrhs) {
+  const SolveScatterDesc g = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int64_t n = (int64_t)(g.na + g.nb) * nrhs;
+  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)chunks * blockDim.x) {
+    int64_t r = e / (g.na + g.nb);
+    int i = (int)(e % (g.na + g.nb));
+    const double* up = uext + r * ext_total + g.par_off;
+    const double* u3r = u3 + r * u3_total + g.u3_off;
+    if (i < g.na) {
+      int c = g.cmap_a[i];
+      uext[r * ext_total + g.a_off + i] = c >= 0 ? up[c] : u3r[-c - 1];
+    } else {
+      i -= g.na;
+      int c = g.cmap_b[i];
+      uext[r * ext_total + g.b_off + i] = c >= 0 ? up[c] : u3r[-c - 1];
+    }
+  }
+}
+
+void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, const double* u3,
+                         int64_t u3_total, double* uext, int64_t ext_total, int nrhs,
+                         cudaStream_t st) {
+  if (ndesc <= 0) return;
+  int64_t work = (int64_t)max_n * nrhs;
+  int chunks = (int)std::min<int64_t>((work + 255) / 256, 64);
+  k_child_scatter<<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(
+      d_desc, chunks, u3, u3_total, uext, ext_total, nrhs);
+}
+
+template void merge_gather<double, double>(const MergeDesc<double, double>*, int, int64_t,
+                                           cudaStream_t);
+template void merge_gather<float, float>(const MergeDesc<float, float>*, int, int64_t,
+                                         cudaStream_t);
+template void merge_gather<float, double>(const MergeDesc<float, double>*, int, int64_t,
+                                          cudaStream_t);
+
+}  // namespace hps

@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libhps (include/hps.h): argument marshalling only.
+
+Every entry point keeps the C name.  Host arrays are numpy float64 arrays;
+device arrays are CUDA torch tensors (float64, contiguous), passed by pointer
+when device_ptrs=True.  No step of the method runs here: a missing or unloadable
+libhps.so raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libhps.so"
+_lib = None
+
+HPS_OK = 0
+HPS_EINVAL = -1
+HPS_ENOMEM = -2
+HPS_ESINGULAR = -3
+HPS_ENOTCONVERGED = -4
+HPS_EDEVICE = -5
+HPS_FP64 = 0
+HPS_MIXED = 1
+
+COEFF_NAMES = ("c11", "c12", "c22", "c1", "c2", "c")
+
+EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
+           "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes", "hps_solve",
+           "hps_solve_ex", "hps_query", "hps_free", "hps_status_string")
+
+
+class HpsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {lib().hps_status_string(status).decode()} ({status})")
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("refine_tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
+                ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("form_root_dtn", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("last_update", ctypes.c_double), ("bad_box", ctypes.c_int)]
+
+
+def lib():
+    """Load libhps.so (built in-tree by paper_1307_2665_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _LIB_PATH.exists():
+        raise RuntimeError(f"libhps.so not built ({_LIB_PATH}); run paper_1307_2665_gb300.build.build()")
+    L = ctypes.CDLL(str(_LIB_PATH), mode=os.RTLD_LOCAL)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    L.hps_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.hps_default_options.restype = None
+    L.hps_boundary_count.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hps_boundary_count.restype = ctypes.c_int64
+    L.hps_cheb_nodes.argtypes = [Domain, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+    L.hps_boundary_nodes_grid.argtypes = [Domain, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp]
+    L.hps_build.argtypes = [Domain, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            vp, vp, vp, vp, vp, vp, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    L.hps_boundary_nodes.argtypes = [vp, dp]
+    L.hps_solve.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.POINTER(SolveInfo)]
+    L.hps_solve_ex.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(SolveInfo)]
+    L.hps_query.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
+                            ctypes.POINTER(ctypes.c_int64)]
+    L.hps_free.argtypes = [vp]
+    L.hps_status_string.argtypes = [ctypes.c_int]
+    L.hps_status_string.restype = ctypes.c_char_p
+    for name in ("hps_cheb_nodes", "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes",
+                 "hps_solve", "hps_solve_ex", "hps_query", "hps_free"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _domain(d):
+    return Domain(*map(float, d))
+
+
+def _ptr(a):
+    """Pointer of a float64 numpy array or CUDA torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def default_options():
+    o = Options()
+    lib().hps_default_options(ctypes.byref(o))
+    return o
+
+
+def hps_boundary_count(nx, ny, q):
+    return int(lib().hps_boundary_count(nx, ny, q))
+
+
+def hps_cheb_nodes(domain, nx, ny, p):
+    """(nx*ny, p, p, 2) coordinates of every leaf's Chebyshev grid."""
+    xy = np.empty((nx * ny, p, p, 2))
+    st = lib().hps_cheb_nodes(_domain(domain), nx, ny, p,
+                              xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != HPS_OK:
+        raise HpsError(st, "hps_cheb_nodes")
+    return xy
+
+
+def hps_boundary_nodes_grid(domain, nx, ny, q):
+    """(nbnd, 2) coordinates of the Dirichlet nodes, in the order of f."""
+    xy = np.empty((hps_boundary_count(nx, ny, q), 2))
+    st = lib().hps_boundary_nodes_grid(_domain(domain), nx, ny, q,
+                                       xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != HPS_OK:
+        raise HpsError(st, "hps_boundary_nodes_grid")
+    return xy
+
+
+class Handle:
+    """Owns an hps_handle; frees it on close() or garbage collection."""
+
+    def __init__(self, ptr, domain, nx, ny, p, q, device_ptrs):
+        self.ptr = ptr
+        self.domain, self.nx, self.ny, self.p, self.q = domain, nx, ny, p, q
+        self.device_ptrs = device_ptrs
+        self.nbnd = hps_boundary_count(nx, ny, q)
+
+    def close(self):
+        if self.ptr:
+            lib().hps_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hps_build(domain, nx, ny, p, q, coeffs, precision=HPS_FP64, device_ptrs=False, stream=None,
+              refine_tol=None, max_refine=None, fp64_top_levels=None, form_root_dtn=False,
+              check=True):
+    """Build stage.  coeffs: dict name -> array of nx*ny*p*p values (or None).
+    Returns a Handle, or raises HpsError (returns the status when check=False)."""
+    opt = default_options()
+    opt.precision = precision
+    opt.device_ptrs = 1 if device_ptrs else 0
+    opt.stream = stream
+    opt.form_root_dtn = 1 if form_root_dtn else 0
+    if refine_tol is not None:
+        opt.refine_tol = refine_tol
+    if max_refine is not None:
+        opt.max_refine = max_refine
+    if fp64_top_levels is not None:
+        opt.fp64_top_levels = fp64_top_levels
+    arrs = [coeffs.get(k) for k in COEFF_NAMES]
+    out = ctypes.c_void_p()
+    st = lib().hps_build(_domain(domain), nx, ny, p, q, *[_ptr(a) for a in arrs],
+                         ctypes.byref(opt), ctypes.byref(out))
+    if st != HPS_OK:
+        if check:
+            raise HpsError(st, "hps_build")
+        return st
+    return Handle(out.value, domain, nx, ny, p, q, device_ptrs)
+
+
+def hps_boundary_nodes(h: Handle):
+    xy = np.empty((h.nbnd, 2))
+    st = lib().hps_boundary_nodes(h.ptr, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != HPS_OK:
+        raise HpsError(st, "hps_boundary_nodes")
+    return xy
+
+
+def hps_solve(h: Handle, f, u=None, device_ptrs=None, info=None, check=True):
+    """Solve stage.  f: (nrhs, nbnd) or (nbnd,) float64; u: output of shape
+    (nrhs, nx*ny, p, p) (allocated on the host when omitted and f is on the host)."""
+    dev = h.device_ptrs if device_ptrs is None else bool(device_ptrs)
+    nrhs = 1 if f.ndim == 1 else f.shape[0]
+    if u is None:
+        if dev:
+            raise ValueError("device solves need a preallocated u")
+        u = np.empty((nrhs, h.nx * h.ny, h.p, h.p))
+    inf = SolveInfo() if info is None else info
+    st = lib().hps_solve_ex(h.ptr, _ptr(f), nrhs, _ptr(u), 1 if dev else 0, ctypes.byref(inf))
+    if st != HPS_OK and check:
+        raise HpsError(st, "hps_solve")
+    return u
+
+
+def hps_query(h: Handle):
+    nl, p, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nb, by = ctypes.c_int64(), ctypes.c_int64()
+    st = lib().hps_query(h.ptr, ctypes.byref(nl), ctypes.byref(p), ctypes.byref(q),
+                         ctypes.byref(nb), ctypes.byref(by))
+    if st != HPS_OK:
+        raise HpsError(st, "hps_query")
+    return {"n_leaves": nl.value, "p": p.value, "q": q.value, "nbnd": nb.value,
+            "device_bytes": by.value}
+
+
+def hps_free(h: Handle):
+    h.close()

@@ -1,0 +1,82 @@
+"""The C-ABI library: it builds, loads, exports every symbol include/hps.h
+declares, and its host-only entry points (node coordinates, options, status
+text, argument validation) behave as documented.  No GPU needed."""
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from oracle import hps_oracle as O
+from paper_1307_2665_gb300 import hps
+from paper_1307_2665_gb300.build import build
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def _declared():
+    txt = (ROOT / "include" / "hps.h").read_text()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(hps_[a-z_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert len(names) >= 10
+    L = ctypes.CDLL(str(ROOT / "paper_1307_2665_gb300" / "_lib" / "libhps.so"))
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(hps.EXPORTS)
+
+
+@pytest.mark.parametrize("dom,nx,ny,p,q", [((0, 1, 0, 1), 3, 2, 16, 14),
+                                           ((-0.3, 0.9, 0.1, 1.7), 4, 7, 9, 9),
+                                           ((2.0, 2.5, -1.0, 3.0), 1, 1, 5, 2)])
+def test_node_coordinates_match_oracle(dom, nx, ny, p, q):
+    """hps_cheb_nodes / hps_boundary_nodes_grid give the nodes the oracle uses
+    (Chebyshev extreme points per leaf, Gauss-Legendre points on Gamma in
+    counter-clockwise order) to rounding."""
+    a = hps.hps_cheb_nodes(dom, nx, ny, p)
+    b = O.cheb_grid(dom, nx, ny, p)
+    assert np.max(np.abs(a - b)) < 1e-14 * max(1.0, np.max(np.abs(b)))
+    ga = hps.hps_boundary_nodes_grid(dom, nx, ny, q)
+    gb = O.boundary_points(O.Problem(dom, nx, ny, p, q, {}))
+    assert ga.shape == gb.shape == (hps.hps_boundary_count(nx, ny, q), 2)
+    assert np.max(np.abs(ga - gb)) < 1e-14 * max(1.0, np.max(np.abs(gb)))
+
+
+def test_default_options_and_status_strings():
+    o = hps.default_options()
+    assert o.precision == hps.HPS_FP64 and o.device_ptrs == 0 and o.max_refine == 10
+    assert abs(o.refine_tol - 1e-11) < 1e-20 and o.fp64_top_levels == 2
+    L = hps.lib()
+    for st in (0, -1, -2, -3, -4, -5):
+        assert len(L.hps_status_string(st)) > 0
+    assert L.hps_status_string(123) == b"unknown status"
+
+
+@pytest.mark.parametrize("args", [
+    dict(nx=0, ny=2, p=16, q=14), dict(nx=2, ny=2, p=2, q=1), dict(nx=2, ny=2, p=8, q=9),
+    dict(nx=2, ny=2, p=8, q=0), dict(nx=2, ny=-1, p=8, q=4)])
+def test_build_rejects_bad_sizes_before_device_work(args):
+    """Validation happens before any device work, so it runs without a GPU."""
+    st = hps.hps_build((0, 1, 0, 1), args["nx"], args["ny"], args["p"], args["q"], {}, check=False)
+    assert st == hps.HPS_EINVAL
+
+
+def test_build_rejects_degenerate_domain():
+    assert hps.hps_build((1, 1, 0, 1), 2, 2, 8, 6, {}, check=False) == hps.HPS_EINVAL
+    assert hps.hps_build((0, 1, 0, float("nan")), 2, 2, 8, 6, {}, check=False) == hps.HPS_EINVAL
+
+
+def test_null_pointer_arguments():
+    L = hps.lib()
+    assert L.hps_free(None) == hps.HPS_OK
+    assert L.hps_solve(None, None, 1, None, None) == hps.HPS_EINVAL
+    assert L.hps_cheb_nodes(hps.Domain(0, 1, 0, 1), 2, 2, 8, None) == hps.HPS_EINVAL
