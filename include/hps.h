@@ -48,7 +48,8 @@ extern "C" {
 #endif
 
 #define HPS_OK 0
-#define HPS_EINVAL (-1)         /* bad sizes, p < 3, q < 1, q > p, NULL required pointer */
+#define HPS_EINVAL (-1)         /* bad sizes, p < 3, q < 1, q > p, q == p on a grid with
+                                   interior vertices (see hps_build), NULL required pointer */
 #define HPS_ENOMEM (-2)         /* device or host allocation failed, or over the memory budget */
 #define HPS_ESINGULAR (-3)      /* zero or non-finite pivot in a leaf or merge factorisation */
 #define HPS_ENOTCONVERGED (-4)  /* iterative refinement did not reach the tolerance */
@@ -100,8 +101,13 @@ int hps_boundary_nodes_grid(hps_domain d, int nx, int ny, int q, double* xy);
  * merge's solution operator S (eq. U_parent) and each leaf's interior solution
  * operator Y = -A_ii^{-1} A_ie L1 (eq. leaf_solve, Section 4.3) on the device.
  * The tree splits a box's longer side at floor(n/2) (ties: x), so any nx, ny
- * >= 1 is accepted.  Returns HPS_ESINGULAR if a pivot is zero or not finite
- * (e.g. a Helmholtz box at a Dirichlet resonance, Remark 1.1). */
+ * >= 1 is accepted.  q must be below p when nx > 1 and ny > 1: with q == p the
+ * side interpolants of Step 1 are bijective and averaging the two values at a
+ * corner leaves one free combination of the four edges at every interior vertex
+ * (+a, +a on the two horizontal edges, -a, -a on the two vertical ones), so the
+ * composite system is singular and so is every merge whose interface holds an
+ * interior vertex.  Returns HPS_ESINGULAR if a pivot is zero or not finite (e.g.
+ * a Helmholtz box at a Dirichlet resonance, Remark 1.1). */
 int hps_build(hps_domain d, int nx, int ny, int p, int q,
               const double* c11, const double* c12, const double* c22,
               const double* c1, const double* c2, const double* c,
@@ -114,9 +120,15 @@ int hps_boundary_nodes(hps_handle h, double* xy);
 /* Solve stage (Algorithm 2 and Section 4.3): given nrhs Dirichlet data sets f,
  * compute u at every leaf's Chebyshev grid.  In HPS_MIXED mode this runs
  * iterative refinement against the FP64 residual of the global collocation
- * system until the tolerance is met (HPS_ENOTCONVERGED otherwise; u then holds
- * the last iterate).  info may be NULL.  f and u follow options.device_ptrs of
- * the build. */
+ * system: each step solves the correction equation (interior residual as a
+ * body load, flux jumps at the interior Gauss nodes) with the low-precision
+ * factors and adds the correction in FP64.  It stops when the correction's
+ * max-norm relative to u's is at most refine_tol (HPS_OK), or after
+ * max_refine steps, or once the correction stops shrinking by half per step
+ * (the iterate has reached the accuracy the FP64 residual resolves for this
+ * conditioning); the latter two return HPS_ENOTCONVERGED with u holding the
+ * last iterate and info->last_update its relative correction.  info may be
+ * NULL.  f and u follow options.device_ptrs of the build. */
 int hps_solve(hps_handle h, const double* f, int nrhs, double* u, hps_solve_info* info);
 
 /* Same as hps_solve with an explicit pointer kind: device_ptrs 0 (host arrays,
@@ -133,6 +145,31 @@ int hps_free(hps_handle h);
 
 /* Static text for a status code. */
 const char* hps_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread inside the library (empty if
+ * none); valid until the next library call on this thread. */
+const char* hps_last_error(void);
+
+/* ---- Launch accounting (instrumentation, not part of the method) --------
+ * Every kernel launch of the library is counted.  With profiling enabled,
+ * each launch is bracketed by CUDA events on its stream and charged, under
+ * its kernel name, with the algorithmic flops and bytes of that launch (the
+ * dense work the method itself defines, counted from the problem sizes).
+ * hps_profile_read synchronises the device, fills up to max_out entries and
+ * returns the number of kernel names recorded since the last reset.  The
+ * name strings stay valid until the next hps_profile_read or reset. */
+typedef struct {
+  const char* name;
+  int64_t launches;
+  double ms;
+  double flops;
+  double bytes;
+} hps_kernel_stat;
+
+int64_t hps_kernel_launches(void);
+void hps_profile_enable(int on);
+void hps_profile_reset(void);
+int hps_profile_read(hps_kernel_stat* out, int max_out);
 
 #ifdef __cplusplus
 }

@@ -20,22 +20,25 @@ struct LuDesc {
   int box;
 };
 
-// C = beta C + alpha A B, all column-major.
-template <typename R>
+// C = beta C + alpha A B, all column-major (element types may differ from the
+// compute type of the launch).
+template <typename TA, typename TB = TA, typename TC = TA>
 struct GemmDesc {
-  const R* A;
-  const R* B;
-  R* C;
+  const TA* A;
+  const TB* B;
+  TC* C;
   int M, N, K, lda, ldb, ldc;
 };
 
 // Gather of one merge (Section 4, eq. U_parent and eq. merge):
 //   Aw = T33^a - T33^b (m x m), S = [-T31^a | T32^b] (m x ne, parent column order),
 //   Cw = [T13^a ; T23^b] (ne x m, parent row order), Tp = diag(T11^a, T22^b).
-template <typename Rin, typename R>
+// The children's T are read in their own precision (ta64 / tb64: double or float).
+template <typename R>
 struct MergeDesc {
-  const Rin* Ta;
-  const Rin* Tb;
+  const void* Ta;
+  const void* Tb;
+  int ta64, tb64;
   R* Aw;
   R* S;
   R* Cw;
@@ -54,16 +57,33 @@ struct SolveScatterDesc {
   int na, nb, m;
 };
 
+// Body-load pass of one merge (correction equation of iterative refinement):
+// z = (T33^a - T33^b)^{-1} (h3^b - h3^a), h^tau = [h1^a; h2^b] + [T13^a; T23^b] z,
+// and in the downward pass u3 = S u_parent + z.  Offsets index the exterior
+// pool (flux offsets h and values u share its layout), the u3 pool, and this
+// merge's block of its level's z buffer (z_off * nrhs elements in, ld m).
+struct BodyDesc {
+  int64_t par_off, a_off, b_off, u3_off, z_off;
+  const int* src;
+  int j3a, j3b, m, ne;
+};
+
 // ---- dense engine (hps_linalg.cu)
+// mode: kLuFactor (factor and solve; the factors are left partly unswapped),
+// kLuFactorKeep (factor and solve, leaving P A = L U in LAPACK form for later
+// solves), kLuSolveOnly (solve with factors from an earlier kLuFactorKeep).
+// h_m / h_nrhs: host copies of each descriptor's m and nrhs (launch accounting
+// only; null means every descriptor has the maximum sizes).
+constexpr int kLuFactor = 0, kLuFactorKeep = 1, kLuSolveOnly = 2;
 template <typename R>
-void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrhs, bool swap_left,
-                      int* d_status, cudaStream_t st);
-template <typename R>
-void gemm_batched(const GemmDesc<R>* d_desc, int ndesc, int max_M, int max_N, R alpha, R beta,
-                  cudaStream_t st);
+void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrhs, int mode,
+                      int* d_status, cudaStream_t st, const int* h_m, const int* h_nrhs);
+// name / flops / bytes: launch accounting (algorithmic work of this launch).
+template <typename R, typename TA, typename TB, typename TC>
+void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
+                  R beta, cudaStream_t st, const char* name, double flops, double bytes);
 
 // ---- leaf kernels (hps_leaf.cu)
-struct LeafConsts;  // device copy of the 1-D constants
 template <typename R>
 void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double hx, double hy,
                    const double* d_D, const double* d_Pg2c, R* Aii, R* Y, cudaStream_t st);
@@ -73,11 +93,28 @@ void leaf_dtn(const R* Y, int nleaves, int p, int q, double hx, double hy, const
 template <typename R>
 void leaf_post(const R* Y, const double* uext, const int64_t* leaf_ext_off, int64_t ext_total,
                int nleaves, int p, int q, int nrhs, const double* d_Pg2c, double* u,
-               cudaStream_t st);
+               cudaStream_t st, const R* z = nullptr, int accumulate = 0,
+               unsigned long long* maxabs = nullptr);
+template <typename R>
+void leaf_residual(const double* const* coef, int nl, int p, double hx, double hy,
+                   const double* d_D, const double* w, int nrhs, R* rbuf, cudaStream_t st);
+template <typename R>
+void leaf_flux(const double* w, const R* z, int nl, int p, int q, int nrhs, double hx, double hy,
+               const double* d_D, const double* d_Pc2g, const int64_t* leaf_off,
+               int64_t ext_total, double* hp, cudaStream_t st);
 
 // ---- merge / solve kernels (hps_merge.cu)
-template <typename Rin, typename R>
-void merge_gather(const MergeDesc<Rin, R>* d_desc, int ndesc, int64_t max_work, cudaStream_t st);
+template <typename R>
+void merge_gather(const MergeDesc<R>* d_desc, int ndesc, int64_t max_work, cudaStream_t st,
+                  double bytes);
+template <typename R>
+void merge_rhs(const BodyDesc* d, int nd, int max_m, const double* hp, int64_t ext_total,
+               int nrhs, R* zlev, cudaStream_t st);
+void merge_hpar(const BodyDesc* d, int nd, int max_ne, double* hp, int64_t ext_total, int nrhs,
+                cudaStream_t st);
+template <typename R>
+void z_to_u3(const BodyDesc* d, int nd, int max_m, const R* zlev, double* u3, int64_t u3_total,
+             int nrhs, cudaStream_t st);
 void solve_root_scatter(const double* f, const int* root_from_f, int nbnd, int nrhs,
                         double* uext, int64_t root_off, int64_t ext_total, cudaStream_t st);
 void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, const double* u3,

@@ -22,6 +22,7 @@
 #include <cstdint>
 
 #include "hps_kernels.cuh"
+#include "hps_prof.hpp"
 
 namespace hps {
 
@@ -30,6 +31,11 @@ namespace {
 struct CoefPtrs {
   const double* c[6];  // c11, c12, c22, c1, c2, c (null = absent)
 };
+
+template <typename R>
+const char* tname(const char* f64, const char* f32) {
+  return sizeof(R) == 8 ? f64 : f32;
+}
 
 }  // namespace
 
@@ -121,10 +127,17 @@ void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double 
   size_t smem = (size_t)(2 * p * p + 2 * p * q + 6 * p * p) * sizeof(double);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_leaf_assemble<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+    if (cudaFuncSetAttribute(k_leaf_assemble<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
+      return;  // reported by the caller's launch check
     attr = true;
   }
+  const double ni = (double)(p - 2) * (p - 2);
+  int ncoef = 0;
+  for (int k = 0; k < 6; ++k) ncoef += coef[k] != nullptr;
+  prof::Scope sc(tname<R>("leaf_assemble<f64>", "leaf_assemble<f32>"), st,
+                 (double)nleaves * (ni * ni * 8.0 + ni * 4.0 * q * 6.0),
+                 (double)nleaves * ((ni * ni + ni * 4.0 * q) * sizeof(R) + ncoef * p * p * 8.0));
   k_leaf_assemble<R><<<nleaves, 256, smem, st>>>(cp, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, Aii,
                                                  Y);
 }
@@ -210,18 +223,34 @@ void leaf_dtn(const R* Y, int nleaves, int p, int q, double hx, double hy, const
               const double* d_Pg2c, const double* d_Pc2g, R* T, cudaStream_t st) {
   if (nleaves <= 0) return;
   size_t smem = (size_t)(p * p + 2 * p * q + p * p * 8 + 4 * p * 8) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_leaf_dtn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
+      return;  // reported by the caller's launch check
+    attr = true;
+  }
+  const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
+  prof::Scope sc(tname<R>("leaf_dtn<f64>", "leaf_dtn<f32>"), st,
+                 (double)nleaves * nq * (8.0 * p * p + 2.0 * nq * p),
+                 (double)nleaves * (ni * nq + nq * nq) * sizeof(R));
   k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, d_Pc2g, T);
 }
 
 // ------------------------------------------------------------ post-process
-// u[(r*nl + l)*pp + node] = (W u_e)(node), W = [L1 ; Y], right-hand sides in
-// chunks of RC.
+// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 4.3), right-hand sides in
+// chunks of RC.  u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or
+// has it added (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior
+// values (ld ni).  maxabs (optional) receives max |w_full| (slot 0) and, after
+// accumulation, max |u| (slot 1), as the bit patterns of non-negative doubles.
 template <typename R>
 __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
                                                    const double* __restrict__ uext,
                                                    const int64_t* __restrict__ leaf_off,
                                                    int64_t ext_total, int nl, int p, int q,
                                                    int nrhs, const double* __restrict__ gPg2c,
+                                                   const R* __restrict__ z, int accumulate,
+                                                   unsigned long long* maxabs,
                                                    double* __restrict__ u) {
   constexpr int RC = 16;
   extern __shared__ __align__(16) double sm[];
@@ -232,6 +261,8 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
   const int64_t off = leaf_off[l];
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
   const R* Yl = Y + (size_t)l * ni * nq;
+  const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
+  double mdw = 0.0, mu = 0.0;
   for (int r0 = 0; r0 < nrhs; r0 += RC) {
     const int nr = min(RC, nrhs - r0);
     __syncthreads();
@@ -252,6 +283,8 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
 #pragma unroll
           for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(y, ue[g * RC + rr], acc[rr]);
         }
+        if (zl)
+          for (int rr = 0; rr < nr; ++rr) acc[rr] += (double)zl[ri + (size_t)(r0 + rr) * ni];
       } else {
         // boundary node: sides containing it, weights halved at corners
         const int sides[4][2] = {{0, b}, {2, b}, {1, a}, {3, a}};
@@ -267,7 +300,24 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
           }
         }
       }
-      for (int rr = 0; rr < nr; ++rr) u[((size_t)(r0 + rr) * nl + l) * pp + node] = acc[rr];
+      for (int rr = 0; rr < nr; ++rr) {
+        double* up = u + ((size_t)(r0 + rr) * nl + l) * pp + node;
+        double v = acc[rr];
+        mdw = fmax(mdw, fabs(v));
+        if (accumulate) v += *up;
+        mu = fmax(mu, fabs(v));
+        *up = v;
+      }
+    }
+  }
+  if (maxabs) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mdw = fmax(mdw, __shfl_xor_sync(0xffffffffu, mdw, o));
+      mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&maxabs[0], (unsigned long long)__double_as_longlong(mdw));
+      atomicMax(&maxabs[1], (unsigned long long)__double_as_longlong(mu));
     }
   }
 }
@@ -275,11 +325,168 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
 template <typename R>
 void leaf_post(const R* Y, const double* uext, const int64_t* leaf_ext_off, int64_t ext_total,
                int nleaves, int p, int q, int nrhs, const double* d_Pg2c, double* u,
-               cudaStream_t st) {
+               cudaStream_t st, const R* z, int accumulate, unsigned long long* maxabs) {
   if (nleaves <= 0 || nrhs <= 0) return;
   size_t smem = (size_t)(p * q + 4 * q * 16) * sizeof(double);
+  const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
+  prof::Scope sc(tname<R>("leaf_post<f64>", "leaf_post<f32>"), st,
+                 (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
+                 (double)nleaves * (ni * nq * sizeof(R) +
+                                    nrhs * (nq + (double)p * p * (accumulate ? 2 : 1)) * 8.0));
   k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, uext, leaf_ext_off, ext_total, nleaves, p, q,
-                                             nrhs, d_Pg2c, u);
+                                             nrhs, d_Pg2c, z, accumulate, maxabs, u);
+}
+
+// ------------------------------------------------------------ FP64 residual
+// r = -(A w_full) at the interior Chebyshev nodes of each leaf, in FP64, from
+// the coefficient samples and D (O(p^3) per leaf and right-hand side):
+//   A w = -c11 Dxx w - 2 c12 Dy (Dx w) - c22 Dyy w + c1 Dx w + c2 Dy w + c w.
+// Output rbuf[l*ni*nrhs + i + r*ni] in the element type of the correction solve.
+template <typename R>
+__global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int nl, int p, double sx,
+                                                       double sy, const double* __restrict__ gD,
+                                                       const double* __restrict__ w, int nrhs,
+                                                       R* __restrict__ rbuf) {
+  extern __shared__ __align__(16) double sm[];
+  const int pp = p * p, pi = p - 2, ni = pi * pi;
+  double* D = sm;
+  double* D2 = D + pp;
+  double* cf = D2 + pp;     // 6 x pp
+  double* W = cf + 6 * pp;  // pp
+  double* Wx = W + pp;      // pp: Dx w
+  const int l = blockIdx.x;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
+  for (int k = 0; k < 6; ++k)
+    for (int e = threadIdx.x; e < pp; e += blockDim.x)
+      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)l * pp + e] : 0.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    int i = e / p, j = e % p;
+    double s = 0.0;
+    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + j], s);
+    D2[e] = s;
+  }
+  R* rl = rbuf + (size_t)l * ni * nrhs;
+  for (int r = 0; r < nrhs; ++r) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) W[e] = w[((size_t)r * nl + l) * pp + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+      int a = e / p, b = e % p;
+      double s = 0.0;
+      for (int d = 0; d < p; ++d) s = fma(D[b * p + d], W[a * p + d], s);
+      Wx[e] = sx * s;
+    }
+    __syncthreads();
+    for (int ri = threadIdx.x; ri < ni; ri += blockDim.x) {
+      const int a = ri / pi + 1, b = ri % pi + 1, node = a * p + b;
+      double dxx = 0.0, dyy = 0.0, dy = 0.0, dxy = 0.0;
+      for (int k = 0; k < p; ++k) {
+        dxx = fma(D2[b * p + k], W[a * p + k], dxx);
+        dyy = fma(D2[a * p + k], W[k * p + b], dyy);
+        dy = fma(D[a * p + k], W[k * p + b], dy);
+        dxy = fma(D[a * p + k], Wx[k * p + b], dxy);
+      }
+      dxx *= sx * sx;
+      dyy *= sy * sy;
+      dy *= sy;
+      dxy *= sy;
+      const double Aw = -cf[node] * dxx - 2.0 * cf[pp + node] * dxy - cf[2 * pp + node] * dyy +
+                        cf[3 * pp + node] * Wx[node] + cf[4 * pp + node] * dy +
+                        cf[5 * pp + node] * W[node];
+      rl[ri + (size_t)r * ni] = (R)(-Aw);
+    }
+  }
+}
+
+template <typename R>
+void leaf_residual(const double* const* coef, int nl, int p, double hx, double hy,
+                   const double* d_D, const double* w, int nrhs, R* rbuf, cudaStream_t st) {
+  if (nl <= 0 || nrhs <= 0) return;
+  CoefPtrs cp;
+  for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
+  size_t smem = (size_t)(10 * p * p) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_leaf_residual<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
+      return;
+    attr = true;
+  }
+  const double pp = (double)p * p, ni = (double)(p - 2) * (p - 2);
+  prof::Scope sc("leaf_residual<f64>", st, (double)nl * nrhs * (2.0 * pp * p + 8.0 * ni * p),
+                 (double)nl * (nrhs * (pp * 8.0 + ni * sizeof(R)) + 6.0 * pp * 8.0));
+  k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, nl, p, 2.0 / hx, 2.0 / hy, d_D, w, nrhs, rbuf);
+}
+
+// ------------------------------------------------- flux offsets of the leaves
+// h[g] = (L4 L3 (w_full + [0 ; z]))[g]: the side fluxes, at the Gauss nodes,
+// of the current iterate plus the interior particular solution z = A_ii^{-1} r.
+// Written to the leaf's exterior slot of the flux pool hp (FP64).
+template <typename R>
+__global__ void __launch_bounds__(256) k_leaf_flux(const double* __restrict__ w,
+                                                   const R* __restrict__ z, int nl, int p, int q,
+                                                   int nrhs, double sx, double sy,
+                                                   const double* __restrict__ gD,
+                                                   const double* __restrict__ gPc2g,
+                                                   const int64_t* __restrict__ leaf_off,
+                                                   int64_t ext_total, double* __restrict__ hp) {
+  extern __shared__ __align__(16) double sm[];
+  const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
+  double* D = sm;
+  double* Pc = D + pp;   // q x p
+  double* V = Pc + q * p;
+  double* F = V + pp;    // 4p
+  const int l = blockIdx.x;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
+  for (int e = threadIdx.x; e < q * p; e += blockDim.x) Pc[e] = gPc2g[e];
+  const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
+  const int64_t off = leaf_off[l];
+  for (int r = 0; r < nrhs; ++r) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+      const int a = e / p, b = e % p;
+      double v = w[((size_t)r * nl + l) * pp + e];
+      if (zl && a > 0 && a < p - 1 && b > 0 && b < p - 1)
+        v += (double)zl[(a - 1) * pi + (b - 1) + (size_t)r * ni];
+      V[e] = v;
+    }
+    __syncthreads();
+    for (int sj = threadIdx.x; sj < 4 * p; sj += blockDim.x) {
+      const int s = sj / p, j = sj % p;
+      double acc = 0.0;
+      if (s == 0 || s == 2) {
+        const int row = (s == 0) ? 0 : p - 1;
+        for (int a = 0; a < p; ++a) acc = fma(D[row * p + a], V[a * p + j], acc);
+        acc *= sy;
+      } else {
+        const int col = (s == 1) ? p - 1 : 0;
+        for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], V[j * p + b], acc);
+        acc *= sx;
+      }
+      F[sj] = acc;
+    }
+    __syncthreads();
+    for (int g = threadIdx.x; g < nq; g += blockDim.x) {
+      const int s = g / q, k = g % q;
+      double acc = 0.0;
+      for (int j = 0; j < p; ++j) acc = fma(Pc[k * p + j], F[s * p + j], acc);
+      hp[(size_t)r * ext_total + off + g] = acc;
+    }
+  }
+}
+
+template <typename R>
+void leaf_flux(const double* w, const R* z, int nl, int p, int q, int nrhs, double hx, double hy,
+               const double* d_D, const double* d_Pc2g, const int64_t* leaf_off,
+               int64_t ext_total, double* hp, cudaStream_t st) {
+  if (nl <= 0 || nrhs <= 0) return;
+  size_t smem = (size_t)(2 * p * p + q * p + 4 * p) * sizeof(double);
+  prof::Scope sc("leaf_flux<f64>", st, (double)nl * nrhs * (8.0 * p * p + 8.0 * q * p),
+                 (double)nl * nrhs * ((double)p * p * 8.0 + (p - 2.0) * (p - 2.0) * sizeof(R) +
+                                      4.0 * q * 8.0));
+  k_leaf_flux<R><<<nl, 256, smem, st>>>(w, z, nl, p, q, nrhs, 2.0 / hx, 2.0 / hy, d_D, d_Pc2g,
+                                        leaf_off, ext_total, hp);
 }
 
 #define HPS_INST_LEAF(R)                                                                        \
@@ -288,7 +495,13 @@ void leaf_post(const R* Y, const double* uext, const int64_t* leaf_ext_off, int6
   template void leaf_dtn<R>(const R*, int, int, int, double, double, const double*,             \
                             const double*, const double*, R*, cudaStream_t);                    \
   template void leaf_post<R>(const R*, const double*, const int64_t*, int64_t, int, int, int,   \
-                             int, const double*, double*, cudaStream_t);
+                             int, const double*, double*, cudaStream_t, const R*, int,          \
+                             unsigned long long*);                                              \
+  template void leaf_residual<R>(const double* const*, int, int, double, double, const double*, \
+                                 const double*, int, R*, cudaStream_t);                         \
+  template void leaf_flux<R>(const double*, const R*, int, int, int, int, double, double,       \
+                             const double*, const double*, const int64_t*, int64_t, double*,    \
+                             cudaStream_t);
 HPS_INST_LEAF(double)
 HPS_INST_LEAF(float)
 

@@ -14,17 +14,39 @@
 // the block row held in registers (lane = row).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 
 #include "hps_kernels.cuh"
+#include "hps_prof.hpp"
 
 namespace hps {
 
 constexpr int kNB = 32;  // panel width == warp width (lane = row of the block row)
 
+template <typename R>
+struct TName;
+template <>
+struct TName<double> {
+  static const char* panel() { return "lu_panel<f64>"; }
+  static const char* swap() { return "lu_swap_trsm<f64>"; }
+  static const char* update() { return "lu_update<f64>"; }
+  static const char* trsm() { return "trsm_upper<f64>"; }
+  static const char* backsub() { return "backsub_update<f64>"; }
+};
+template <>
+struct TName<float> {
+  static const char* panel() { return "lu_panel<f32>"; }
+  static const char* swap() { return "lu_swap_trsm<f32>"; }
+  static const char* update() { return "lu_update<f32>"; }
+  static const char* trsm() { return "trsm_upper<f32>"; }
+  static const char* backsub() { return "backsub_update<f32>"; }
+};
+
 // ------------------------------------------------------------------- GEMM tile
-// C[m0:m0+BM, n0:n0+BN] = beta C + alpha A[m0:, 0:K] B[0:K, n0:].
+// C[m0:m0+BM, n0:n0+BN] = beta C + alpha A[m0:, 0:K] B[0:K, n0:], computed in R.
+// A, B and C may have other element types (converted on load and store).
 // Threads: (BM/TM) x (BN/TN); thread t covers TM consecutive rows and TN
 // consecutive columns, with the column-tile index varying fastest so that one
 // warp owns a contiguous band of rows and a ragged tail of rows idles whole warps.
@@ -36,9 +58,10 @@ struct Tile {
   static constexpr int NT = NTN * NTM;
   static constexpr int SMEM = (BK * BM + BK * BN) * (int)sizeof(R);
 
-  __device__ static void run(int M, int N, int K, R alpha, const R* __restrict__ A, int lda,
-                             const R* __restrict__ B, int ldb, R beta, R* __restrict__ C, int ldc,
-                             int m0, int n0, R* sm) {
+  // B and C may alias when one CTA owns all M rows of its columns (M <= BM).
+  template <typename TA, typename TB, typename TC>
+  __device__ static void run(int M, int N, int K, R alpha, const TA* __restrict__ A, int lda,
+                             const TB* B, int ldb, R beta, TC* C, int ldc, int m0, int n0, R* sm) {
     R* As = sm;            // [BK][BM]
     R* Bs = sm + BK * BM;  // [BK][BN]
     const int t = threadIdx.x;
@@ -56,12 +79,12 @@ struct Tile {
       for (int e = t; e < BM * BK; e += NT) {
         int i = e % BM, k = e / BM;
         int gi = m0 + i, gk = k0 + k;
-        As[k * BM + i] = (gi < M && gk < K) ? A[gi + (size_t)gk * lda] : R(0);
+        As[k * BM + i] = (gi < M && gk < K) ? (R)A[gi + (size_t)gk * lda] : R(0);
       }
       for (int e = t; e < BK * BN; e += NT) {
         int k = e % BK, j = e / BK;
         int gk = k0 + k, gj = n0 + j;
-        Bs[k * BN + j] = (gk < K && gj < N) ? B[gk + (size_t)gj * ldb] : R(0);
+        Bs[k * BN + j] = (gk < K && gj < N) ? (R)B[gk + (size_t)gj * ldb] : R(0);
       }
       __syncthreads();
       if (warp_live) {
@@ -88,8 +111,11 @@ struct Tile {
       for (int j = 0; j < TN; ++j) {
         int gj = n0 + c0 + j;
         if (gj >= N) continue;
-        R* cp = C + gi + (size_t)gj * ldc;
-        *cp = (beta == R(0)) ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *cp);
+        TC* cp = C + gi + (size_t)gj * ldc;
+        if (beta == R(0))
+          *cp = (TC)(alpha * acc[i][j]);
+        else  // accumulate in the wider of the two types
+          *cp = (TC)fma((TC)alpha, (TC)acc[i][j], (TC)beta * *cp);
       }
     }
   }
@@ -101,12 +127,12 @@ template <typename R>
 using TileNarrow = Tile<R, 128, 16, 16, 4, 4>;
 
 // ------------------------------------------------------------ explicit GEMMs
-template <typename R, class TL>
-__global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<R>* __restrict__ d, int tpm,
-                                                 int tpn, R alpha, R beta) {
+template <typename R, class TL, typename TA, typename TB, typename TC>
+__global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<TA, TB, TC>* __restrict__ d,
+                                                 int tpm, int tpn, R alpha, R beta) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int per = tpm * tpn;
-  const GemmDesc<R> g = d[blockIdx.x / per];
+  const GemmDesc<TA, TB, TC> g = d[blockIdx.x / per];
   const int tile = blockIdx.x % per;
   const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
   if (m0 >= g.M || n0 >= g.N) return;
@@ -114,28 +140,30 @@ __global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<R>* __restrict__
           reinterpret_cast<R*>(smraw));
 }
 
-template <typename R, class TL>
-static void launch_gemm(const GemmDesc<R>* d, int nd, int max_M, int max_N, R alpha, R beta,
-                        cudaStream_t st) {
+template <typename R, class TL, typename TA, typename TB, typename TC>
+static void launch_gemm(const GemmDesc<TA, TB, TC>* d, int nd, int max_M, int max_N, R alpha,
+                        R beta, cudaStream_t st, const char* name, double flops, double bytes) {
   int tpm = (max_M + TL::BM - 1) / TL::BM, tpn = (max_N + TL::BN - 1) / TL::BN;
   if (nd <= 0 || tpm <= 0 || tpn <= 0) return;
   long long blocks = (long long)nd * tpm * tpn;
-  k_gemm<R, TL><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
+  prof::Scope sc(name, st, flops, bytes);
+  k_gemm<R, TL, TA, TB, TC><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
 }
 
-template <typename R>
-void gemm_batched(const GemmDesc<R>* d_desc, int ndesc, int max_M, int max_N, R alpha, R beta,
-                  cudaStream_t st) {
+template <typename R, typename TA, typename TB, typename TC>
+void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
+                  R beta, cudaStream_t st, const char* name, double flops, double bytes) {
   if (max_N <= 16)
-    launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st);
+    launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st, name, flops,
+                                  bytes);
   else
-    launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st);
+    launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st, name, flops, bytes);
 }
 
 // ------------------------------------------------------------ LU: the panel
 // Factor columns k0..k0+nbk-1 (rows k0..m-1) of one matrix per CTA.
 template <typename R>
-__global__ void __launch_bounds__(256) k_lu_panel(const LuDesc<R>* __restrict__ d, int k0,
+__global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ d, int k0,
                                                   int smem_elems, int* status) {
   const LuDesc<R> D = d[blockIdx.x];
   const int m = D.m;
@@ -238,14 +266,14 @@ __global__ void __launch_bounds__(256) k_lu_panel(const LuDesc<R>* __restrict__ 
 template <typename R>
 __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restrict__ d, int k0,
                                                       int chunks, int cols_per_cta,
-                                                      int swap_left) {
+                                                      int swap_left, int b_only) {
   const LuDesc<R> D = d[blockIdx.x / chunks];
   const int chunk = blockIdx.x % chunks;
   const int m = D.m;
   if (k0 >= m) return;
   const int nbk = min(kNB, m - k0);
-  const int nleft = swap_left ? k0 : 0;
-  const int ntr = m - k0 - nbk;
+  const int nleft = (swap_left && !b_only) ? k0 : 0;
+  const int ntr = b_only ? 0 : m - k0 - nbk;
   const int total = nleft + ntr + D.nrhs;
   const int cbeg = chunk * cols_per_cta;
   if (cbeg >= total) return;
@@ -356,37 +384,46 @@ __global__ void __launch_bounds__(TL::NT) k_lu_update(const LuDesc<R>* __restric
 }
 
 // ------------------------------------------- back substitution: diagonal block
-// Rows kb0..kb0+nbk-1 of B := U11^{-1} (those rows).  One warp per column.
+// Rows kb0..kb0+nbk-1 of B := U11^{-1} (those rows) by column-sweep back
+// substitution: one thread per column, the nbk values in registers, U11 and the
+// reciprocals of its diagonal in shared memory (broadcast reads).
 template <typename R>
 __global__ void __launch_bounds__(256) k_trsm_upper(const LuDesc<R>* __restrict__ d, int kb0,
-                                                    int chunks, int cols_per_cta) {
+                                                    int chunks) {
   const LuDesc<R> D = d[blockIdx.x / chunks];
   const int chunk = blockIdx.x % chunks;
   const int m = D.m;
-  if (kb0 >= m) return;
+  if (kb0 >= m || chunk * (int)blockDim.x >= D.nrhs) return;
   const int nbk = min(kNB, m - kb0);
-  const int cbeg = chunk * cols_per_cta;
-  if (cbeg >= D.nrhs) return;
-  const int cend = min(D.nrhs, cbeg + cols_per_cta);
-  __shared__ R U11[kNB * kNB];
-  for (int e = threadIdx.x; e < nbk * nbk; e += blockDim.x) {
-    int i = e % nbk, j = e / nbk;
-    U11[i + j * kNB] = D.A[(kb0 + i) + (size_t)(kb0 + j) * D.lda];
+  __shared__ R U[kNB][kNB + 1];
+  __shared__ R rd[kNB];
+  for (int e = threadIdx.x; e < kNB * kNB; e += blockDim.x) {
+    int i = e % kNB, j = e / kNB;
+    U[i][j] = (i < nbk && j < nbk) ? D.A[(kb0 + i) + (size_t)(kb0 + j) * D.lda] : R(0);
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int col = cbeg + wid; col < cend; col += nw) {
-    R* x = D.B + kb0 + (size_t)col * D.ldb;
-    R v = lane < nbk ? x[lane] : R(0);
-    for (int j = nbk - 1; j >= 0; --j) {
-      R dj = U11[j + j * kNB];
-      R xj = __shfl_sync(0xffffffffu, v, j);
-      xj = (dj != R(0)) ? xj / dj : R(0);
-      if (lane == j) v = xj;
-      if (lane < j) v = fma(-U11[lane + j * kNB], xj, v);
-    }
-    if (lane < nbk) x[lane] = v;
+  if (threadIdx.x < kNB) {
+    R dj = U[threadIdx.x][threadIdx.x];
+    rd[threadIdx.x] = (dj != R(0)) ? R(1) / dj : R(0);
   }
+  __syncthreads();
+  const int col = chunk * blockDim.x + threadIdx.x;
+  if (col >= D.nrhs) return;
+  R* x = D.B + kb0 + (size_t)col * D.ldb;
+  R v[kNB];
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) v[i] = (i < nbk) ? x[i] : R(0);
+#pragma unroll
+  for (int j = kNB - 1; j >= 0; --j) {
+    if (j < nbk) {
+      v[j] *= rd[j];
+#pragma unroll
+      for (int i = 0; i < j; ++i) v[i] = fma(-U[i][j], v[j], v[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kNB; ++i)
+    if (i < nbk) x[i] = v[i];
 }
 
 // ---------------------------------------------- back substitution: update
@@ -408,41 +445,119 @@ __global__ void __launch_bounds__(TL::NT) k_backsub_update(const LuDesc<R>* __re
 
 // ------------------------------------------------------------------ driver
 template <typename R>
-void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, bool swap_left,
-                      int* d_status, cudaStream_t st) {
+void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, int mode,
+                      int* d_status, cudaStream_t st, const int* h_m, const int* h_nrhs) {
   if (nd <= 0 || max_m <= 0) return;
+  const bool factor = mode != kLuSolveOnly;
+  const bool swap_left = mode == kLuFactorKeep;
+  const double es = (double)sizeof(R);
+  // algorithmic flops / bytes of each launch, from the host copy of the sizes
+  auto sum = [&](auto fn) {
+    double t = 0.0;
+    for (int i = 0; i < nd; ++i) t += fn(h_m ? h_m[i] : max_m, h_nrhs ? h_nrhs[i] : max_nrhs);
+    return t;
+  };
   using TL = TileSq<R>;
   using TN = TileNarrow<R>;
-  // panel staging budget: keep two CTAs per SM
-  const int smem_bytes = 96 * 1024;
-  const int smem_elems = smem_bytes / (int)sizeof(R);
+  // panel staging: as much shared memory as the tallest panel needs, up to the
+  // per-CTA maximum less the kernel's static shared arrays (taller panels are
+  // factored in global memory)
+  const int smem_max = 224 * 1024;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_lu_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_lu_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e != cudaSuccess) return;  // reported by the caller's launch check
     attr_done = true;
   }
   const int cols_per_cta = 64;
   for (int k0 = 0; k0 < max_m; k0 += kNB) {
-    k_lu_panel<R><<<nd, 256, smem_bytes, st>>>(d_desc, k0, smem_elems, d_status);
-    int total_cols = (swap_left ? k0 : 0) + max_m + max_nrhs;
+    if (factor) {
+      double fl = sum([&](int m, int nr) {
+        if (k0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - k0), rows = m - k0;
+        double t = 0.0;
+        for (int jj = 0; jj < nbk; ++jj) t += (double)(rows - jj - 1) * (2.0 * (nbk - jj - 1) + 1.0);
+        return t;
+      });
+      double by = sum([&](int m, int nr) {
+        return k0 < m ? 2.0 * (m - k0) * std::min(kNB, m - k0) * es : 0.0;
+      });
+      const int rows = max_m - k0;
+      const long long need = (long long)rows * std::min(kNB, rows) * (long long)sizeof(R);
+      const int smem_bytes = (int)std::min<long long>(need, smem_max);
+      const int smem_elems = smem_bytes / (int)sizeof(R);
+      const int threads = rows > 512 ? 512 : 256;
+      prof::Scope sc(TName<R>::panel(), st, fl, by);
+      k_lu_panel<R><<<nd, threads, smem_bytes, st>>>(d_desc, k0, smem_elems, d_status);
+    }
+    int total_cols = (factor ? (swap_left ? k0 : 0) + max_m : 0) + max_nrhs;
     int chunks = (total_cols + cols_per_cta - 1) / cols_per_cta;
-    k_lu_swap_trsm<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(
-        d_desc, k0, chunks, cols_per_cta, swap_left ? 1 : 0);
+    {
+      double fl = sum([&](int m, int nr) {
+        if (k0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - k0);
+        return (double)nbk * (nbk - 1) * ((factor ? m - k0 - nbk : 0) + nr);
+      });
+      double by = sum([&](int m, int nr) {
+        if (k0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - k0);
+        return 2.0 * nbk * ((swap_left ? k0 : 0) + (factor ? m - k0 - nbk : 0) + nr) * es;
+      });
+      prof::Scope sc(TName<R>::swap(), st, fl, by);
+      k_lu_swap_trsm<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(
+          d_desc, k0, chunks, cols_per_cta, swap_left ? 1 : 0, factor ? 0 : 1);
+    }
     int rem = max_m - k0 - kNB;
     if (rem > 0) {
       int tpm = (rem + TL::BM - 1) / TL::BM;
-      int tpnA = (rem + TL::BN - 1) / TL::BN;
+      int tpnA = factor ? (rem + TL::BN - 1) / TL::BN : 0;
       int tpnB = (max_nrhs + TL::BN - 1) / TL::BN;
       long long blocks = (long long)nd * tpm * (tpnA + tpnB);
+      double fl = sum([&](int m, int nr) {
+        if (k0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - k0);
+        double M = m - k0 - nbk, N = (factor ? m - k0 - nbk : 0) + nr;
+        return 2.0 * M * N * nbk;
+      });
+      double by = sum([&](int m, int nr) {
+        if (k0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - k0);
+        double M = m - k0 - nbk, N = (factor ? m - k0 - nbk : 0) + nr;
+        return (M * nbk + nbk * N + 2.0 * M * N) * es;
+      });
+      prof::Scope sc(TName<R>::update(), st, fl, by);
       k_lu_update<R, TL><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d_desc, k0, tpm, tpnA, tpnB);
     }
   }
   const int last = ((max_m - 1) / kNB) * kNB;
   for (int kb0 = last; kb0 >= 0; kb0 -= kNB) {
-    int chunks = (max_nrhs + cols_per_cta - 1) / cols_per_cta;
-    k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, kb0, chunks,
-                                                                       cols_per_cta);
+    {
+      double fl = sum([&](int m, int nr) {
+        if (kb0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - kb0);
+        return (double)nbk * nbk * nr;
+      });
+      double by = sum([&](int m, int nr) {
+        if (kb0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - kb0);
+        return (2.0 * nbk * nr + 0.5 * nbk * nbk) * es;
+      });
+      prof::Scope sc(TName<R>::trsm(), st, fl, by);
+      int chunks = (max_nrhs + 255) / 256;
+      k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, kb0, chunks);
+    }
     if (kb0 > 0) {
+      double fl = sum([&](int m, int nr) {
+        if (kb0 >= m) return 0.0;
+        return 2.0 * kb0 * nr * std::min(kNB, m - kb0);
+      });
+      double by = sum([&](int m, int nr) {
+        if (kb0 >= m) return 0.0;
+        int nbk = std::min(kNB, m - kb0);
+        return ((double)kb0 * nbk + nbk * nr + 2.0 * kb0 * nr) * es;
+      });
+      prof::Scope sc(TName<R>::backsub(), st, fl, by);
       if (max_nrhs <= 16) {
         int tpm = (kb0 + TN::BM - 1) / TN::BM, tpn = (max_nrhs + TN::BN - 1) / TN::BN;
         k_backsub_update<R, TN><<<(unsigned)((long long)nd * tpm * tpn), TN::NT, TN::SMEM, st>>>(
@@ -456,13 +571,17 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
   }
 }
 
-template void lu_solve_batched<double>(const LuDesc<double>*, int, int, int, bool, int*,
-                                       cudaStream_t);
-template void lu_solve_batched<float>(const LuDesc<float>*, int, int, int, bool, int*,
-                                      cudaStream_t);
-template void gemm_batched<double>(const GemmDesc<double>*, int, int, int, double, double,
-                                   cudaStream_t);
-template void gemm_batched<float>(const GemmDesc<float>*, int, int, int, float, float,
-                                  cudaStream_t);
+template void lu_solve_batched<double>(const LuDesc<double>*, int, int, int, int, int*,
+                                       cudaStream_t, const int*, const int*);
+template void lu_solve_batched<float>(const LuDesc<float>*, int, int, int, int, int*,
+                                      cudaStream_t, const int*, const int*);
+#define HPS_INST_GEMM(R, TA, TB, TC)                                                            \
+  template void gemm_batched<R, TA, TB, TC>(const GemmDesc<TA, TB, TC>*, int, int, int, R, R,   \
+                                            cudaStream_t, const char*, double, double);
+HPS_INST_GEMM(double, double, double, double)
+HPS_INST_GEMM(float, float, float, float)
+HPS_INST_GEMM(float, float, double, double)
+HPS_INST_GEMM(float, float, float, double)
+HPS_INST_GEMM(double, double, double, float)
 
 }  // namespace hps

@@ -14,13 +14,18 @@
 #include <cstdint>
 
 #include "hps_kernels.cuh"
+#include "hps_prof.hpp"
 
 namespace hps {
 
-template <typename Rin, typename R>
-__global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<Rin, R>* __restrict__ d,
+__device__ __forceinline__ double tload(const void* p, int f64, int64_t i) {
+  return f64 ? static_cast<const double*>(p)[i] : (double)static_cast<const float*>(p)[i];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<R>* __restrict__ d,
                                                       int chunks, int64_t per_chunk) {
-  const MergeDesc<Rin, R> g = d[blockIdx.x / chunks];
+  const MergeDesc<R> g = d[blockIdx.x / chunks];
   const int chunk = blockIdx.x % chunks;
   const int64_t m = g.m, ne = g.ne;
   const int64_t nA = m * m, nS = m * ne, nC = ne * m, nT = g.Tp ? ne * ne : 0;
@@ -31,37 +36,117 @@ __global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<Rin, R>* _
   for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
     if (e < nA) {
       int64_t i = e % m, j = e / m;
-      g.Aw[e] = (R)g.Ta[(g.j3a + i) + (g.j3a + j) * na] - (R)g.Tb[(g.j3b + i) + (g.j3b + j) * nb];
+      g.Aw[e] = (R)(tload(g.Ta, g.ta64, (g.j3a + i) + (g.j3a + j) * na) -
+                    tload(g.Tb, g.tb64, (g.j3b + i) + (g.j3b + j) * nb));
     } else if (e < nA + nS) {
       int64_t x = e - nA, i = x % m, k = x / m;
       int s = g.src[k];
-      g.S[x] = s >= 0 ? -(R)g.Ta[(g.j3a + i) + (int64_t)s * na]
-                      : (R)g.Tb[(g.j3b + i) + (int64_t)(-s - 1) * nb];
+      g.S[x] = s >= 0 ? (R)(-tload(g.Ta, g.ta64, (g.j3a + i) + (int64_t)s * na))
+                      : (R)tload(g.Tb, g.tb64, (g.j3b + i) + (int64_t)(-s - 1) * nb);
     } else if (e < nA + nS + nC) {
       int64_t x = e - nA - nS, k = x % ne, i = x / ne;
       int s = g.src[k];
-      g.Cw[x] = s >= 0 ? (R)g.Ta[s + (g.j3a + i) * na]
-                       : (R)g.Tb[(int64_t)(-s - 1) + (g.j3b + i) * nb];
+      g.Cw[x] = s >= 0 ? (R)tload(g.Ta, g.ta64, s + (g.j3a + i) * na)
+                       : (R)tload(g.Tb, g.tb64, (int64_t)(-s - 1) + (g.j3b + i) * nb);
     } else {
       int64_t x = e - nA - nS - nC, k = x % ne, k2 = x / ne;
       int s = g.src[k], s2 = g.src[k2];
       R v = R(0);
       if (s >= 0 && s2 >= 0)
-        v = (R)g.Ta[s + (int64_t)s2 * na];
+        v = (R)tload(g.Ta, g.ta64, s + (int64_t)s2 * na);
       else if (s < 0 && s2 < 0)
-        v = (R)g.Tb[(int64_t)(-s - 1) + (int64_t)(-s2 - 1) * nb];
+        v = (R)tload(g.Tb, g.tb64, (int64_t)(-s - 1) + (int64_t)(-s2 - 1) * nb);
       g.Tp[x] = v;
     }
   }
 }
 
-template <typename Rin, typename R>
-void merge_gather(const MergeDesc<Rin, R>* d_desc, int ndesc, int64_t max_work, cudaStream_t st) {
+template <typename R>
+void merge_gather(const MergeDesc<R>* d_desc, int ndesc, int64_t max_work, cudaStream_t st,
+                  double bytes) {
   if (ndesc <= 0 || max_work <= 0) return;
   const int64_t per_chunk = 256 * 16;
   int chunks = (int)((max_work + per_chunk - 1) / per_chunk);
-  k_merge_gather<Rin, R><<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(d_desc, chunks,
-                                                                             per_chunk);
+  prof::Scope sc(sizeof(R) == 8 ? "merge_gather<f64>" : "merge_gather<f32>", st, 0.0, bytes);
+  k_merge_gather<R><<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(d_desc, chunks,
+                                                                        per_chunk);
+}
+
+// ------------------------------------------------------ body-load upward pass
+// Right-hand side of a merge's interface equation for the correction:
+// (T33^a - T33^b) z = h3^b - h3^a, the flux offsets of the two children at J3.
+template <typename R>
+__global__ void k_merge_rhs(const BodyDesc* __restrict__ d, int chunks,
+                            const double* __restrict__ hp, int64_t ext_total, int nrhs,
+                            R* __restrict__ zlev) {
+  const BodyDesc g = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int64_t n = (int64_t)g.m * nrhs;
+  R* z = zlev + g.z_off * nrhs;
+  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)chunks * blockDim.x) {
+    const int64_t i = e % g.m, r = e / g.m;
+    const double* h = hp + r * ext_total;
+    z[i + r * g.m] = (R)(h[g.b_off + g.j3b + i] - h[g.a_off + g.j3a + i]);
+  }
+}
+
+// The parent's flux offsets before the Schur term: h^tau(k) = h^a(src) or h^b(src).
+__global__ void k_merge_hpar(const BodyDesc* __restrict__ d, int chunks, double* __restrict__ hp,
+                             int64_t ext_total, int nrhs) {
+  const BodyDesc g = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int64_t n = (int64_t)g.ne * nrhs;
+  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)chunks * blockDim.x) {
+    const int64_t k = e % g.ne, r = e / g.ne;
+    double* h = hp + r * ext_total;
+    const int s = g.src[k];
+    h[g.par_off + k] = s >= 0 ? h[g.a_off + s] : h[g.b_off + (-s - 1)];
+  }
+}
+
+// u3 := z (the particular part of the interface values), before u3 += S u_parent.
+template <typename R>
+__global__ void k_z_to_u3(const BodyDesc* __restrict__ d, int chunks, const R* __restrict__ zlev,
+                          double* __restrict__ u3, int64_t u3_total, int nrhs) {
+  const BodyDesc g = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int64_t n = (int64_t)g.m * nrhs;
+  const R* z = zlev + g.z_off * nrhs;
+  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)chunks * blockDim.x) {
+    const int64_t i = e % g.m, r = e / g.m;
+    u3[r * u3_total + g.u3_off + i] = (double)z[i + r * g.m];
+  }
+}
+
+static int body_chunks(int64_t work) { return (int)std::min<int64_t>((work + 255) / 256, 64); }
+
+template <typename R>
+void merge_rhs(const BodyDesc* d, int nd, int max_m, const double* hp, int64_t ext_total,
+               int nrhs, R* zlev, cudaStream_t st) {
+  if (nd <= 0) return;
+  int ch = body_chunks((int64_t)max_m * nrhs);
+  prof::Scope sc("merge_rhs", st, 0.0, (double)nd * max_m * nrhs * (16.0 + sizeof(R)));
+  k_merge_rhs<R><<<(unsigned)((int64_t)nd * ch), 256, 0, st>>>(d, ch, hp, ext_total, nrhs, zlev);
+}
+
+void merge_hpar(const BodyDesc* d, int nd, int max_ne, double* hp, int64_t ext_total, int nrhs,
+                cudaStream_t st) {
+  if (nd <= 0) return;
+  int ch = body_chunks((int64_t)max_ne * nrhs);
+  prof::Scope sc("merge_hpar", st, 0.0, (double)nd * max_ne * nrhs * 16.0);
+  k_merge_hpar<<<(unsigned)((int64_t)nd * ch), 256, 0, st>>>(d, ch, hp, ext_total, nrhs);
+}
+
+template <typename R>
+void z_to_u3(const BodyDesc* d, int nd, int max_m, const R* zlev, double* u3, int64_t u3_total,
+             int nrhs, cudaStream_t st) {
+  if (nd <= 0) return;
+  int ch = body_chunks((int64_t)max_m * nrhs);
+  prof::Scope sc("z_to_u3", st, 0.0, (double)nd * max_m * nrhs * (8.0 + sizeof(R)));
+  k_z_to_u3<R><<<(unsigned)((int64_t)nd * ch), 256, 0, st>>>(d, ch, zlev, u3, u3_total, nrhs);
 }
 
 // ----------------------------------------------------------- downward pass
@@ -82,8 +167,10 @@ void solve_root_scatter(const double* f, const int* root_from_f, int nbnd, int n
                         double* uext, int64_t root_off, int64_t ext_total, cudaStream_t st) {
   int64_t n = (int64_t)nbnd * nrhs;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  if (blocks > 0)
+  if (blocks > 0) {
+    prof::Scope sc("root_scatter", st, 0.0, 2.0 * n * 8.0);
     k_root_scatter<<<blocks, 256, 0, st>>>(f, root_from_f, nbnd, nrhs, uext, root_off, ext_total);
+  }
 }
 
 // children's exterior values from the parent's and u3 = S u_parent
@@ -116,15 +203,20 @@ void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, c
   if (ndesc <= 0) return;
   int64_t work = (int64_t)max_n * nrhs;
   int chunks = (int)std::min<int64_t>((work + 255) / 256, 64);
+  prof::Scope sc("child_scatter", st, 0.0, 2.0 * (double)ndesc * max_n * nrhs * 8.0);
   k_child_scatter<<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(
       d_desc, chunks, u3, u3_total, uext, ext_total, nrhs);
 }
 
-template void merge_gather<double, double>(const MergeDesc<double, double>*, int, int64_t,
-                                           cudaStream_t);
-template void merge_gather<float, float>(const MergeDesc<float, float>*, int, int64_t,
-                                         cudaStream_t);
-template void merge_gather<float, double>(const MergeDesc<float, double>*, int, int64_t,
-                                          cudaStream_t);
+template void merge_gather<double>(const MergeDesc<double>*, int, int64_t, cudaStream_t, double);
+template void merge_gather<float>(const MergeDesc<float>*, int, int64_t, cudaStream_t, double);
+template void merge_rhs<double>(const BodyDesc*, int, int, const double*, int64_t, int, double*,
+                                cudaStream_t);
+template void merge_rhs<float>(const BodyDesc*, int, int, const double*, int64_t, int, float*,
+                               cudaStream_t);
+template void z_to_u3<double>(const BodyDesc*, int, int, const double*, double*, int64_t, int,
+                              cudaStream_t);
+template void z_to_u3<float>(const BodyDesc*, int, int, const float*, double*, int64_t, int,
+                             cudaStream_t);
 
 }  // namespace hps

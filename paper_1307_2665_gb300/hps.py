@@ -29,13 +29,16 @@ COEFF_NAMES = ("c11", "c12", "c22", "c1", "c2", "c")
 
 EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes", "hps_solve",
-           "hps_solve_ex", "hps_query", "hps_free", "hps_status_string")
+           "hps_solve_ex", "hps_query", "hps_free", "hps_status_string", "hps_kernel_launches",
+           "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error")
 
 
 class HpsError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__(f"{where}: {lib().hps_status_string(status).decode()} ({status})")
+        extra = lib().hps_last_error().decode() if status == HPS_EDEVICE else ""
+        super().__init__(f"{where}: {lib().hps_status_string(status).decode()} ({status})"
+                         + (f" [{extra}]" if extra else ""))
 
 
 class Domain(ctypes.Structure):
@@ -48,6 +51,11 @@ class Options(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("form_root_dtn", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -80,6 +88,16 @@ def lib():
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64),
                             ctypes.POINTER(ctypes.c_int64)]
     L.hps_free.argtypes = [vp]
+    L.hps_kernel_launches.argtypes = []
+    L.hps_kernel_launches.restype = ctypes.c_int64
+    L.hps_profile_enable.argtypes = [ctypes.c_int]
+    L.hps_profile_enable.restype = None
+    L.hps_profile_reset.argtypes = []
+    L.hps_profile_reset.restype = None
+    L.hps_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int]
+    L.hps_profile_read.restype = ctypes.c_int
+    L.hps_last_error.argtypes = []
+    L.hps_last_error.restype = ctypes.c_char_p
     L.hps_status_string.argtypes = [ctypes.c_int]
     L.hps_status_string.restype = ctypes.c_char_p
     for name in ("hps_cheb_nodes", "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes",
@@ -203,6 +221,7 @@ def hps_solve(h: Handle, f, u=None, device_ptrs=None, info=None, check=True):
         u = np.empty((nrhs, h.nx * h.ny, h.p, h.p))
     inf = SolveInfo() if info is None else info
     st = lib().hps_solve_ex(h.ptr, _ptr(f), nrhs, _ptr(u), 1 if dev else 0, ctypes.byref(inf))
+    inf.status = st
     if st != HPS_OK and check:
         raise HpsError(st, "hps_solve")
     return u
@@ -221,3 +240,24 @@ def hps_query(h: Handle):
 
 def hps_free(h: Handle):
     h.close()
+
+
+def hps_kernel_launches():
+    return int(lib().hps_kernel_launches())
+
+
+def hps_profile_enable(on=True):
+    lib().hps_profile_enable(1 if on else 0)
+
+
+def hps_profile_reset():
+    lib().hps_profile_reset()
+
+
+def hps_profile_read(max_out=64):
+    """Per-kernel launch statistics since the last reset (synchronises the device)."""
+    arr = (KernelStat * max_out)()
+    n = lib().hps_profile_read(arr, max_out)
+    return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms,
+                                   "flops": arr[i].flops, "bytes": arr[i].bytes}
+            for i in range(min(n, max_out))}

@@ -63,7 +63,7 @@ def test_default_options_and_status_strings():
 
 @pytest.mark.parametrize("args", [
     dict(nx=0, ny=2, p=16, q=14), dict(nx=2, ny=2, p=2, q=1), dict(nx=2, ny=2, p=8, q=9),
-    dict(nx=2, ny=2, p=8, q=0), dict(nx=2, ny=-1, p=8, q=4)])
+    dict(nx=2, ny=2, p=8, q=0), dict(nx=2, ny=-1, p=8, q=4), dict(nx=2, ny=2, p=8, q=8)])
 def test_build_rejects_bad_sizes_before_device_work(args):
     """Validation happens before any device work, so it runs without a GPU."""
     st = hps.hps_build((0, 1, 0, 1), args["nx"], args["ny"], args["p"], args["q"], {}, check=False)

@@ -1,0 +1,89 @@
+"""Mixed precision with iterative refinement (FP32 leaves and lower merges,
+FP64 top merges, FP64 residual of the global collocation system) against the
+FP64 oracle.  Tolerance: relative max error <= 1e-10 after refinement."""
+import numpy as np
+import pytest
+
+from oracle import hps_oracle as O
+from paper_1307_2665_gb300 import hps
+from paper_1307_2665_gb300 import inputs as I
+from paper_1307_2665_gb300.build import build
+
+UNIT = (0.0, 1.0, 0.0, 1.0)
+SKEW = (-0.3, 0.9, 0.1, 1.7)
+TOL = 1e-10
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def varcoef(x, y):
+    return {"c11": 1 + 0.3 * np.sin(x + 2 * y), "c12": 0.2 * np.cos(3 * x - y),
+            "c22": 1.2 + 0.1 * x * y, "c1": 5 * np.cos(x), "c2": -4 * np.sin(2 * y),
+            "c": 7 * np.exp(x * y)}
+
+
+def setup(dom, nx, ny, p, q, fn, seeds=(0, 1)):
+    xy = hps.hps_cheb_nodes(dom, nx, ny, p)
+    co = {k: (None if v is None else np.ascontiguousarray(v, dtype=np.float64))
+          for k, v in fn(xy[..., 0], xy[..., 1]).items()}
+    bxy = hps.hps_boundary_nodes_grid(dom, nx, ny, q)
+    f = np.ascontiguousarray(np.stack([I.exp_sin(bxy[:, 0], bxy[:, 1])] +
+                                      [I.fourier_boundary(s, bxy[:, 0], bxy[:, 1], dom) for s in seeds]))
+    return co, f
+
+
+def run(dom, nx, ny, p, q, co, f, **kw):
+    h = hps.hps_build(dom, nx, ny, p, q, co, precision=hps.HPS_MIXED, **kw)
+    info = hps.SolveInfo()
+    u = hps.hps_solve(h, f, info=info, check=False)
+    h.close()
+    return u, info
+
+
+@pytest.mark.parametrize("dom,nx,ny,p,q,fn", [
+    (UNIT, 1, 1, 16, 14, I.laplace), (UNIT, 8, 8, 16, 14, I.laplace),
+    (SKEW, 5, 3, 9, 8, varcoef), (SKEW, 3, 5, 12, 10, varcoef), (UNIT, 1, 7, 10, 8, varcoef),
+    (UNIT, 16, 16, 16, 14, I.convection_diffusion), (UNIT, 2, 2, 24, 22, varcoef)])
+def test_mixed_matches_oracle(dom, nx, ny, p, q, fn):
+    co, f = setup(dom, nx, ny, p, q, fn)
+    u, info = run(dom, nx, ny, p, q, co, f)
+    assert info.status == hps.HPS_OK and 1 <= info.iterations <= 10
+    assert info.last_update <= 1e-11
+    sol = O.solve_condensed(O.make_problem(dom, nx, ny, p, q, fn), f.T)
+    err = np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w))
+    assert err < TOL, err
+
+
+def test_all_float_merges_still_converge():
+    """fp64_top_levels = 0: every merge in FP32; refinement still reaches the
+    FP64 solution on a benign problem."""
+    co, f = setup(UNIT, 8, 8, 12, 10, I.convection_diffusion)
+    u, info = run(UNIT, 8, 8, 12, 10, co, f, fp64_top_levels=0)
+    assert info.status == hps.HPS_OK
+    h = hps.hps_build(UNIT, 8, 8, 12, 10, co)
+    u64 = hps.hps_solve(h, f)
+    h.close()
+    assert np.max(np.abs(u - u64)) / np.max(np.abs(u64)) < TOL
+
+
+def test_oscillatory_helmholtz_with_stated_tolerance():
+    """-Lap u - 40^2 (1 - 0.5 bump) u = 0 on 16 x 16 leaves: the FP64 residual
+    resolves about 1e-10 here, so the stated refinement tolerance is 1e-9."""
+    fn = lambda x, y: I.gaussian_bump_helmholtz(x, y, 40.0)
+    co, f = setup(UNIT, 16, 16, 16, 14, fn)
+    u, info = run(UNIT, 16, 16, 16, 14, co, f, refine_tol=1e-9)
+    assert info.status == hps.HPS_OK
+    sol = O.solve_condensed(O.make_problem(UNIT, 16, 16, 16, 14, fn), f.T)
+    assert np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w)) < 1e-9
+
+
+def test_not_converged_is_reported():
+    co, f = setup(UNIT, 4, 4, 12, 10, varcoef)
+    u, info = run(UNIT, 4, 4, 12, 10, co, f, max_refine=1, refine_tol=1e-15)
+    assert info.status == hps.HPS_ENOTCONVERGED and info.iterations == 1
+    assert np.all(np.isfinite(u))

@@ -352,6 +352,24 @@ def test_condensed_equals_global_with_loads():
     assert np.max(np.abs(a.w - b.w)) < 1e-11 * np.max(np.abs(a.w))
 
 
+# ------------------------------------------------------- p = q singularity
+@pytest.mark.parametrize("nx,ny,p,q", [(3, 2, 6, 6), (3, 3, 6, 6), (2, 2, 7, 7), (4, 1, 6, 6),
+                                       (3, 2, 6, 5), (3, 3, 7, 5)])
+def test_nullity_equals_interior_vertices_when_p_equals_q(nx, ny, p, q):
+    """With q = p the Step-1 side map is a bijection, so the Lagrange basis
+    polynomial of a side's corner point changes only that corner value, and the
+    averaged corner rule leaves the combination (+a, +a, -a, -a) of the four
+    edges at an interior vertex invisible to every equation: the nullity of the
+    composite system is exactly the number of interior vertices.  With q < p
+    the system is nonsingular.  A different corner rule (one side's value
+    instead of the mean) changes this count."""
+    prob = O.make_problem(UNIT, nx, ny, p, q, I.laplace)
+    _, A, _ = O.solve_global(prob, np.ones(len(O.boundary_points(prob))), dense=True)
+    s = np.linalg.svd(A.toarray(), compute_uv=False)
+    nullity = int(np.sum(s < 1e-10 * s[0]))
+    assert nullity == ((nx - 1) * (ny - 1) if p == q else 0)
+
+
 # ---------------------------------------------------------------- residual
 def test_residual_zero_at_solution_and_linear():
     """The matrix-free residual vanishes at the solution and equals b - A x of
