@@ -67,7 +67,7 @@ typedef struct {
 typedef struct {
   int precision;          /* HPS_FP64 or HPS_MIXED */
   double refine_tol;      /* mixed mode: stop when max|delta| <= tol * max|u| (default 1e-11) */
-  int max_refine;         /* mixed mode: iteration cap (default 10) */
+  int max_refine;         /* mixed mode: iteration cap (default 10; 0: low-precision solve only) */
   int fp64_top_levels;    /* mixed mode: merge levels below the root kept in FP64 (default 2) */
   int device_ptrs;        /* 1: coefficient / f / u pointers are device pointers */
   void* stream;           /* cudaStream_t to run on; NULL: the library's own stream */

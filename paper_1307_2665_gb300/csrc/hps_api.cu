@@ -161,12 +161,12 @@ struct LevelOps {
   std::vector<int> boxes;
   int max_m = 0, max_ne = 0, max_nanb = 0;
   int64_t sum_m = 0;              // rows of the height's z buffer
-  std::unique_ptr<PoolBuf> S, Aw, piv, Cw;  // S kept always; Aw / piv / Cw kept in mixed mode
+  std::unique_ptr<PoolBuf> S, Cw;  // [S | W (mixed)] per merge; Cw kept in mixed mode
   std::vector<int64_t> s_off, aw_off, cw_off, piv_off, z_off;
   std::vector<int> hm, hne;       // host copies of m and ne (launch accounting)
   SolveScatterDesc* scatter = nullptr;  // device descriptors (the handle's stager)
   BodyDesc* body = nullptr;
-  LevelOps() : S(new PoolBuf()), Aw(new PoolBuf()), piv(new PoolBuf()), Cw(new PoolBuf()) {}
+  LevelOps() : S(new PoolBuf()), Cw(new PoolBuf()) {}
 };
 
 }  // namespace
@@ -185,20 +185,21 @@ struct hps_handle_s {
   std::vector<int64_t> src_off, cma_off, cmb_off;
   PoolBuf coef;                    // FP64 coefficient copy (mixed mode: the residual)
   const double* coefp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  PoolBuf Y, Aii, leaf_piv;        // Aii / leaf_piv kept in mixed mode
+  PoolBuf Y;                       // per leaf [Y | A_ii^{-1} (mixed mode)], stride ys
+  int64_t ys = 0;
   std::vector<LevelOps> levels;    // index = height (0 unused)
   std::vector<int64_t> u3_off;
   int64_t u3_total = 0;
   Stager keep;                     // descriptors that live as long as the handle
   // solve workspace and descriptors, cached for one nrhs
   int cache_nrhs = 0;
-  PoolBuf uext, u3, hpool, zleaf, fstage, ustage, maxabs;
-  std::vector<std::unique_ptr<PoolBuf>> zlev;
+  PoolBuf uext, u3, hpool, rleaf, zleaf, fstage, ustage, maxabs, split_ws;
+  std::vector<std::unique_ptr<PoolBuf>> rlev, zlev;
   Stager solve_st;
   std::vector<void*> gemm_down;    // per height: GemmDesc array (typed by level)
   std::vector<void*> gemm_hpar;    // per height (mixed)
-  std::vector<void*> lu_merge;     // per height (mixed, solve-only)
-  void* lu_leaf = nullptr;         // (mixed, solve-only)
+  std::vector<void*> gemm_w;       // per height (mixed): z = W rhs
+  void* gemm_leaf = nullptr;       // (mixed): z = A_ii^{-1} r
   std::vector<double> down_flops1, down_bytes;
   unsigned long long* h_maxabs = nullptr;  // pinned
   ~hps_handle_s() {
@@ -233,32 +234,32 @@ void build_leaves(hps_handle_s& H, Stager& stg, std::vector<TRef>& Tref, PoolBuf
   const Plan& pl = H.plan;
   cudaStream_t st = H.stream;
   const int p = pl.p, q = pl.q, ni = H.ni, nq = H.nq, nl = H.nl;
-  H.Y.alloc((size_t)nl * ni * nq * sizeof(R), st);
-  PoolBuf aii_tmp, piv_tmp;
-  PoolBuf& Aii = H.mixed ? H.Aii : aii_tmp;
-  PoolBuf& piv = H.mixed ? H.leaf_piv : piv_tmp;
+  // mixed mode also solves for A_ii^{-1} (identity columns after -A_ie L1)
+  const int nrhs_leaf = nq + (H.mixed ? ni : 0);
+  H.ys = (int64_t)ni * nrhs_leaf;
+  H.Y.alloc((size_t)nl * H.ys * sizeof(R), st);
+  PoolBuf Aii, piv;
   Aii.alloc((size_t)nl * ni * ni * sizeof(R), st);
   piv.alloc((size_t)nl * ni * sizeof(int), st);
   leaf_assemble<R>(H.coefp, nl, p, q, H.hx, H.hy, H.dD.as<double>(), H.dPg2c.as<double>(),
-                   Aii.as<R>(), H.Y.as<R>(), st);
+                   Aii.as<R>(), H.Y.as<R>(), H.ys, H.mixed ? 1 : 0, st);
   ck(cudaGetLastError());
   std::vector<LuDesc<R>> ld(nl);
   for (int l = 0; l < nl; ++l) {
     ld[l].A = Aii.as<R>() + (size_t)l * ni * ni;
     ld[l].ipiv = piv.as<int>() + (size_t)l * ni;
-    ld[l].B = H.Y.as<R>() + (size_t)l * ni * nq;
+    ld[l].B = H.Y.as<R>() + (size_t)l * H.ys;
     ld[l].m = ni;
     ld[l].lda = ni;
-    ld[l].nrhs = nq;
+    ld[l].nrhs = nrhs_leaf;
     ld[l].ldb = ni;
     ld[l].box = pl.leaf_box[l];
   }
   LuDesc<R>* dl = stg.push(ld, st);
-  lu_solve_batched<R>(dl, nl, ni, nq, H.mixed ? kLuFactorKeep : kLuFactor, H.status.as<int>(), st,
-                      nullptr, nullptr);
+  lu_solve_batched<R>(dl, nl, ni, nrhs_leaf, kLuFactor, H.status.as<int>(), st, nullptr, nullptr);
   ck(cudaGetLastError());
   T0.alloc((size_t)nl * nq * nq * sizeof(R), st);
-  leaf_dtn<R>(H.Y.as<R>(), nl, p, q, H.hx, H.hy, H.dD.as<double>(), H.dPg2c.as<double>(),
+  leaf_dtn<R>(H.Y.as<R>(), H.ys, nl, p, q, H.hx, H.hy, H.dD.as<double>(), H.dPg2c.as<double>(),
               H.dPc2g.as<double>(), T0.as<R>(), st);
   ck(cudaGetLastError());
   for (int l = 0; l < nl; ++l) {
@@ -284,19 +285,20 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
     L.aw_off[i] = aw_tot;
     L.cw_off[i] = cw_tot;
     L.piv_off[i] = piv_tot;
-    s_tot += (int64_t)sh.m * sh.ne;
+    s_tot += (int64_t)sh.m * (sh.ne + (H.mixed ? sh.m : 0));
     aw_tot += (int64_t)sh.m * sh.m;
     cw_tot += (int64_t)sh.ne * sh.m;
     tp_tot += tp ? (int64_t)sh.ne * sh.ne : 0;
     piv_tot += sh.m;
+    // gather work: T33 difference, S block, [T13; T23], diag(T11, T22) and, in
+    // mixed mode, the identity block that turns into W
     max_work = std::max<int64_t>(max_work, (int64_t)sh.m * sh.m + 2LL * sh.m * sh.ne +
-                                               (tp ? (int64_t)sh.ne * sh.ne : 0));
+                                               (tp ? (int64_t)sh.ne * sh.ne : 0) +
+                                               (H.mixed ? (int64_t)sh.m * sh.m : 0));
   }
   L.S->alloc((size_t)s_tot * sizeof(R), st);
-  PoolBuf aw_tmp, cw_tmp, piv_tmp;
-  PoolBuf& Aw = H.mixed ? *L.Aw : aw_tmp;
+  PoolBuf Aw, piv, cw_tmp;
   PoolBuf& Cw = H.mixed ? *L.Cw : cw_tmp;
-  PoolBuf& piv = H.mixed ? *L.piv : piv_tmp;
   Aw.alloc((size_t)aw_tot * sizeof(R), st);
   Cw.alloc((size_t)cw_tot * sizeof(R), st);
   piv.alloc((size_t)piv_tot * sizeof(int), st);
@@ -320,6 +322,7 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
     g.S = L.S->as<R>() + L.s_off[i];
     g.Cw = Cw.as<R>() + L.cw_off[i];
     g.Tp = tp ? Tout.as<R>() + ot : nullptr;
+    g.W = H.mixed ? g.S + (int64_t)sh.m * sh.ne : nullptr;
     g.src = H.maps.as<int>() + H.src_off[B.shape];
     g.na = sh.na;
     g.nb = sh.nb;
@@ -332,7 +335,7 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
     lu[i].B = g.S;
     lu[i].m = sh.m;
     lu[i].lda = sh.m;
-    lu[i].nrhs = sh.ne;
+    lu[i].nrhs = sh.ne + (H.mixed ? sh.m : 0);
     lu[i].ldb = sh.m;
     lu[i].box = b;
     gather_bytes += (sizeof(R) + 8.0) *
@@ -360,8 +363,10 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
   LuDesc<R>* dlu = stg.push(lu, st);
   merge_gather<R>(dmd, nm, max_work, st, gather_bytes);
   ck(cudaGetLastError());
-  lu_solve_batched<R>(dlu, nm, L.max_m, L.max_ne, H.mixed ? kLuFactorKeep : kLuFactor,
-                      H.status.as<int>(), st, L.hm.data(), L.hne.data());
+  std::vector<int> hn(nm);
+  for (int i = 0; i < nm; ++i) hn[i] = L.hne[i] + (H.mixed ? L.hm[i] : 0);
+  lu_solve_batched<R>(dlu, nm, L.max_m, L.max_ne + (H.mixed ? L.max_m : 0), kLuFactor,
+                      H.status.as<int>(), st, L.hm.data(), hn.data());
   ck(cudaGetLastError());
   if (!gm.empty()) {
     GemmDesc<R>* dg = stg.push(gm, st);
@@ -579,22 +584,24 @@ void push_body(hps_handle_s& H, int h, int nrhs) {
   const Plan& pl = H.plan;
   LevelOps& L = H.levels[h];
   std::vector<GemmDesc<R, R, double>> gh;
-  std::vector<LuDesc<R>> lu;
+  std::vector<GemmDesc<R>> gw;
   R* z = H.zlev[h]->as<R>();
+  R* r = H.rlev[h]->as<R>();
   for (size_t i = 0; i < L.boxes.size(); ++i) {
     const int b = L.boxes[i];
     const MergeShape& sh = pl.shapes[pl.boxes[b].shape];
-    LuDesc<R> d;
-    d.A = L.Aw->as<R>() + L.aw_off[i];
-    d.ipiv = L.piv->as<int>() + L.piv_off[i];
-    d.B = z + L.z_off[i] * nrhs;
-    d.m = sh.m;
-    d.lda = sh.m;
-    d.nrhs = nrhs;
-    d.ldb = sh.m;
-    d.box = b;
-    lu.push_back(d);
-    GemmDesc<R, R, double> g;
+    GemmDesc<R> w;  // z = W (h3^b - h3^a), W = (T33^a - T33^b)^{-1}
+    w.A = L.S->as<R>() + L.s_off[i] + (int64_t)sh.m * sh.ne;
+    w.B = r + L.z_off[i] * nrhs;
+    w.C = z + L.z_off[i] * nrhs;
+    w.M = sh.m;
+    w.N = nrhs;
+    w.K = sh.m;
+    w.lda = sh.m;
+    w.ldb = sh.m;
+    w.ldc = sh.m;
+    gw.push_back(w);
+    GemmDesc<R, R, double> g;  // h^tau += [T13^a; T23^b] z
     g.A = L.Cw->as<R>() + L.cw_off[i];
     g.B = z + L.z_off[i] * nrhs;
     g.C = H.hpool.as<double>() + pl.boxes[b].ext_off;
@@ -606,8 +613,26 @@ void push_body(hps_handle_s& H, int h, int nrhs) {
     g.ldc = (int)pl.ext_total;
     gh.push_back(g);
   }
-  H.lu_merge[h] = H.solve_st.push(lu, H.stream);
+  H.gemm_w[h] = H.solve_st.push(gw, H.stream);
   H.gemm_hpar[h] = H.solve_st.push(gh, H.stream);
+}
+
+template <typename R>
+void push_leaf_inverse(hps_handle_s& H, int nrhs) {
+  std::vector<GemmDesc<R>> g(H.nl);
+  const int ni = H.ni;
+  for (int l = 0; l < H.nl; ++l) {  // z_l = A_ii^{-1} r_l
+    g[l].A = H.Y.as<R>() + (size_t)l * H.ys + (size_t)ni * H.nq;
+    g[l].B = H.rleaf.as<R>() + (size_t)l * ni * nrhs;
+    g[l].C = H.zleaf.as<R>() + (size_t)l * ni * nrhs;
+    g[l].M = ni;
+    g[l].N = nrhs;
+    g[l].K = ni;
+    g[l].lda = ni;
+    g[l].ldb = ni;
+    g[l].ldc = ni;
+  }
+  H.gemm_leaf = H.solve_st.push(g, H.stream);
 }
 
 void prepare_solve(hps_handle_s& H, int nrhs) {
@@ -617,47 +642,37 @@ void prepare_solve(hps_handle_s& H, int nrhs) {
   H.cache_nrhs = 0;
   H.uext.alloc((size_t)nrhs * pl.ext_total * sizeof(double), st);
   H.u3.alloc((size_t)nrhs * std::max<int64_t>(H.u3_total, 1) * sizeof(double), st);
+  H.split_ws.alloc((size_t)64 << 20, st);
   H.gemm_down.assign(pl.height + 1, nullptr);
   H.gemm_hpar.assign(pl.height + 1, nullptr);
-  H.lu_merge.assign(pl.height + 1, nullptr);
+  H.gemm_w.assign(pl.height + 1, nullptr);
   H.down_flops1.assign(pl.height + 1, 0.0);
   H.down_bytes.assign(pl.height + 1, 0.0);
-  size_t bytes = 4 * 256 * (pl.height + 2) + stage_bytes<LuDesc<double>>(H.nl);
-  for (int h = 1; h <= pl.height; ++h)
-    bytes += 2 * stage_bytes<GemmDesc<double>>(H.levels[h].boxes.size()) +
-             stage_bytes<LuDesc<double>>(H.levels[h].boxes.size());
+  size_t bytes = 4 * 256 * (pl.height + 2) + stage_bytes<GemmDesc<double>>(H.nl);
+  for (int h = 1; h <= pl.height; ++h) bytes += 3 * stage_bytes<GemmDesc<double>>(H.levels[h].boxes.size());
   H.solve_st.begin(bytes, st);
   if (H.mixed) {
     H.hpool.alloc((size_t)nrhs * pl.ext_total * sizeof(double), st);
     const size_t es = H.leaf_f64 ? 8 : 4;
+    H.rleaf.alloc((size_t)H.nl * H.ni * nrhs * es, st);
     H.zleaf.alloc((size_t)H.nl * H.ni * nrhs * es, st);
+    H.rlev.clear();
     H.zlev.clear();
     for (int h = 0; h <= pl.height; ++h) {
+      H.rlev.emplace_back(new PoolBuf());
       H.zlev.emplace_back(new PoolBuf());
-      if (h >= 1)
-        H.zlev[h]->alloc((size_t)H.levels[h].sum_m * nrhs * (H.levels[h].f64 ? 8 : 4), st);
+      if (h >= 1) {
+        const size_t n = (size_t)H.levels[h].sum_m * nrhs * (H.levels[h].f64 ? 8 : 4);
+        H.rlev[h]->alloc(n, st);
+        H.zlev[h]->alloc(n, st);
+      }
     }
     H.maxabs.alloc(2 * sizeof(unsigned long long), st);
     if (!H.h_maxabs) ck(cudaMallocHost(&H.h_maxabs, 2 * sizeof(unsigned long long)));
-    auto push_leaf = [&](auto tag) {
-      using R = decltype(tag);
-      std::vector<LuDesc<R>> ld(H.nl);
-      for (int l = 0; l < H.nl; ++l) {
-        ld[l].A = H.Aii.as<R>() + (size_t)l * H.ni * H.ni;
-        ld[l].ipiv = H.leaf_piv.as<int>() + (size_t)l * H.ni;
-        ld[l].B = H.zleaf.as<R>() + (size_t)l * H.ni * nrhs;
-        ld[l].m = H.ni;
-        ld[l].lda = H.ni;
-        ld[l].nrhs = nrhs;
-        ld[l].ldb = H.ni;
-        ld[l].box = pl.leaf_box[l];
-      }
-      H.lu_leaf = H.solve_st.push(ld, st);
-    };
     if (H.leaf_f64)
-      push_leaf(double());
+      push_leaf_inverse<double>(H, nrhs);
     else
-      push_leaf(float());
+      push_leaf_inverse<float>(H, nrhs);
   }
   for (int h = 1; h <= pl.height; ++h) {
     if (H.levels[h].f64) {
@@ -671,6 +686,12 @@ void prepare_solve(hps_handle_s& H, int nrhs) {
   H.cache_nrhs = nrhs;
 }
 
+template <typename R>
+R* split_ws(hps_handle_s& H, size_t* elems) {
+  *elems = H.split_ws.bytes / sizeof(R);
+  return H.split_ws.as<R>();
+}
+
 // Downward pass (Algorithm 2) from the root exterior values already in uext;
 // with_z adds the body-load interface values z of each merge.
 template <typename R>
@@ -680,10 +701,12 @@ void down_level(hps_handle_s& H, int h, int nrhs, bool with_z) {
   const int nm = (int)L.boxes.size();
   if (with_z)
     z_to_u3<R>(L.body, nm, L.max_m, H.zlev[h]->as<R>(), H.u3.as<double>(), H.u3_total, nrhs, st);
+  size_t wse = 0;
+  R* ws = split_ws<R>(H, &wse);
   gemm_batched<R>(static_cast<GemmDesc<R, double, double>*>(H.gemm_down[h]), nm, L.max_m, nrhs,
                   R(1), with_z ? R(1) : R(0), st,
                   sizeof(R) == 8 ? "gemm_solve<f64>" : "gemm_solve<f32>",
-                  H.down_flops1[h] * nrhs, H.down_bytes[h]);
+                  H.down_flops1[h] * nrhs, H.down_bytes[h], L.max_ne, ws, wse);
   solve_child_scatter(L.scatter, nm, L.max_nanb, H.u3.as<double>(), H.u3_total,
                       H.uext.as<double>(), H.plan.ext_total, nrhs, st);
 }
@@ -700,22 +723,23 @@ void downward(hps_handle_s& H, int nrhs, bool with_z) {
 template <typename R>
 void leaf_out(hps_handle_s& H, int nrhs, double* u, bool correction) {
   const Plan& pl = H.plan;
-  leaf_post<R>(H.Y.as<R>(), H.uext.as<double>(), H.leaf_off.as<int64_t>(), pl.ext_total, H.nl,
+  leaf_post<R>(H.Y.as<R>(), H.ys, H.uext.as<double>(), H.leaf_off.as<int64_t>(), pl.ext_total, H.nl,
                pl.p, pl.q, nrhs, H.dPg2c.as<double>(), u, H.stream,
                correction ? H.zleaf.as<R>() : nullptr, correction ? 1 : 0,
                correction ? H.maxabs.as<unsigned long long>() : nullptr);
 }
 
-// Leaf part of one refinement step: r = -(A w)_i in FP64, z = A_ii^{-1} r with
-// the kept factors, and the leaves' flux offsets h = L4 L3 (w + [0; z]).
+// Leaf part of one refinement step: r = -(A w)_i in FP64, z = A_ii^{-1} r, and
+// the leaves' flux offsets h = L4 L3 (w + [0; z]).
 template <typename RL>
 void leaf_correction_rhs(hps_handle_s& H, int nrhs, const double* u) {
   const Plan& pl = H.plan;
   cudaStream_t st = H.stream;
   leaf_residual<RL>(H.coefp, H.nl, pl.p, H.hx, H.hy, H.dD.as<double>(), u, nrhs,
-                    H.zleaf.as<RL>(), st);
-  lu_solve_batched<RL>(static_cast<LuDesc<RL>*>(H.lu_leaf), H.nl, H.ni, nrhs, kLuSolveOnly,
-                       H.status.as<int>(), st, nullptr, nullptr);
+                    H.rleaf.as<RL>(), st);
+  gemm_batched<RL>(static_cast<GemmDesc<RL>*>(H.gemm_leaf), H.nl, H.ni, nrhs, RL(1), RL(0), st,
+                   sizeof(RL) == 8 ? "gemm_leafinv<f64>" : "gemm_leafinv<f32>",
+                   2.0 * H.nl * (double)H.ni * H.ni * nrhs, (double)H.nl * H.ni * H.ni * sizeof(RL));
   leaf_flux<RL>(u, H.zleaf.as<RL>(), H.nl, pl.p, pl.q, nrhs, H.hx, H.hy, H.dD.as<double>(),
                 H.dPc2g.as<double>(), H.leaf_off.as<int64_t>(), pl.ext_total,
                 H.hpool.as<double>(), st);
@@ -728,18 +752,23 @@ void up_level(hps_handle_s& H, int h, int nrhs) {
   cudaStream_t st = H.stream;
   const Plan& pl = H.plan;
   const int nm = (int)L.boxes.size();
+  size_t wse = 0;
+  R* ws = split_ws<R>(H, &wse);
   merge_rhs<R>(L.body, nm, L.max_m, H.hpool.as<double>(), pl.ext_total, nrhs,
-               H.zlev[h]->as<R>(), st);
-  std::vector<int> hn(nm, nrhs);
-  lu_solve_batched<R>(static_cast<LuDesc<R>*>(H.lu_merge[h]), nm, L.max_m, nrhs, kLuSolveOnly,
-                      H.status.as<int>(), st, L.hm.data(), hn.data());
+               H.rlev[h]->as<R>(), st);
+  double flw = 0, flc = 0;
+  for (int i = 0; i < nm; ++i) {
+    flw += 2.0 * L.hm[i] * (double)L.hm[i] * nrhs;
+    flc += 2.0 * L.hne[i] * (double)L.hm[i] * nrhs;
+  }
+  gemm_batched<R>(static_cast<GemmDesc<R>*>(H.gemm_w[h]), nm, L.max_m, nrhs, R(1), R(0), st,
+                  sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flw, 0.0, L.max_m, ws,
+                  wse);
   if (h < pl.height) {  // the root's flux offsets are not needed
     merge_hpar(L.body, nm, L.max_ne, H.hpool.as<double>(), pl.ext_total, nrhs, st);
-    double fl = 0;
-    for (int i = 0; i < nm; ++i) fl += 2.0 * L.hne[i] * (double)L.hm[i] * nrhs;
     gemm_batched<R>(static_cast<GemmDesc<R, R, double>*>(H.gemm_hpar[h]), nm, L.max_ne, nrhs,
-                    R(1), R(1), st, sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", fl,
-                    0.0);
+                    R(1), R(1), st, sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flc,
+                    0.0, L.max_m, ws, wse);
   }
 }
 
@@ -756,7 +785,7 @@ int solve_all(hps_handle_s& H, const double* f_dev, int nrhs, double* u_dev,
   else
     leaf_out<float>(H, nrhs, u_dev, false);
   ck(cudaGetLastError());
-  if (!H.mixed) return HPS_OK;
+  if (!H.mixed || H.opt.max_refine == 0) return HPS_OK;
   // ---- iterative refinement against the FP64 residual
   double last = 0.0;
   int it = 0;
@@ -849,7 +878,7 @@ int hps_build(hps_domain d, int nx, int ny, int p, int q, const double* c11, con
   if (opt_in) opt = *opt_in;
   if (opt.precision != HPS_FP64 && opt.precision != HPS_MIXED) return HPS_EINVAL;
   if (opt.precision == HPS_MIXED &&
-      (!(opt.refine_tol > 0) || opt.max_refine < 1 || opt.fp64_top_levels < 0))
+      (!(opt.refine_tol > 0) || opt.max_refine < 0 || opt.fp64_top_levels < 0))
     return HPS_EINVAL;
   g_last_error.clear();
   hps_handle_s* H = nullptr;
@@ -950,13 +979,13 @@ int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_
   if (nbnd) *nbnd = h->nbnd;
   if (device_bytes) {
     int64_t b = 0;
-    for (const PoolBuf* x : {&h->Y, &h->Aii, &h->leaf_piv, &h->coef, &h->maps, &h->uext, &h->u3,
-                             &h->hpool, &h->zleaf, &h->fstage, &h->ustage, &h->keep.dev,
+    for (const PoolBuf* x : {&h->Y, &h->coef, &h->maps, &h->uext, &h->u3, &h->hpool, &h->rleaf,
+                             &h->zleaf, &h->fstage, &h->ustage, &h->split_ws, &h->keep.dev,
                              &h->solve_st.dev})
       b += (int64_t)x->bytes;
-    for (const auto& L : h->levels)
-      b += (int64_t)(L.S->bytes + L.Aw->bytes + L.piv->bytes + L.Cw->bytes);
+    for (const auto& L : h->levels) b += (int64_t)(L.S->bytes + L.Cw->bytes);
     for (const auto& z : h->zlev) b += (int64_t)z->bytes;
+    for (const auto& r : h->rlev) b += (int64_t)r->bytes;
     *device_bytes = b;
   }
   return HPS_OK;

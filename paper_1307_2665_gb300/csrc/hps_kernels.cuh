@@ -43,6 +43,7 @@ struct MergeDesc {
   R* S;
   R* Cw;
   R* Tp;       // may be null (root DtN not formed)
+  R* W;        // may be null; else an m x m identity is written there (ld m)
   const int* src;
   int na, nb, m, ne, j3a, j3b;
 };
@@ -79,21 +80,30 @@ template <typename R>
 void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrhs, int mode,
                       int* d_status, cudaStream_t st, const int* h_m, const int* h_nrhs);
 // name / flops / bytes: launch accounting (algorithmic work of this launch).
+// ws / ws_elems (optional): scratch of element type R; when the launch would
+// occupy few SMs and K is long, the K range is split across CTAs, partial
+// products go to ws and a second kernel sums them in a fixed order (so results
+// do not depend on the split or on other launches).  max_K: largest K.
 template <typename R, typename TA, typename TB, typename TC>
 void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
-                  R beta, cudaStream_t st, const char* name, double flops, double bytes);
+                  R beta, cudaStream_t st, const char* name, double flops, double bytes,
+                  int max_K = 0, R* ws = nullptr, size_t ws_elems = 0);
 
 // ---- leaf kernels (hps_leaf.cu)
+// Y of leaf l starts at Y + l*ys (ni x 4q, ld ni); with_identity also writes
+// an ni x ni identity after it so that the leaf solve returns A_ii^{-1} as well.
 template <typename R>
 void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double hx, double hy,
-                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, cudaStream_t st);
+                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, int64_t ys,
+                   int with_identity, cudaStream_t st);
 template <typename R>
-void leaf_dtn(const R* Y, int nleaves, int p, int q, double hx, double hy, const double* d_D,
-              const double* d_Pg2c, const double* d_Pc2g, R* T, cudaStream_t st);
+void leaf_dtn(const R* Y, int64_t ys, int nleaves, int p, int q, double hx, double hy,
+              const double* d_D, const double* d_Pg2c, const double* d_Pc2g, R* T,
+              cudaStream_t st);
 template <typename R>
-void leaf_post(const R* Y, const double* uext, const int64_t* leaf_ext_off, int64_t ext_total,
-               int nleaves, int p, int q, int nrhs, const double* d_Pg2c, double* u,
-               cudaStream_t st, const R* z = nullptr, int accumulate = 0,
+void leaf_post(const R* Y, int64_t ys, const double* uext, const int64_t* leaf_ext_off,
+               int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
+               double* u, cudaStream_t st, const R* z = nullptr, int accumulate = 0,
                unsigned long long* maxabs = nullptr);
 template <typename R>
 void leaf_residual(const double* const* coef, int nl, int p, double hx, double hy,

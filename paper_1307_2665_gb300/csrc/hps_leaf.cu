@@ -44,7 +44,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q, double sx,
                                                        double sy, const double* __restrict__ gD,
                                                        const double* __restrict__ gPg2c,
-                                                       R* __restrict__ Aii, R* __restrict__ Y) {
+                                                       R* __restrict__ Aii, R* __restrict__ Y,
+                                                       int64_t ys, int with_identity) {
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
   double* D = sm;             // p x p
@@ -98,7 +99,10 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q
   // B = -A_ie L1 (ni x 4q).  For an interior row (a, b) only the boundary nodes
   // of row a / column b are reached by the pure x / pure y terms; the mixed term
   // reaches every node of a side, collapsed through G.
-  R* Yl = Y + (size_t)l * ni * nq;
+  R* Yl = Y + (size_t)l * ys;
+  if (with_identity)  // columns nq .. nq+ni-1: the identity, so the solve also returns A_ii^{-1}
+    for (int e = threadIdx.x; e < ni * ni; e += blockDim.x)
+      Yl[(size_t)ni * nq + e] = (e % ni == e / ni) ? R(1) : R(0);
   for (int e = threadIdx.x; e < ni * nq; e += blockDim.x) {
     const int ri = e % ni, gcol = e / ni;
     const int s = gcol / q, k = gcol % q;
@@ -120,7 +124,8 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q
 
 template <typename R>
 void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double hx, double hy,
-                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, cudaStream_t st) {
+                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, int64_t ys,
+                   int with_identity, cudaStream_t st) {
   if (nleaves <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
@@ -139,13 +144,14 @@ void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double 
                  (double)nleaves * (ni * ni * 8.0 + ni * 4.0 * q * 6.0),
                  (double)nleaves * ((ni * ni + ni * 4.0 * q) * sizeof(R) + ncoef * p * p * 8.0));
   k_leaf_assemble<R><<<nleaves, 256, smem, st>>>(cp, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, Aii,
-                                                 Y);
+                                                 Y, ys, with_identity);
 }
 
 // ------------------------------------------------------------------ leaf DtN
 // One CTA per leaf; the 4q columns of W are processed in chunks of CH.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int p, int q, double sx,
+__global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64_t ys, int p,
+                                                  int q, double sx,
                                                   double sy, const double* __restrict__ gD,
                                                   const double* __restrict__ gPg2c,
                                                   const double* __restrict__ gPc2g,
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int p
     Pg[e] = gPg2c[e];
     Pc[e] = gPc2g[e];
   }
-  const R* Yl = Y + (size_t)l * ni * nq;
+  const R* Yl = Y + (size_t)l * ys;
   R* Tl = T + (size_t)l * nq * nq;
   for (int g0 = 0; g0 < nq; g0 += CH) {
     const int nc = min(CH, nq - g0);
@@ -219,8 +225,9 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int p
 }
 
 template <typename R>
-void leaf_dtn(const R* Y, int nleaves, int p, int q, double hx, double hy, const double* d_D,
-              const double* d_Pg2c, const double* d_Pc2g, R* T, cudaStream_t st) {
+void leaf_dtn(const R* Y, int64_t ys, int nleaves, int p, int q, double hx, double hy,
+              const double* d_D, const double* d_Pg2c, const double* d_Pc2g, R* T,
+              cudaStream_t st) {
   if (nleaves <= 0) return;
   size_t smem = (size_t)(p * p + 2 * p * q + p * p * 8 + 4 * p * 8) * sizeof(double);
   static bool attr = false;
@@ -234,17 +241,19 @@ void leaf_dtn(const R* Y, int nleaves, int p, int q, double hx, double hy, const
   prof::Scope sc(tname<R>("leaf_dtn<f64>", "leaf_dtn<f32>"), st,
                  (double)nleaves * nq * (8.0 * p * p + 2.0 * nq * p),
                  (double)nleaves * (ni * nq + nq * nq) * sizeof(R));
-  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, d_Pc2g, T);
+  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, ys, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, d_Pc2g,
+                                            T);
 }
 
 // ------------------------------------------------------------ post-process
-// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 4.3), right-hand sides in
-// chunks of RC.  u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or
-// has it added (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior
-// values (ld ni).  maxabs (optional) receives max |w_full| (slot 0) and, after
+// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 4.3), computed in the
+// element type R of Y, right-hand sides in chunks of RC.
+// u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or has it added in
+// FP64 (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior values
+// (ld ni).  maxabs (optional) receives max |w_full| (slot 0) and, after
 // accumulation, max |u| (slot 1), as the bit patterns of non-negative doubles.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
+__global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int64_t ys,
                                                    const double* __restrict__ uext,
                                                    const int64_t* __restrict__ leaf_off,
                                                    int64_t ext_total, int nl, int p, int q,
@@ -253,14 +262,15 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
                                                    unsigned long long* maxabs,
                                                    double* __restrict__ u) {
   constexpr int RC = 16;
-  extern __shared__ __align__(16) double sm[];
+  extern __shared__ __align__(16) double smd[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
-  double* Pg = sm;           // p x q
-  double* ue = Pg + p * q;   // nq x RC
+  double* Pg = smd;                               // p x q
+  double* ued = Pg + p * q;                       // nq x RC, FP64 (boundary rows)
+  R* uer = reinterpret_cast<R*>(ued + nq * RC);   // nq x RC, element type of Y (interior rows)
   const int l = blockIdx.x;
   const int64_t off = leaf_off[l];
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
-  const R* Yl = Y + (size_t)l * ni * nq;
+  const R* Yl = Y + (size_t)l * ys;
   const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
   double mdw = 0.0, mu = 0.0;
   for (int r0 = 0; r0 < nrhs; r0 += RC) {
@@ -268,41 +278,50 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
     __syncthreads();
     for (int e = threadIdx.x; e < nq * RC; e += blockDim.x) {
       const int g = e % nq, rr = e / nq;
-      ue[g * RC + rr] = rr < nr ? uext[(size_t)(r0 + rr) * ext_total + off + g] : 0.0;
+      const double v = rr < nr ? uext[(size_t)(r0 + rr) * ext_total + off + g] : 0.0;
+      ued[g * RC + rr] = v;
+      uer[g * RC + rr] = (R)v;
     }
     __syncthreads();
     for (int node = threadIdx.x; node < pp; node += blockDim.x) {
       const int a = node / p, b = node % p;
-      double acc[RC];
-#pragma unroll
-      for (int rr = 0; rr < RC; ++rr) acc[rr] = 0.0;
+      double out[RC];
       if (a > 0 && a < p - 1 && b > 0 && b < p - 1) {
+        // interior: Y u_e (+ z) in the precision of Y
         const int ri = (a - 1) * pi + (b - 1);
-        for (int g = 0; g < nq; ++g) {
-          const double y = (double)Yl[ri + (size_t)g * ni];
+        R acc[RC];
 #pragma unroll
-          for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(y, ue[g * RC + rr], acc[rr]);
+        for (int rr = 0; rr < RC; ++rr) acc[rr] = R(0);
+        for (int g = 0; g < nq; ++g) {
+          const R y = Yl[ri + (size_t)g * ni];
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(y, uer[g * RC + rr], acc[rr]);
         }
         if (zl)
-          for (int rr = 0; rr < nr; ++rr) acc[rr] += (double)zl[ri + (size_t)(r0 + rr) * ni];
+          for (int rr = 0; rr < nr; ++rr) acc[rr] += zl[ri + (size_t)(r0 + rr) * ni];
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) out[rr] = (double)acc[rr];
       } else {
-        // boundary node: sides containing it, weights halved at corners
+        // boundary: L1 u_e in FP64 (the boundary values are defined by the Gauss
+        // values and must stay consistent between neighbouring leaves)
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) out[rr] = 0.0;
         const int sides[4][2] = {{0, b}, {2, b}, {1, a}, {3, a}};
         const bool on[4] = {a == 0, a == p - 1, b == p - 1, b == 0};
         for (int t = 0; t < 4; ++t) {
           if (!on[t]) continue;
-          const int s = sides[t][0], j = sides[t][1];
+          const int sd = sides[t][0], j = sides[t][1];
           const double w = (j == 0 || j == p - 1) ? 0.5 : 1.0;
           for (int k = 0; k < q; ++k) {
             const double c = w * Pg[j * q + k];
 #pragma unroll
-            for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(c, ue[(s * q + k) * RC + rr], acc[rr]);
+            for (int rr = 0; rr < RC; ++rr) out[rr] = fma(c, ued[(sd * q + k) * RC + rr], out[rr]);
           }
         }
       }
       for (int rr = 0; rr < nr; ++rr) {
         double* up = u + ((size_t)(r0 + rr) * nl + l) * pp + node;
-        double v = acc[rr];
+        double v = out[rr];
         mdw = fmax(mdw, fabs(v));
         if (accumulate) v += *up;
         mu = fmax(mu, fabs(v));
@@ -323,17 +342,18 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y,
 }
 
 template <typename R>
-void leaf_post(const R* Y, const double* uext, const int64_t* leaf_ext_off, int64_t ext_total,
-               int nleaves, int p, int q, int nrhs, const double* d_Pg2c, double* u,
-               cudaStream_t st, const R* z, int accumulate, unsigned long long* maxabs) {
+void leaf_post(const R* Y, int64_t ys, const double* uext, const int64_t* leaf_ext_off,
+               int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
+               double* u, cudaStream_t st, const R* z, int accumulate,
+               unsigned long long* maxabs) {
   if (nleaves <= 0 || nrhs <= 0) return;
-  size_t smem = (size_t)(p * q + 4 * q * 16) * sizeof(double);
+  size_t smem = (size_t)(p * q + 4 * q * 16) * sizeof(double) + (size_t)4 * q * 16 * sizeof(R);
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
   prof::Scope sc(tname<R>("leaf_post<f64>", "leaf_post<f32>"), st,
                  (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
                  (double)nleaves * (ni * nq * sizeof(R) +
                                     nrhs * (nq + (double)p * p * (accumulate ? 2 : 1)) * 8.0));
-  k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, uext, leaf_ext_off, ext_total, nleaves, p, q,
+  k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, ys, uext, leaf_ext_off, ext_total, nleaves, p, q,
                                              nrhs, d_Pg2c, z, accumulate, maxabs, u);
 }
 
@@ -367,6 +387,7 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int nl, int 
     D2[e] = s;
   }
   R* rl = rbuf + (size_t)l * ni * nrhs;
+  const bool has12 = cp.c[1] != nullptr, has2 = cp.c[4] != nullptr;
   for (int r = 0; r < nrhs; ++r) {
     __syncthreads();
     for (int e = threadIdx.x; e < pp; e += blockDim.x) W[e] = w[((size_t)r * nl + l) * pp + e];
@@ -384,9 +405,11 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int nl, int 
       for (int k = 0; k < p; ++k) {
         dxx = fma(D2[b * p + k], W[a * p + k], dxx);
         dyy = fma(D2[a * p + k], W[k * p + b], dyy);
-        dy = fma(D[a * p + k], W[k * p + b], dy);
-        dxy = fma(D[a * p + k], Wx[k * p + b], dxy);
       }
+      if (has2)
+        for (int k = 0; k < p; ++k) dy = fma(D[a * p + k], W[k * p + b], dy);
+      if (has12)
+        for (int k = 0; k < p; ++k) dxy = fma(D[a * p + k], Wx[k * p + b], dxy);
       dxx *= sx * sx;
       dyy *= sy * sy;
       dy *= sy;
@@ -491,11 +514,12 @@ void leaf_flux(const double* w, const R* z, int nl, int p, int q, int nrhs, doub
 
 #define HPS_INST_LEAF(R)                                                                        \
   template void leaf_assemble<R>(const double* const*, int, int, int, double, double,           \
-                                 const double*, const double*, R*, R*, cudaStream_t);           \
-  template void leaf_dtn<R>(const R*, int, int, int, double, double, const double*,             \
+                                 const double*, const double*, R*, R*, int64_t, int,            \
+                                 cudaStream_t);                                                 \
+  template void leaf_dtn<R>(const R*, int64_t, int, int, int, double, double, const double*,    \
                             const double*, const double*, R*, cudaStream_t);                    \
-  template void leaf_post<R>(const R*, const double*, const int64_t*, int64_t, int, int, int,   \
-                             int, const double*, double*, cudaStream_t, const R*, int,          \
+  template void leaf_post<R>(const R*, int64_t, const double*, const int64_t*, int64_t, int,    \
+                             int, int, int, const double*, double*, cudaStream_t, const R*, int, \
                              unsigned long long*);                                              \
   template void leaf_residual<R>(const double* const*, int, int, double, double, const double*, \
                                  const double*, int, R*, cudaStream_t);                         \

@@ -140,24 +140,86 @@ __global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<TA, TB, TC>* __r
           reinterpret_cast<R*>(smraw));
 }
 
+// Split-K: CTA (desc, tile, split) computes the partial product over its K
+// range into ws[(desc*splits + split)] (max_M x max_N blocks, ld max_M); the
+// reduction adds the partials in split order.
 template <typename R, class TL, typename TA, typename TB, typename TC>
-static void launch_gemm(const GemmDesc<TA, TB, TC>* d, int nd, int max_M, int max_N, R alpha,
-                        R beta, cudaStream_t st, const char* name, double flops, double bytes) {
+__global__ void __launch_bounds__(TL::NT) k_gemm_split(const GemmDesc<TA, TB, TC>* __restrict__ d,
+                                                       int tpm, int tpn, int splits, int kc,
+                                                       R* __restrict__ ws, int wsM, int wsN) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int per = tpm * tpn * splits;
+  const int di = blockIdx.x / per;
+  const GemmDesc<TA, TB, TC> g = d[di];
+  const int rem = blockIdx.x % per;
+  const int sp = rem / (tpm * tpn), tile = rem % (tpm * tpn);
+  const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
+  const int k0 = sp * kc;
+  if (m0 >= g.M || n0 >= g.N || k0 >= g.K) return;
+  const int kn = min(kc, g.K - k0);
+  R* wp = ws + ((size_t)di * splits + sp) * wsM * wsN;
+  TL::run(g.M, g.N, kn, R(1), g.A + (size_t)k0 * g.lda, g.lda, g.B + k0, g.ldb, R(0), wp, wsM, m0,
+          n0, reinterpret_cast<R*>(smraw));
+}
+
+template <typename R, typename TA, typename TB, typename TC>
+__global__ void k_gemm_split_reduce(const GemmDesc<TA, TB, TC>* __restrict__ d, int splits, int kc,
+                                    const R* __restrict__ ws, int wsM, int wsN, int chunks,
+                                    R alpha, R beta) {
+  const int di = blockIdx.x / chunks;
+  const GemmDesc<TA, TB, TC> g = d[di];
+  const int ns = min(splits, (g.K + kc - 1) / kc);
+  const int64_t n = (int64_t)g.M * g.N;
+  for (int64_t e = (int64_t)(blockIdx.x % chunks) * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)chunks * blockDim.x) {
+    const int i = (int)(e % g.M), j = (int)(e / g.M);
+    R acc = R(0);
+    for (int s = 0; s < ns; ++s) acc += ws[((size_t)di * splits + s) * wsM * wsN + i + (size_t)j * wsM];
+    TC* cp = g.C + i + (size_t)j * g.ldc;
+    if (beta == R(0))
+      *cp = (TC)(alpha * acc);
+    else
+      *cp = (TC)fma((TC)alpha, (TC)acc, (TC)beta * *cp);
+  }
+}
+
+template <typename R, class TL, typename TA, typename TB, typename TC>
+static void launch_gemm(const GemmDesc<TA, TB, TC>* d, int nd, int max_M, int max_N, int max_K,
+                        R alpha, R beta, cudaStream_t st, const char* name, double flops,
+                        double bytes, R* ws, size_t ws_elems) {
   int tpm = (max_M + TL::BM - 1) / TL::BM, tpn = (max_N + TL::BN - 1) / TL::BN;
   if (nd <= 0 || tpm <= 0 || tpn <= 0) return;
-  long long blocks = (long long)nd * tpm * tpn;
+  long long tiles = (long long)nd * tpm * tpn;
   prof::Scope sc(name, st, flops, bytes);
-  k_gemm<R, TL, TA, TB, TC><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
+  int splits = 1;
+  if (ws && tiles < 2 * 152 && max_K >= 512) {
+    splits = (int)std::min<long long>((2 * 152 + tiles - 1) / tiles, max_K / 128);
+    long long fit = (long long)(ws_elems / ((size_t)nd * max_M * max_N));
+    splits = (int)std::min<long long>(splits, fit);
+  }
+  if (splits < 2) {
+    k_gemm<R, TL, TA, TB, TC><<<(unsigned)tiles, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
+    return;
+  }
+  int kc = (max_K + splits - 1) / splits;
+  kc = ((kc + TL::BK - 1) / TL::BK) * TL::BK;
+  k_gemm_split<R, TL, TA, TB, TC><<<(unsigned)(tiles * splits), TL::NT, TL::SMEM, st>>>(
+      d, tpm, tpn, splits, kc, ws, max_M, max_N);
+  int chunks = (int)std::min<long long>(((long long)max_M * max_N + 255) / 256, 256);
+  k_gemm_split_reduce<R, TA, TB, TC><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(
+      d, splits, kc, ws, max_M, max_N, chunks, alpha, beta);
 }
 
 template <typename R, typename TA, typename TB, typename TC>
 void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
-                  R beta, cudaStream_t st, const char* name, double flops, double bytes) {
+                  R beta, cudaStream_t st, const char* name, double flops, double bytes,
+                  int max_K, R* ws, size_t ws_elems) {
   if (max_N <= 16)
-    launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st, name, flops,
-                                  bytes);
+    launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name,
+                                  flops, bytes, ws, ws_elems);
   else
-    launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, alpha, beta, st, name, flops, bytes);
+    launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name, flops,
+                              bytes, ws, ws_elems);
 }
 
 // ------------------------------------------------------------ LU: the panel
@@ -577,7 +639,8 @@ template void lu_solve_batched<float>(const LuDesc<float>*, int, int, int, int, 
                                       cudaStream_t, const int*, const int*);
 #define HPS_INST_GEMM(R, TA, TB, TC)                                                            \
   template void gemm_batched<R, TA, TB, TC>(const GemmDesc<TA, TB, TC>*, int, int, int, R, R,   \
-                                            cudaStream_t, const char*, double, double);
+                                            cudaStream_t, const char*, double, double, int, R*, \
+                                            size_t);
 HPS_INST_GEMM(double, double, double, double)
 HPS_INST_GEMM(float, float, float, float)
 HPS_INST_GEMM(float, float, double, double)

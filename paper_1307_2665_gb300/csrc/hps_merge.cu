@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<R>* __rest
   const int chunk = blockIdx.x % chunks;
   const int64_t m = g.m, ne = g.ne;
   const int64_t nA = m * m, nS = m * ne, nC = ne * m, nT = g.Tp ? ne * ne : 0;
-  const int64_t total = nA + nS + nC + nT;
+  const int64_t nW = g.W ? m * m : 0;
+  const int64_t total = nA + nS + nC + nT + nW;
   const int64_t beg = (int64_t)chunk * per_chunk;
   const int64_t end = min(total, beg + per_chunk);
   const int64_t na = g.na, nb = g.nb;
@@ -48,6 +49,9 @@ __global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<R>* __rest
       int s = g.src[k];
       g.Cw[x] = s >= 0 ? (R)tload(g.Ta, g.ta64, s + (g.j3a + i) * na)
                        : (R)tload(g.Tb, g.tb64, (int64_t)(-s - 1) + (g.j3b + i) * nb);
+    } else if (e >= nA + nS + nC + nT) {
+      int64_t x = e - nA - nS - nC - nT;
+      g.W[x] = (x % m == x / m) ? R(1) : R(0);
     } else {
       int64_t x = e - nA - nS - nC, k = x % ne, k2 = x / ne;
       int s = g.src[k], s2 = g.src[k2];
