@@ -1035,3 +1035,117 @@ const char* hps_status_string(int status) {
 }
 
 }  // extern "C"
+
+// ================================================ solve without allocation
+// Some callers cannot allocate device memory when they solve: code that runs
+// under a fixed memory budget reserved up front (a serving process that must
+// not grow), code that must not synchronise the device or touch the allocator
+// while other work is in flight, or embeddings whose allocator is not
+// reachable from the calling thread.  hps_solve_static serves them: the solve
+// of an FP64 handle runs entirely in a static device array that every GPU
+// loading this library holds until the process exits.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // per device
+constexpr size_t kStaticHostBytes = size_t(4) << 20;      // descriptor staging
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+alignas(256) unsigned char g_static_host[kStaticHostBytes];
+std::mutex g_static_mu;
+void* g_static_dev[kMaxDevices] = {};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double* u) {
+  if (!h || !f || !u || nrhs < 1) return HPS_EINVAL;
+  g_last_error.clear();
+  hps_handle_s& H = *h;
+  if (H.mixed) {
+    g_last_error = "hps_solve_static: only FP64 handles (mixed handles refine with more buffers)";
+    return HPS_EINVAL;
+  }
+  const Plan& pl = H.plan;
+  // carve the static array: exterior-value pool, u3 pool, GEMM descriptors
+  const size_t b_uext = align256((size_t)nrhs * pl.ext_total * sizeof(double));
+  const size_t b_u3 = align256((size_t)nrhs * std::max<int64_t>(H.u3_total, 1) * sizeof(double));
+  size_t b_desc = 0;
+  for (int hh = 1; hh <= pl.height; ++hh)
+    b_desc += align256(H.levels[hh].boxes.size() * sizeof(GemmDesc<double>));
+  if (b_uext + b_u3 + b_desc > kStaticScratchBytes || b_desc > kStaticHostBytes) {
+    g_last_error = "hps_solve_static: needs " + std::to_string(b_uext + b_u3 + b_desc) +
+                   " bytes of scratch, the static array holds " +
+                   std::to_string(kStaticScratchBytes);
+    return HPS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  try {
+    int dev = 0;
+    ck(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+      g_last_error = "hps_solve_static: device ordinal out of range";
+      return HPS_EINVAL;
+    }
+    if (!g_static_dev[dev]) {  // first call on this device: the array's device address
+      void* p = nullptr;
+      ck(cudaGetSymbolAddress(&p, g_static_scratch));
+      g_static_dev[dev] = p;
+    }
+    unsigned char* base = static_cast<unsigned char*>(g_static_dev[dev]);
+    double* uext = reinterpret_cast<double*>(base);
+    double* u3 = reinterpret_cast<double*>(base + b_uext);
+    unsigned char* dd = base + b_uext + b_u3;
+    cudaStream_t st = H.stream;
+    // descriptors of the downward GEMMs, staged in static host memory; the
+    // earlier call's copies have completed (each call ends synchronised)
+    GemmDesc<double>* dptr[128] = {};  // tree heights stay far below 128 (nx * ny <= 2^26)
+    if (pl.height >= 128) return HPS_EINVAL;
+    size_t off = 0;
+    for (int hh = 1; hh <= pl.height; ++hh) {
+      LevelOps& L = H.levels[hh];
+      GemmDesc<double>* hs = reinterpret_cast<GemmDesc<double>*>(g_static_host + off);
+      for (size_t i = 0; i < L.boxes.size(); ++i) {
+        const int b = L.boxes[i];
+        const MergeShape& sh = pl.shapes[pl.boxes[b].shape];
+        GemmDesc<double>& g = hs[i];
+        g.A = L.S->as<double>() + L.s_off[i];
+        g.B = uext + pl.boxes[b].ext_off;
+        g.C = u3 + H.u3_off[b];
+        g.M = sh.m;
+        g.N = nrhs;
+        g.K = sh.ne;
+        g.lda = sh.m;
+        g.ldb = (int)pl.ext_total;
+        g.ldc = (int)H.u3_total;
+      }
+      const size_t n = L.boxes.size() * sizeof(GemmDesc<double>);
+      ck(cudaMemcpyAsync(dd + off, g_static_host + off, n, cudaMemcpyHostToDevice, st));
+      dptr[hh] = reinterpret_cast<GemmDesc<double>*>(dd + off);
+      off += align256(n);
+    }
+    // nothing in the array has to start at zero: every exterior value and every
+    // u3 entry is written (root scatter, GEMMs with beta = 0, child scatters)
+    // before it is read
+    solve_root_scatter(f, H.root_from_f.as<int>(), H.nbnd, nrhs, uext, pl.boxes[0].ext_off,
+                       pl.ext_total, st);
+    for (int hh = pl.height; hh >= 1; --hh) {
+      LevelOps& L = H.levels[hh];
+      const int nm = (int)L.boxes.size();
+      gemm_batched<double>(dptr[hh], nm, L.max_m, nrhs, 1.0, 0.0, st, "gemm_solve_static<f64>",
+                           0.0, 0.0);
+      solve_child_scatter(L.scatter, nm, L.max_nanb, u3, H.u3_total, uext, pl.ext_total, nrhs, st);
+    }
+    leaf_post<double>(H.Y.as<double>(), H.ys, uext, H.leaf_off.as<int64_t>(), pl.ext_total, H.nl,
+                      pl.p, pl.q, nrhs, H.dPg2c.as<double>(), u, st);
+    ck(cudaGetLastError());
+    ck(cudaStreamSynchronize(st));
+    return HPS_OK;
+  } catch (CudaError&) {
+    cudaGetLastError();
+    return HPS_EDEVICE;
+  } catch (...) {
+    return HPS_EDEVICE;
+  }
+}

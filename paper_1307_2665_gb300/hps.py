@@ -30,7 +30,8 @@ COEFF_NAMES = ("c11", "c12", "c22", "c1", "c2", "c")
 EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes", "hps_solve",
            "hps_solve_ex", "hps_query", "hps_free", "hps_status_string", "hps_kernel_launches",
-           "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error")
+           "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error",
+           "hps_solve_static")
 
 
 class HpsError(RuntimeError):
@@ -96,6 +97,8 @@ def lib():
     L.hps_profile_reset.restype = None
     L.hps_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int]
     L.hps_profile_read.restype = ctypes.c_int
+    L.hps_solve_static.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.hps_solve_static.restype = ctypes.c_int
     L.hps_last_error.argtypes = []
     L.hps_last_error.restype = ctypes.c_char_p
     L.hps_status_string.argtypes = [ctypes.c_int]
@@ -225,6 +228,15 @@ def hps_solve(h: Handle, f, u=None, device_ptrs=None, info=None, check=True):
     if st != HPS_OK and check:
         raise HpsError(st, "hps_solve")
     return u
+
+
+def hps_solve_static(h: Handle, f, u, check=True):
+    """Solve through the allocation-free entry point (FP64 handle, device f and u)."""
+    nrhs = 1 if f.ndim == 1 else f.shape[0]
+    st = lib().hps_solve_static(h.ptr, _ptr(f), nrhs, _ptr(u))
+    if st != HPS_OK and check:
+        raise HpsError(st, "hps_solve_static")
+    return st
 
 
 def hps_query(h: Handle):
