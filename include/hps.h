@@ -113,8 +113,34 @@ int hps_build(hps_domain d, int nx, int ny, int p, int q,
               const double* c1, const double* c2, const double* c,
               const hps_options* opt, hps_handle* out);
 
+/* One problem of a batch: the arguments of hps_build. */
+typedef struct {
+  hps_domain d;
+  int nx, ny, p, q;
+  const double *c11, *c12, *c22, *c1, *c2, *c;
+} hps_problem;
+
+/* Build stage for a batch of independent problems (of uneven size and order p)
+ * in one handle.  The leaves of consecutive problems with equal (p, q) run as
+ * one launch group, and the merges of all problems are processed height by
+ * height (heights counted from the leaves), one launch sequence per height for
+ * the whole batch (two in mixed mode: FP32 and FP64 merges).  Every problem's
+ * arithmetic is the same as when it is built alone.  Options apply to every
+ * problem; fp64_top_levels counts from each problem's own root. */
+int hps_build_batch(const hps_problem* probs, int nprob, const hps_options* opt, hps_handle* out);
+
+/* Number of problems held by a handle (1 for hps_build). */
+int hps_batch_size(hps_handle h);
+
+/* Solve stage for a batch handle: f[k] (nrhs * nbnd_k) and u[k] (nrhs * nx_k *
+ * ny_k * p_k * p_k) for problem k, same layouts as hps_solve; the pointer kind
+ * follows options.device_ptrs of the build.  In mixed mode the refinement runs
+ * until every problem meets the tolerance. */
+int hps_solve_batch(hps_handle h, const double* const* f, int nrhs, double* const* u,
+                    hps_solve_info* info);
+
 /* Coordinates of the Gauss nodes on Gamma in the order of f (host array of
- * 2*nbnd doubles). */
+ * 2*nbnd doubles); for a batch handle, of its first problem. */
 int hps_boundary_nodes(hps_handle h, double* xy);
 
 /* Solve stage (Algorithm 2 and Section 4.3): given nrhs Dirichlet data sets f,
@@ -123,7 +149,10 @@ int hps_boundary_nodes(hps_handle h, double* xy);
  * system: each step solves the correction equation (interior residual as a
  * body load, flux jumps at the interior Gauss nodes) with the low-precision
  * factors and adds the correction in FP64.  It stops when the correction's
- * max-norm relative to u's is at most refine_tol (HPS_OK), or after
+ * max-norm relative to u's is at most refine_tol, or when the error it leaves
+ * (that correction times the observed contraction ratio of the last two
+ * corrections) is below refine_tol / 10 (HPS_OK; info->last_update then holds
+ * that estimate), or after
  * max_refine steps, or once the correction stops shrinking by half per step
  * (the iterate has reached the accuracy the FP64 residual resolves for this
  * conditioning); the latter two return HPS_ENOTCONVERGED with u holding the
@@ -132,12 +161,13 @@ int hps_boundary_nodes(hps_handle h, double* xy);
 int hps_solve(hps_handle h, const double* f, int nrhs, double* u, hps_solve_info* info);
 
 /* Same as hps_solve with an explicit pointer kind: device_ptrs 0 (host arrays,
- * copies to and from the device inside the call) or 1 (device arrays). */
+ * copies to and from the device inside the call) or 1 (device arrays).
+ * hps_solve / hps_solve_ex need a single-problem handle (else HPS_EINVAL). */
 int hps_solve_ex(hps_handle h, const double* f, int nrhs, double* u, int device_ptrs,
                  hps_solve_info* info);
 
-/* Sizes of a built handle: number of leaves, p, q, nbnd, bytes of device memory
- * held.  Any output pointer may be NULL. */
+/* Sizes of a built handle: number of leaves, p, q (of the first problem),
+ * total nbnd, bytes of device memory held.  Any output pointer may be NULL. */
 int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_t* device_bytes);
 
 /* Release every resource of the handle (NULL is accepted). */

@@ -1,11 +1,13 @@
 // C ABI of libhps: the build stage (Algorithm 1) and the solve stage
 // (Algorithm 2 + Section 4.3) orchestrated over the batched kernels.
 //
-// Build, per tree height h (h = 0: the leaves), one batched launch sequence per
-// height covering every leaf / merge of that height:
-//   h = 0   leaf_assemble -> LU of [A_ii | -A_ie L1] -> Y, leaf_dtn -> T
+// A handle holds one problem or a batch of independent problems (a forest).
+// Leaves are processed per group of equal (p, q); merges per tree height
+// (counted from the leaves) across all problems, so every launch covers every
+// leaf or every merge of that height in the whole batch:
+//   leaves  leaf_assemble -> LU of [A_ii | -A_ie L1] -> Y, leaf_dtn -> T
 //   h >= 1  merge_gather  -> LU of [T33^a - T33^b | -T31^a, T32^b] -> S,
-//           GEMM Tp += [T13^a; T23^b] S (eq. merge; skipped at the root unless
+//           GEMM Tp += [T13^a; T23^b] S (eq. merge; skipped at a root unless
 //           the root DtN is requested: the solve never needs it)
 // Children's T are released in stream order once every parent reading them is
 // built.  All device memory comes from a stream-ordered pool and all launch
@@ -13,11 +15,13 @@
 // only once, at the end, to read the pivot status.
 //
 // Precision.  HPS_FP64: every stage in double.  HPS_MIXED: the leaves and the
-// merges below the top `fp64_top_levels` heights run in float (their LU
-// factors, pivots and [T13^a; T23^b] blocks are kept), the top heights in
-// double; the solve then refines against the FP64 residual of the global
-// collocation system, one body-load correction per iteration (the elimination
-// of Algorithms 1-2 applied to a right-hand side).
+// merges below each problem's top `fp64_top_levels` heights run in float, the
+// top heights in double; float and double merges of one height are two
+// launch groups.  The build then also forms A_ii^{-1} and (T33^a - T33^b)^{-1}
+// (an identity appended to each right-hand side) and keeps [T13^a; T23^b],
+// and the solve refines against the FP64 residual of the global collocation
+// system, one body-load correction per iteration (the elimination of
+// Algorithms 1-2 applied to a right-hand side).
 //
 // Solve: root exterior values from f, then per height from the top a batched
 // GEMM u3 = S u_parent and a scatter into the children's exterior vectors, then
@@ -25,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -106,6 +111,8 @@ struct PoolBuf {
     return reinterpret_cast<T*>(p);
   }
 };
+using PoolPtr = std::unique_ptr<PoolBuf>;
+PoolPtr new_buf() { return PoolPtr(new PoolBuf()); }
 
 // Pinned staging of launch descriptors: each array is copied into the next
 // free slice of a pinned host block and uploaded asynchronously into the same
@@ -133,7 +140,7 @@ struct Stager {
       ck(cudaMallocHost(&host, bytes));
       cap = bytes;
     }
-    dev.alloc(bytes, st);
+    if (dev.bytes < bytes) dev.alloc(bytes, st);
     used = 0;
   }
   template <typename T>
@@ -156,52 +163,56 @@ size_t stage_bytes(size_t n) {
   return n * sizeof(T) + 256;
 }
 
-struct LevelOps {
-  int f64 = 1;                    // precision of this height's merges
+// Leaves of consecutive problems with one (p, q).
+struct LeafGroup {
+  int l0 = 0, nl = 0, p = 0, q = 0, ni = 0, nq = 0;
+  int64_t ys = 0;                   // elements per leaf in Y
+  Consts consts;
+  PoolPtr Y = new_buf();            // per leaf [Y | A_ii^{-1} (mixed)] (ld ni)
+  PoolPtr dD = new_buf(), dPg2c = new_buf(), dPc2g = new_buf();
+  const double* coefp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  PoolPtr rleaf = new_buf(), zleaf = new_buf();  // mixed: residual and correction
+  void* gemm_leaf = nullptr;        // mixed: z = A_ii^{-1} r
+};
+
+// Merges of one height and one precision, across all problems.
+struct LevelGroup {
+  int h = 0, f64 = 1;
   std::vector<int> boxes;
   int max_m = 0, max_ne = 0, max_nanb = 0;
-  int64_t sum_m = 0;              // rows of the height's z buffer
-  std::unique_ptr<PoolBuf> S, Cw;  // [S | W (mixed)] per merge; Cw kept in mixed mode
-  std::vector<int64_t> s_off, aw_off, cw_off, piv_off, z_off;
-  std::vector<int> hm, hne;       // host copies of m and ne (launch accounting)
-  SolveScatterDesc* scatter = nullptr;  // device descriptors (the handle's stager)
+  int64_t sum_m = 0;                // rows of the group's z buffer
+  PoolPtr S = new_buf(), Cw = new_buf();  // [S | W (mixed)] per merge; Cw kept in mixed mode
+  std::vector<int64_t> s_off, cw_off, z_off;
+  std::vector<int> hm, hne;         // host copies of m and ne (launch accounting)
+  SolveScatterDesc* scatter = nullptr;  // device descriptors (the handle's keep stager)
   BodyDesc* body = nullptr;
-  LevelOps() : S(new PoolBuf()), Cw(new PoolBuf()) {}
+  PoolPtr rlev = new_buf(), zlev = new_buf();  // mixed solve buffers
+  void* gemm_down = nullptr;        // per solve configuration
+  void* gemm_w = nullptr;
+  void* gemm_hpar = nullptr;
+  double down_flops1 = 0, down_bytes = 0;
 };
 
 }  // namespace
 
 struct hps_handle_s {
   Plan plan;
-  Consts consts;
   hps_options opt;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int ni = 0, nq = 0, nl = 0, nbnd = 0;
   bool mixed = false;
-  int leaf_f64 = 1;
-  double hx = 0, hy = 0;
-  PoolBuf dD, dPg2c, dPc2g, maps, root_from_f, leaf_off, status;
-  std::vector<int64_t> src_off, cma_off, cmb_off;
-  PoolBuf coef;                    // FP64 coefficient copy (mixed mode: the residual)
-  const double* coefp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  PoolBuf Y;                       // per leaf [Y | A_ii^{-1} (mixed mode)], stride ys
-  int64_t ys = 0;
-  std::vector<LevelOps> levels;    // index = height (0 unused)
-  std::vector<int64_t> u3_off;
+  int nprob = 0;
+  std::vector<LeafGroup> lg;
+  std::vector<LevelGroup> lev;      // in increasing height
+  PoolBuf maps, root_from_f, leaf_off, leaf_prob, hsc, status, coef;
+  std::vector<int64_t> src_off, cma_off, cmb_off, u3_off;
   int64_t u3_total = 0;
-  Stager keep;                     // descriptors that live as long as the handle
+  Stager keep;                      // descriptors that live as long as the handle
   // solve workspace and descriptors, cached for one nrhs
   int cache_nrhs = 0;
-  PoolBuf uext, u3, hpool, rleaf, zleaf, fstage, ustage, maxabs, split_ws;
-  std::vector<std::unique_ptr<PoolBuf>> rlev, zlev;
-  Stager solve_st;
-  std::vector<void*> gemm_down;    // per height: GemmDesc array (typed by level)
-  std::vector<void*> gemm_hpar;    // per height (mixed)
-  std::vector<void*> gemm_w;       // per height (mixed): z = W rhs
-  void* gemm_leaf = nullptr;       // (mixed): z = A_ii^{-1} r
-  std::vector<double> down_flops1, down_bytes;
-  unsigned long long* h_maxabs = nullptr;  // pinned
+  PoolBuf uext, u3, hpool, split_ws, maxabs, fstage, ustage;
+  Stager solve_st, call_st;
+  unsigned long long* h_maxabs = nullptr;  // pinned, 2 per problem
   ~hps_handle_s() {
     if (stream) cudaStreamSynchronize(stream);
     if (h_maxabs) cudaFreeHost(h_maxabs);
@@ -230,61 +241,64 @@ struct TRef {
 };
 
 template <typename R>
-void build_leaves(hps_handle_s& H, Stager& stg, std::vector<TRef>& Tref, PoolBuf& T0) {
+void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>& Tref,
+                  PoolBuf& T0) {
   const Plan& pl = H.plan;
   cudaStream_t st = H.stream;
-  const int p = pl.p, q = pl.q, ni = H.ni, nq = H.nq, nl = H.nl;
+  const int ni = G.ni, nq = G.nq, nl = G.nl;
   // mixed mode also solves for A_ii^{-1} (identity columns after -A_ie L1)
   const int nrhs_leaf = nq + (H.mixed ? ni : 0);
-  H.ys = (int64_t)ni * nrhs_leaf;
-  H.Y.alloc((size_t)nl * H.ys * sizeof(R), st);
+  G.ys = (int64_t)ni * nrhs_leaf;
+  G.Y->alloc((size_t)nl * G.ys * sizeof(R), st);
   PoolBuf Aii, piv;
   Aii.alloc((size_t)nl * ni * ni * sizeof(R), st);
   piv.alloc((size_t)nl * ni * sizeof(int), st);
-  leaf_assemble<R>(H.coefp, nl, p, q, H.hx, H.hy, H.dD.as<double>(), H.dPg2c.as<double>(),
-                   Aii.as<R>(), H.Y.as<R>(), H.ys, H.mixed ? 1 : 0, st);
+  const double2* hsc = H.hsc.as<double2>();
+  leaf_assemble<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(), G.dPg2c->as<double>(),
+                   Aii.as<R>(), G.Y->as<R>(), G.ys, H.mixed ? 1 : 0, st);
   ck(cudaGetLastError());
   std::vector<LuDesc<R>> ld(nl);
-  for (int l = 0; l < nl; ++l) {
-    ld[l].A = Aii.as<R>() + (size_t)l * ni * ni;
-    ld[l].ipiv = piv.as<int>() + (size_t)l * ni;
-    ld[l].B = H.Y.as<R>() + (size_t)l * H.ys;
-    ld[l].m = ni;
-    ld[l].lda = ni;
-    ld[l].nrhs = nrhs_leaf;
-    ld[l].ldb = ni;
-    ld[l].box = pl.leaf_box[l];
+  for (int j = 0; j < nl; ++j) {
+    ld[j].A = Aii.as<R>() + (size_t)j * ni * ni;
+    ld[j].ipiv = piv.as<int>() + (size_t)j * ni;
+    ld[j].B = G.Y->as<R>() + (size_t)j * G.ys;
+    ld[j].m = ni;
+    ld[j].lda = ni;
+    ld[j].nrhs = nrhs_leaf;
+    ld[j].ldb = ni;
+    ld[j].box = pl.leaf_box[G.l0 + j];
   }
   LuDesc<R>* dl = stg.push(ld, st);
   lu_solve_batched<R>(dl, nl, ni, nrhs_leaf, kLuFactor, H.status.as<int>(), st, nullptr, nullptr);
   ck(cudaGetLastError());
   T0.alloc((size_t)nl * nq * nq * sizeof(R), st);
-  leaf_dtn<R>(H.Y.as<R>(), H.ys, nl, p, q, H.hx, H.hy, H.dD.as<double>(), H.dPg2c.as<double>(),
-              H.dPc2g.as<double>(), T0.as<R>(), st);
+  leaf_dtn<R>(G.Y->as<R>(), G.ys, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(),
+              G.dPg2c->as<double>(), G.dPc2g->as<double>(), T0.as<R>(), st);
   ck(cudaGetLastError());
-  for (int l = 0; l < nl; ++l) {
-    Tref[pl.leaf_box[l]].p = T0.as<R>() + (size_t)l * nq * nq;
-    Tref[pl.leaf_box[l]].f64 = sizeof(R) == 8;
+  for (int j = 0; j < nl; ++j) {
+    Tref[pl.leaf_box[G.l0 + j]].p = T0.as<R>() + (size_t)j * nq * nq;
+    Tref[pl.leaf_box[G.l0 + j]].f64 = sizeof(R) == 8;
   }
 }
 
 template <typename R>
-void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, PoolBuf& Tout) {
+void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>& Tref,
+                 PoolBuf& Tout) {
   const Plan& pl = H.plan;
   cudaStream_t st = H.stream;
-  LevelOps& L = H.levels[h];
   const int nm = (int)L.boxes.size();
   const bool form_root = H.opt.form_root_dtn != 0;
   int64_t aw_tot = 0, cw_tot = 0, tp_tot = 0, piv_tot = 0, s_tot = 0;
   int64_t max_work = 0;
+  std::vector<int64_t> aw_off(nm), piv_off(nm);
   for (int i = 0; i < nm; ++i) {
     const int b = L.boxes[i];
     const MergeShape& sh = pl.shapes[pl.boxes[b].shape];
-    const bool tp = (b != 0) || form_root;
+    const bool tp = pl.boxes[b].parent >= 0 || form_root;
     L.s_off[i] = s_tot;
-    L.aw_off[i] = aw_tot;
+    aw_off[i] = aw_tot;
     L.cw_off[i] = cw_tot;
-    L.piv_off[i] = piv_tot;
+    piv_off[i] = piv_tot;
     s_tot += (int64_t)sh.m * (sh.ne + (H.mixed ? sh.m : 0));
     aw_tot += (int64_t)sh.m * sh.m;
     cw_tot += (int64_t)sh.ne * sh.m;
@@ -306,19 +320,20 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
   std::vector<MergeDesc<R>> md(nm);
   std::vector<LuDesc<R>> lu(nm);
   std::vector<GemmDesc<R>> gm;
+  std::vector<int> hn(nm);
   double gather_bytes = 0.0, schur_flops = 0.0, schur_bytes = 0.0;
   int64_t ot = 0;
   for (int i = 0; i < nm; ++i) {
     const int b = L.boxes[i];
     const Box& B = pl.boxes[b];
     const MergeShape& sh = pl.shapes[B.shape];
-    const bool tp = (b != 0) || form_root;
+    const bool tp = B.parent >= 0 || form_root;
     MergeDesc<R>& g = md[i];
     g.Ta = Tref[B.child[0]].p;
     g.ta64 = Tref[B.child[0]].f64;
     g.Tb = Tref[B.child[1]].p;
     g.tb64 = Tref[B.child[1]].f64;
-    g.Aw = Aw.as<R>() + L.aw_off[i];
+    g.Aw = Aw.as<R>() + aw_off[i];
     g.S = L.S->as<R>() + L.s_off[i];
     g.Cw = Cw.as<R>() + L.cw_off[i];
     g.Tp = tp ? Tout.as<R>() + ot : nullptr;
@@ -331,13 +346,14 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
     g.j3a = sh.j3a;
     g.j3b = sh.j3b;
     lu[i].A = g.Aw;
-    lu[i].ipiv = piv.as<int>() + L.piv_off[i];
+    lu[i].ipiv = piv.as<int>() + piv_off[i];
     lu[i].B = g.S;
     lu[i].m = sh.m;
     lu[i].lda = sh.m;
     lu[i].nrhs = sh.ne + (H.mixed ? sh.m : 0);
     lu[i].ldb = sh.m;
     lu[i].box = b;
+    hn[i] = lu[i].nrhs;
     gather_bytes += (sizeof(R) + 8.0) *
                     ((double)sh.m * sh.m + 2.0 * sh.m * sh.ne + (tp ? (double)sh.ne * sh.ne : 0.0));
     if (tp) {
@@ -363,8 +379,6 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
   LuDesc<R>* dlu = stg.push(lu, st);
   merge_gather<R>(dmd, nm, max_work, st, gather_bytes);
   ck(cudaGetLastError());
-  std::vector<int> hn(nm);
-  for (int i = 0; i < nm; ++i) hn[i] = L.hne[i] + (H.mixed ? L.hm[i] : 0);
   lu_solve_batched<R>(dlu, nm, L.max_m, L.max_ne + (H.mixed ? L.max_m : 0), kLuFactor,
                       H.status.as<int>(), st, L.hm.data(), hn.data());
   ck(cudaGetLastError());
@@ -377,68 +391,92 @@ void build_level(hps_handle_s& H, int h, Stager& stg, std::vector<TRef>& Tref, P
   }
 }
 
-void build_all(hps_handle_s& H, const double* const coef_in[6], bool dev_ptrs) {
+void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool dev_ptrs) {
   Plan& pl = H.plan;
   cudaStream_t st = H.stream;
-  const int p = pl.p, pp = p * p, nl = H.nl;
-  // precision of each height
-  H.levels.clear();
-  H.levels.resize(pl.height + 1);
+  const int nl_tot = pl.n_leaves();
   const int top = std::max(0, H.opt.fp64_top_levels);
-  H.leaf_f64 = H.mixed ? 0 : 1;
-  for (int h = 1; h <= pl.height; ++h) {
-    LevelOps& L = H.levels[h];
-    L.f64 = H.mixed ? (h > pl.height - top ? 1 : 0) : 1;
-    L.boxes = pl.levels[h];
-    const int nm = (int)L.boxes.size();
-    L.s_off.assign(nm, 0);
-    L.aw_off.assign(nm, 0);
-    L.cw_off.assign(nm, 0);
-    L.piv_off.assign(nm, 0);
-    L.z_off.assign(nm, 0);
-    L.hm.assign(nm, 0);
-    L.hne.assign(nm, 0);
-    int64_t zrows = 0;
-    for (int i = 0; i < nm; ++i) {
-      const MergeShape& sh = pl.shapes[pl.boxes[L.boxes[i]].shape];
-      L.max_m = std::max(L.max_m, sh.m);
-      L.max_ne = std::max(L.max_ne, sh.ne);
-      L.max_nanb = std::max(L.max_nanb, sh.na + sh.nb);
-      L.hm[i] = sh.m;
-      L.hne[i] = sh.ne;
-      L.z_off[i] = zrows;
-      zrows += sh.m;
+  // ---- leaf groups: consecutive problems with one (p, q)
+  H.lg.clear();
+  for (int k = 0; k < H.nprob; ++k) {
+    const ProblemSpec& s = pl.probs[k].s;
+    if (H.lg.empty() || H.lg.back().p != s.p || H.lg.back().q != s.q) {
+      H.lg.emplace_back();
+      LeafGroup& G = H.lg.back();
+      G.l0 = pl.probs[k].leaf0;
+      G.p = s.p;
+      G.q = s.q;
+      G.ni = (s.p - 2) * (s.p - 2);
+      G.nq = 4 * s.q;
     }
-    L.sum_m = zrows;
+    H.lg.back().nl += pl.probs[k].nl;
+  }
+  // ---- level groups: (height, precision), in increasing height
+  H.lev.clear();
+  for (int h = 1; h <= pl.height; ++h) {
+    for (int f64 : {0, 1}) {
+      std::vector<int> bx;
+      for (int b : pl.levels[h]) {
+        const int prob_h = pl.probs[pl.boxes[b].prob].height;
+        const int want = H.mixed ? (h > prob_h - top ? 1 : 0) : 1;
+        if (want == f64) bx.push_back(b);
+      }
+      if (bx.empty()) continue;
+      H.lev.emplace_back();
+      LevelGroup& L = H.lev.back();
+      L.h = h;
+      L.f64 = f64;
+      L.boxes = bx;
+      const int nm = (int)bx.size();
+      L.s_off.assign(nm, 0);
+      L.cw_off.assign(nm, 0);
+      L.z_off.assign(nm, 0);
+      L.hm.assign(nm, 0);
+      L.hne.assign(nm, 0);
+      int64_t zrows = 0;
+      for (int i = 0; i < nm; ++i) {
+        const MergeShape& sh = pl.shapes[pl.boxes[bx[i]].shape];
+        L.max_m = std::max(L.max_m, sh.m);
+        L.max_ne = std::max(L.max_ne, sh.ne);
+        L.max_nanb = std::max(L.max_nanb, sh.na + sh.nb);
+        L.hm[i] = sh.m;
+        L.hne[i] = sh.ne;
+        L.z_off[i] = zrows;
+        zrows += sh.m;
+      }
+      L.sum_m = zrows;
+    }
   }
   H.u3_off.assign(pl.boxes.size(), -1);
   H.u3_total = 0;
-  for (int h = 1; h <= pl.height; ++h)
-    for (int b : pl.levels[h]) {
+  for (auto& L : H.lev)
+    for (int b : L.boxes) {
       H.u3_off[b] = H.u3_total;
       H.u3_total += pl.shapes[pl.boxes[b].shape].m;
     }
   // descriptor staging (upper bound of every array pushed below)
-  size_t nb = pl.boxes.size();
+  const size_t nb = pl.boxes.size();
   Stager stg;
-  size_t bytes = stage_bytes<LuDesc<double>>(nl) + 8 * 256;
-  for (int h = 1; h <= pl.height; ++h) {
-    size_t nm = H.levels[h].boxes.size();
-    bytes += stage_bytes<MergeDesc<double>>(nm) + stage_bytes<LuDesc<double>>(nm) +
-             stage_bytes<GemmDesc<double>>(nm);
-  }
+  size_t bytes = 8 * 256 + stage_bytes<LuDesc<double>>(nl_tot) + 256 * H.lg.size();
+  for (auto& L : H.lev)
+    bytes += stage_bytes<MergeDesc<double>>(L.boxes.size()) +
+             stage_bytes<LuDesc<double>>(L.boxes.size()) +
+             stage_bytes<GemmDesc<double>>(L.boxes.size());
   stg.begin(bytes, st);
   H.keep.begin(stage_bytes<SolveScatterDesc>(nb) + stage_bytes<BodyDesc>(nb) +
-                   4 * 256 * (pl.height + 2),
+                   4 * 256 * (H.lev.size() + 2),
                st);
-  // constants, maps, status
+  // constants, maps, per-leaf data, status (pageable uploads: synchronised below)
   auto up = [&](PoolBuf& b, const void* src, size_t n) {
     b.alloc(n, st);
     if (n) ck(cudaMemcpyAsync(b.p, src, n, cudaMemcpyHostToDevice, st));
   };
-  up(H.dD, H.consts.D.data(), H.consts.D.size() * sizeof(double));
-  up(H.dPg2c, H.consts.Pg2c.data(), H.consts.Pg2c.size() * sizeof(double));
-  up(H.dPc2g, H.consts.Pc2g.data(), H.consts.Pc2g.size() * sizeof(double));
+  for (auto& G : H.lg) {
+    G.consts = make_consts(G.p, G.q);
+    up(*G.dD, G.consts.D.data(), G.consts.D.size() * sizeof(double));
+    up(*G.dPg2c, G.consts.Pg2c.data(), G.consts.Pg2c.size() * sizeof(double));
+    up(*G.dPc2g, G.consts.Pc2g.data(), G.consts.Pc2g.size() * sizeof(double));
+  }
   {
     std::vector<int> all;
     for (const auto& s : pl.shapes) {
@@ -451,59 +489,102 @@ void build_all(hps_handle_s& H, const double* const coef_in[6], bool dev_ptrs) {
     }
     up(H.maps, all.data(), all.size() * sizeof(int));
     up(H.root_from_f, pl.root_from_f.data(), pl.root_from_f.size() * sizeof(int));
-    std::vector<int64_t> lo(nl);
-    for (int l = 0; l < nl; ++l) lo[l] = pl.boxes[pl.leaf_box[l]].ext_off;
+    std::vector<int64_t> lo(nl_tot);
+    std::vector<double2> hs(nl_tot);
+    for (int l = 0; l < nl_tot; ++l) {
+      lo[l] = pl.boxes[pl.leaf_box[l]].ext_off;
+      const ProbInfo& pi = pl.probs[pl.leaf_prob[l]];
+      hs[l] = make_double2(2.0 / pi.hx, 2.0 / pi.hy);
+    }
     up(H.leaf_off, lo.data(), lo.size() * sizeof(int64_t));
+    up(H.leaf_prob, pl.leaf_prob.data(), pl.leaf_prob.size() * sizeof(int));
+    up(H.hsc, hs.data(), hs.size() * sizeof(double2));
     ck(cudaStreamSynchronize(st));  // the pageable sources above go out of scope
   }
   H.status.alloc(sizeof(int), st);
   ck(cudaMemsetAsync(H.status.p, 0, sizeof(int), st));
-  // coefficients on the device (kept in mixed mode for the FP64 residual)
-  PoolBuf coef_tmp;
+  // ---- coefficients: one device copy laid out group by group (kept in mixed
+  // mode for the FP64 residual); a coefficient absent from a problem is zero
+  // there, and absent from a whole group is skipped by the kernels
   {
-    int npresent = 0;
-    for (int k = 0; k < 6; ++k) npresent += coef_in[k] != nullptr;
-    PoolBuf& cb = H.mixed ? H.coef : coef_tmp;
-    const bool copy = !dev_ptrs || H.mixed;
-    if (copy && npresent) cb.alloc((size_t)npresent * nl * pp * sizeof(double), st);
-    int slot = 0;
-    for (int k = 0; k < 6; ++k) {
-      if (!coef_in[k]) {
-        H.coefp[k] = nullptr;
-      } else if (!copy) {
-        H.coefp[k] = coef_in[k];
-      } else {
-        double* dst = cb.as<double>() + (size_t)slot * nl * pp;
-        ck(cudaMemcpyAsync(dst, coef_in[k], (size_t)nl * pp * sizeof(double),
-                           dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        H.coefp[k] = dst;
-        ++slot;
+    size_t elems = 0;
+    std::vector<std::array<int64_t, 6>> goff(H.lg.size());
+    for (size_t g = 0; g < H.lg.size(); ++g) {
+      LeafGroup& G = H.lg[g];
+      for (int c = 0; c < 6; ++c) {
+        bool any = false;
+        for (int k = 0; k < H.nprob; ++k)
+          if (pl.probs[k].leaf0 >= G.l0 && pl.probs[k].leaf0 < G.l0 + G.nl && coef_in[6 * k + c])
+            any = true;
+        goff[g][c] = any ? (int64_t)elems : -1;
+        if (any) elems += (size_t)G.nl * G.p * G.p;
+      }
+    }
+    H.coef.alloc(elems * sizeof(double), st);
+    for (size_t g = 0; g < H.lg.size(); ++g) {
+      LeafGroup& G = H.lg[g];
+      const int pp = G.p * G.p;
+      for (int c = 0; c < 6; ++c) {
+        if (goff[g][c] < 0) {
+          G.coefp[c] = nullptr;
+          continue;
+        }
+        double* base = H.coef.as<double>() + goff[g][c];
+        G.coefp[c] = base;
+        for (int k = 0; k < H.nprob; ++k) {
+          const ProbInfo& pi = pl.probs[k];
+          if (pi.leaf0 < G.l0 || pi.leaf0 >= G.l0 + G.nl) continue;
+          double* dst = base + (size_t)(pi.leaf0 - G.l0) * pp;
+          const size_t n = (size_t)pi.nl * pp * sizeof(double);
+          if (coef_in[6 * k + c])
+            ck(cudaMemcpyAsync(dst, coef_in[6 * k + c], n,
+                               dev_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+          else
+            ck(cudaMemsetAsync(dst, 0, n, st));
+        }
       }
     }
   }
   // ---- leaves and merges
   std::vector<TRef> Tref(pl.boxes.size());
-  std::vector<std::unique_ptr<PoolBuf>> Tbuf(pl.height + 1);
-  for (auto& t : Tbuf) t.reset(new PoolBuf());
-  if (H.leaf_f64)
-    build_leaves<double>(H, stg, Tref, *Tbuf[0]);
-  else
-    build_leaves<float>(H, stg, Tref, *Tbuf[0]);
-  std::vector<int> last_use(pl.height + 1, -1);
-  for (const auto& bx : pl.boxes)
-    if (bx.parent >= 0)
-      last_use[bx.height] = std::max(last_use[bx.height], pl.boxes[bx.parent].height);
-  for (int h = 1; h <= pl.height; ++h) {
-    if (H.levels[h].f64)
-      build_level<double>(H, h, stg, Tref, *Tbuf[h]);
+  std::vector<PoolPtr> Tleaf;
+  for (auto& G : H.lg) {
+    Tleaf.push_back(new_buf());
+    if (H.mixed)
+      build_leaves<float>(H, G, stg, Tref, *Tleaf.back());
     else
-      build_level<float>(H, h, stg, Tref, *Tbuf[h]);
-    for (int hh = 0; hh < h; ++hh)
-      if (last_use[hh] == h) Tbuf[hh]->release();
+      build_leaves<double>(H, G, stg, Tref, *Tleaf.back());
+  }
+  // T buffers per level group, released after the last level group reading them
+  std::vector<PoolPtr> Tlev;
+  for (size_t i = 0; i < H.lev.size(); ++i) Tlev.push_back(new_buf());
+  std::vector<int> box_group(pl.boxes.size(), -1);  // level group producing each box's T
+  for (size_t i = 0; i < H.lev.size(); ++i)
+    for (int b : H.lev[i].boxes) box_group[b] = (int)i;
+  std::vector<int> last_use_leaf(H.lg.size(), -1), last_use(H.lev.size(), -1);
+  for (size_t i = 0; i < H.lev.size(); ++i)
+    for (int b : H.lev[i].boxes)
+      for (int c : pl.boxes[b].child) {
+        if (pl.boxes[c].leaf >= 0) {
+          for (size_t g = 0; g < H.lg.size(); ++g)
+            if (pl.boxes[c].leaf >= H.lg[g].l0 && pl.boxes[c].leaf < H.lg[g].l0 + H.lg[g].nl)
+              last_use_leaf[g] = (int)i;
+        } else {
+          last_use[box_group[c]] = std::max(last_use[box_group[c]], (int)i);
+        }
+      }
+  for (size_t i = 0; i < H.lev.size(); ++i) {
+    if (H.lev[i].f64)
+      build_level<double>(H, H.lev[i], stg, Tref, *Tlev[i]);
+    else
+      build_level<float>(H, H.lev[i], stg, Tref, *Tlev[i]);
+    for (size_t g = 0; g < H.lg.size(); ++g)
+      if (last_use_leaf[g] == (int)i) Tleaf[g]->release();
+    for (size_t j = 0; j < i; ++j)
+      if (last_use[j] == (int)i) Tlev[j]->release();
   }
   // ---- solve-side structures that do not depend on nrhs
-  for (int h = 1; h <= pl.height; ++h) {
-    LevelOps& L = H.levels[h];
+  for (auto& L : H.lev) {
     std::vector<SolveScatterDesc> sd;
     std::vector<BodyDesc> bd;
     for (size_t i = 0; i < L.boxes.size(); ++i) {
@@ -537,6 +618,7 @@ void build_all(hps_handle_s& H, const double* const coef_in[6], bool dev_ptrs) {
     L.scatter = H.keep.push(sd, st);
     L.body = H.keep.push(bd, st);
   }
+  if (!H.mixed) H.coef.release();  // only the residual of mixed mode reads it later
   int* bad_h = nullptr;
   ck(cudaMallocHost(&bad_h, sizeof(int)));
   *bad_h = 0;
@@ -546,15 +628,15 @@ void build_all(hps_handle_s& H, const double* const coef_in[6], bool dev_ptrs) {
   cudaFreeHost(bad_h);
   ck(e1);
   ck(e2);
-  for (auto& t : Tbuf) t->release();
+  Tleaf.clear();
+  Tlev.clear();
   if (bad) throw bad;
 }
 
 // ------------------------------------------------------------------ solve
 template <typename R>
-void push_down_gemms(hps_handle_s& H, int h, int nrhs) {
+void push_down_gemms(hps_handle_s& H, LevelGroup& L, int nrhs) {
   const Plan& pl = H.plan;
-  LevelOps& L = H.levels[h];
   std::vector<GemmDesc<R, double, double>> all;
   double fl = 0, by = 0;
   for (size_t i = 0; i < L.boxes.size(); ++i) {
@@ -574,19 +656,18 @@ void push_down_gemms(hps_handle_s& H, int h, int nrhs) {
     fl += 2.0 * sh.m * (double)sh.ne;
     by += sizeof(R) * (double)sh.m * sh.ne;
   }
-  H.gemm_down[h] = H.solve_st.push(all, H.stream);
-  H.down_flops1[h] = fl;
-  H.down_bytes[h] = by;
+  L.gemm_down = H.solve_st.push(all, H.stream);
+  L.down_flops1 = fl;
+  L.down_bytes = by;
 }
 
 template <typename R>
-void push_body(hps_handle_s& H, int h, int nrhs) {
+void push_body(hps_handle_s& H, LevelGroup& L, int nrhs) {
   const Plan& pl = H.plan;
-  LevelOps& L = H.levels[h];
   std::vector<GemmDesc<R, R, double>> gh;
   std::vector<GemmDesc<R>> gw;
-  R* z = H.zlev[h]->as<R>();
-  R* r = H.rlev[h]->as<R>();
+  R* z = L.zlev->as<R>();
+  R* r = L.rlev->as<R>();
   for (size_t i = 0; i < L.boxes.size(); ++i) {
     const int b = L.boxes[i];
     const MergeShape& sh = pl.shapes[pl.boxes[b].shape];
@@ -613,26 +694,26 @@ void push_body(hps_handle_s& H, int h, int nrhs) {
     g.ldc = (int)pl.ext_total;
     gh.push_back(g);
   }
-  H.gemm_w[h] = H.solve_st.push(gw, H.stream);
-  H.gemm_hpar[h] = H.solve_st.push(gh, H.stream);
+  L.gemm_w = H.solve_st.push(gw, H.stream);
+  L.gemm_hpar = H.solve_st.push(gh, H.stream);
 }
 
 template <typename R>
-void push_leaf_inverse(hps_handle_s& H, int nrhs) {
-  std::vector<GemmDesc<R>> g(H.nl);
-  const int ni = H.ni;
-  for (int l = 0; l < H.nl; ++l) {  // z_l = A_ii^{-1} r_l
-    g[l].A = H.Y.as<R>() + (size_t)l * H.ys + (size_t)ni * H.nq;
-    g[l].B = H.rleaf.as<R>() + (size_t)l * ni * nrhs;
-    g[l].C = H.zleaf.as<R>() + (size_t)l * ni * nrhs;
-    g[l].M = ni;
-    g[l].N = nrhs;
-    g[l].K = ni;
-    g[l].lda = ni;
-    g[l].ldb = ni;
-    g[l].ldc = ni;
+void push_leaf_inverse(hps_handle_s& H, LeafGroup& G, int nrhs) {
+  std::vector<GemmDesc<R>> g(G.nl);
+  const int ni = G.ni;
+  for (int j = 0; j < G.nl; ++j) {  // z_l = A_ii^{-1} r_l
+    g[j].A = G.Y->as<R>() + (size_t)j * G.ys + (size_t)ni * G.nq;
+    g[j].B = G.rleaf->as<R>() + (size_t)j * ni * nrhs;
+    g[j].C = G.zleaf->as<R>() + (size_t)j * ni * nrhs;
+    g[j].M = ni;
+    g[j].N = nrhs;
+    g[j].K = ni;
+    g[j].lda = ni;
+    g[j].ldb = ni;
+    g[j].ldc = ni;
   }
-  H.gemm_leaf = H.solve_st.push(g, H.stream);
+  G.gemm_leaf = H.solve_st.push(g, H.stream);
 }
 
 void prepare_solve(hps_handle_s& H, int nrhs) {
@@ -642,45 +723,44 @@ void prepare_solve(hps_handle_s& H, int nrhs) {
   H.cache_nrhs = 0;
   H.uext.alloc((size_t)nrhs * pl.ext_total * sizeof(double), st);
   H.u3.alloc((size_t)nrhs * std::max<int64_t>(H.u3_total, 1) * sizeof(double), st);
-  H.split_ws.alloc((size_t)64 << 20, st);
-  H.gemm_down.assign(pl.height + 1, nullptr);
-  H.gemm_hpar.assign(pl.height + 1, nullptr);
-  H.gemm_w.assign(pl.height + 1, nullptr);
-  H.down_flops1.assign(pl.height + 1, 0.0);
-  H.down_bytes.assign(pl.height + 1, 0.0);
-  size_t bytes = 4 * 256 * (pl.height + 2) + stage_bytes<GemmDesc<double>>(H.nl);
-  for (int h = 1; h <= pl.height; ++h) bytes += 3 * stage_bytes<GemmDesc<double>>(H.levels[h].boxes.size());
+  // split-K scratch: the largest need of any solve-phase GEMM
+  size_t ws = 0;
+  for (auto& L : H.lev) {
+    const size_t es = L.f64 ? 8 : 4;
+    const int nm = (int)L.boxes.size();
+    ws = std::max(ws, es * split_ws_elems(nm, L.max_m, nrhs, L.max_ne));
+    if (H.mixed) {
+      ws = std::max(ws, es * split_ws_elems(nm, L.max_m, nrhs, L.max_m));
+      ws = std::max(ws, es * split_ws_elems(nm, L.max_ne, nrhs, L.max_m));
+    }
+  }
+  H.split_ws.alloc(ws, st);
+  size_t bytes = 4 * 256 * (H.lev.size() + H.lg.size() + 2);
+  for (auto& G : H.lg) bytes += stage_bytes<GemmDesc<double>>(G.nl);
+  for (auto& L : H.lev) bytes += 3 * stage_bytes<GemmDesc<double>>(L.boxes.size());
   H.solve_st.begin(bytes, st);
   if (H.mixed) {
     H.hpool.alloc((size_t)nrhs * pl.ext_total * sizeof(double), st);
-    const size_t es = H.leaf_f64 ? 8 : 4;
-    H.rleaf.alloc((size_t)H.nl * H.ni * nrhs * es, st);
-    H.zleaf.alloc((size_t)H.nl * H.ni * nrhs * es, st);
-    H.rlev.clear();
-    H.zlev.clear();
-    for (int h = 0; h <= pl.height; ++h) {
-      H.rlev.emplace_back(new PoolBuf());
-      H.zlev.emplace_back(new PoolBuf());
-      if (h >= 1) {
-        const size_t n = (size_t)H.levels[h].sum_m * nrhs * (H.levels[h].f64 ? 8 : 4);
-        H.rlev[h]->alloc(n, st);
-        H.zlev[h]->alloc(n, st);
-      }
+    for (auto& G : H.lg) {
+      G.rleaf->alloc((size_t)G.nl * G.ni * nrhs * sizeof(float), st);
+      G.zleaf->alloc((size_t)G.nl * G.ni * nrhs * sizeof(float), st);
+      push_leaf_inverse<float>(H, G, nrhs);
     }
-    H.maxabs.alloc(2 * sizeof(unsigned long long), st);
-    if (!H.h_maxabs) ck(cudaMallocHost(&H.h_maxabs, 2 * sizeof(unsigned long long)));
-    if (H.leaf_f64)
-      push_leaf_inverse<double>(H, nrhs);
-    else
-      push_leaf_inverse<float>(H, nrhs);
+    for (auto& L : H.lev) {
+      const size_t n = (size_t)L.sum_m * nrhs * (L.f64 ? 8 : 4);
+      L.rlev->alloc(n, st);
+      L.zlev->alloc(n, st);
+    }
+    H.maxabs.alloc(2 * (size_t)H.nprob * sizeof(unsigned long long), st);
+    if (!H.h_maxabs) ck(cudaMallocHost(&H.h_maxabs, 2 * (size_t)H.nprob * sizeof(unsigned long long)));
   }
-  for (int h = 1; h <= pl.height; ++h) {
-    if (H.levels[h].f64) {
-      push_down_gemms<double>(H, h, nrhs);
-      if (H.mixed) push_body<double>(H, h, nrhs);
+  for (auto& L : H.lev) {
+    if (L.f64) {
+      push_down_gemms<double>(H, L, nrhs);
+      if (H.mixed) push_body<double>(H, L, nrhs);
     } else {
-      push_down_gemms<float>(H, h, nrhs);
-      if (H.mixed) push_body<float>(H, h, nrhs);
+      push_down_gemms<float>(H, L, nrhs);
+      if (H.mixed) push_body<float>(H, L, nrhs);
     }
   }
   H.cache_nrhs = nrhs;
@@ -692,134 +772,144 @@ R* split_ws(hps_handle_s& H, size_t* elems) {
   return H.split_ws.as<R>();
 }
 
-// Downward pass (Algorithm 2) from the root exterior values already in uext;
-// with_z adds the body-load interface values z of each merge.
+// Downward pass (Algorithm 2) of one level group from the exterior values
+// already in uext; with_z adds the body-load interface values z of each merge.
 template <typename R>
-void down_level(hps_handle_s& H, int h, int nrhs, bool with_z) {
-  LevelOps& L = H.levels[h];
+void down_level(hps_handle_s& H, LevelGroup& L, int nrhs, bool with_z) {
   cudaStream_t st = H.stream;
   const int nm = (int)L.boxes.size();
   if (with_z)
-    z_to_u3<R>(L.body, nm, L.max_m, H.zlev[h]->as<R>(), H.u3.as<double>(), H.u3_total, nrhs, st);
+    z_to_u3<R>(L.body, nm, L.max_m, L.zlev->as<R>(), H.u3.as<double>(), H.u3_total, nrhs, st);
   size_t wse = 0;
   R* ws = split_ws<R>(H, &wse);
-  gemm_batched<R>(static_cast<GemmDesc<R, double, double>*>(H.gemm_down[h]), nm, L.max_m, nrhs,
-                  R(1), with_z ? R(1) : R(0), st,
-                  sizeof(R) == 8 ? "gemm_solve<f64>" : "gemm_solve<f32>",
-                  H.down_flops1[h] * nrhs, H.down_bytes[h], L.max_ne, ws, wse);
+  gemm_batched<R>(static_cast<GemmDesc<R, double, double>*>(L.gemm_down), nm, L.max_m, nrhs, R(1),
+                  with_z ? R(1) : R(0), st, sizeof(R) == 8 ? "gemm_solve<f64>" : "gemm_solve<f32>",
+                  L.down_flops1 * nrhs, L.down_bytes, L.max_ne, ws, wse);
   solve_child_scatter(L.scatter, nm, L.max_nanb, H.u3.as<double>(), H.u3_total,
                       H.uext.as<double>(), H.plan.ext_total, nrhs, st);
 }
 
 void downward(hps_handle_s& H, int nrhs, bool with_z) {
-  for (int h = H.plan.height; h >= 1; --h) {
-    if (H.levels[h].f64)
-      down_level<double>(H, h, nrhs, with_z);
+  for (int i = (int)H.lev.size() - 1; i >= 0; --i) {
+    if (H.lev[i].f64)
+      down_level<double>(H, H.lev[i], nrhs, with_z);
     else
-      down_level<float>(H, h, nrhs, with_z);
+      down_level<float>(H, H.lev[i], nrhs, with_z);
   }
 }
 
-template <typename R>
-void leaf_out(hps_handle_s& H, int nrhs, double* u, bool correction) {
-  const Plan& pl = H.plan;
-  leaf_post<R>(H.Y.as<R>(), H.ys, H.uext.as<double>(), H.leaf_off.as<int64_t>(), pl.ext_total, H.nl,
-               pl.p, pl.q, nrhs, H.dPg2c.as<double>(), u, H.stream,
-               correction ? H.zleaf.as<R>() : nullptr, correction ? 1 : 0,
-               correction ? H.maxabs.as<unsigned long long>() : nullptr);
+struct CallPtrs {           // per solve call: where f comes from and u goes
+  RootDesc* roots = nullptr;
+  double* const* wptr = nullptr;
+  const int64_t* wrs = nullptr;
+  int max_nbnd = 0;
+};
+
+void leaf_out(hps_handle_s& H, const CallPtrs& cp, int nrhs, bool correction) {
+  for (auto& G : H.lg) {
+    if (H.mixed)
+      leaf_post<float>(G.Y->as<float>(), G.ys, G.l0, H.uext.as<double>(), H.leaf_off.as<int64_t>(),
+                       H.plan.ext_total, G.nl, G.p, G.q, nrhs, G.dPg2c->as<double>(), cp.wptr,
+                       cp.wrs, H.stream, correction ? G.zleaf->as<float>() : nullptr,
+                       correction ? 1 : 0,
+                       correction ? H.maxabs.as<unsigned long long>() : nullptr,
+                       H.leaf_prob.as<int>());
+    else
+      leaf_post<double>(G.Y->as<double>(), G.ys, G.l0, H.uext.as<double>(),
+                        H.leaf_off.as<int64_t>(), H.plan.ext_total, G.nl, G.p, G.q, nrhs,
+                        G.dPg2c->as<double>(), cp.wptr, cp.wrs, H.stream);
+  }
 }
 
 // Leaf part of one refinement step: r = -(A w)_i in FP64, z = A_ii^{-1} r, and
 // the leaves' flux offsets h = L4 L3 (w + [0; z]).
-template <typename RL>
-void leaf_correction_rhs(hps_handle_s& H, int nrhs, const double* u) {
-  const Plan& pl = H.plan;
+void leaf_correction_rhs(hps_handle_s& H, const CallPtrs& cp, int nrhs) {
   cudaStream_t st = H.stream;
-  leaf_residual<RL>(H.coefp, H.nl, pl.p, H.hx, H.hy, H.dD.as<double>(), u, nrhs,
-                    H.rleaf.as<RL>(), st);
-  gemm_batched<RL>(static_cast<GemmDesc<RL>*>(H.gemm_leaf), H.nl, H.ni, nrhs, RL(1), RL(0), st,
-                   sizeof(RL) == 8 ? "gemm_leafinv<f64>" : "gemm_leafinv<f32>",
-                   2.0 * H.nl * (double)H.ni * H.ni * nrhs, (double)H.nl * H.ni * H.ni * sizeof(RL));
-  leaf_flux<RL>(u, H.zleaf.as<RL>(), H.nl, pl.p, pl.q, nrhs, H.hx, H.hy, H.dD.as<double>(),
-                H.dPc2g.as<double>(), H.leaf_off.as<int64_t>(), pl.ext_total,
-                H.hpool.as<double>(), st);
+  for (auto& G : H.lg) {
+    leaf_residual<float>(G.coefp, G.l0, G.nl, G.p, H.hsc.as<double2>(), G.dD->as<double>(),
+                         cp.wptr, cp.wrs, nrhs, G.rleaf->as<float>(), st);
+    gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f, 0.0f,
+                        st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
+                        (double)G.nl * G.ni * G.ni * sizeof(float));
+    leaf_flux<float>(cp.wptr, cp.wrs, G.zleaf->as<float>(), G.l0, G.nl, G.p, G.q, nrhs,
+                     H.hsc.as<double2>(), G.dD->as<double>(), G.dPc2g->as<double>(),
+                     H.leaf_off.as<int64_t>(), H.plan.ext_total, H.hpool.as<double>(), st);
+  }
 }
 
 // Merge part of the upward pass: z = W (h3^b - h3^a), h^tau = [h1^a; h2^b] + C z.
 template <typename R>
-void up_level(hps_handle_s& H, int h, int nrhs) {
-  LevelOps& L = H.levels[h];
+void up_level(hps_handle_s& H, LevelGroup& L, int nrhs) {
   cudaStream_t st = H.stream;
   const Plan& pl = H.plan;
   const int nm = (int)L.boxes.size();
   size_t wse = 0;
   R* ws = split_ws<R>(H, &wse);
-  merge_rhs<R>(L.body, nm, L.max_m, H.hpool.as<double>(), pl.ext_total, nrhs,
-               H.rlev[h]->as<R>(), st);
+  merge_rhs<R>(L.body, nm, L.max_m, H.hpool.as<double>(), pl.ext_total, nrhs, L.rlev->as<R>(),
+               st);
   double flw = 0, flc = 0;
   for (int i = 0; i < nm; ++i) {
     flw += 2.0 * L.hm[i] * (double)L.hm[i] * nrhs;
     flc += 2.0 * L.hne[i] * (double)L.hm[i] * nrhs;
   }
-  gemm_batched<R>(static_cast<GemmDesc<R>*>(H.gemm_w[h]), nm, L.max_m, nrhs, R(1), R(0), st,
+  gemm_batched<R>(static_cast<GemmDesc<R>*>(L.gemm_w), nm, L.max_m, nrhs, R(1), R(0), st,
                   sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flw, 0.0, L.max_m, ws,
                   wse);
-  if (h < pl.height) {  // the root's flux offsets are not needed
-    merge_hpar(L.body, nm, L.max_ne, H.hpool.as<double>(), pl.ext_total, nrhs, st);
-    gemm_batched<R>(static_cast<GemmDesc<R, R, double>*>(H.gemm_hpar[h]), nm, L.max_ne, nrhs,
-                    R(1), R(1), st, sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flc,
-                    0.0, L.max_m, ws, wse);
-  }
+  // parents' flux offsets (a root's are never read; computing them is harmless)
+  merge_hpar(L.body, nm, L.max_ne, H.hpool.as<double>(), pl.ext_total, nrhs, st);
+  gemm_batched<R>(static_cast<GemmDesc<R, R, double>*>(L.gemm_hpar), nm, L.max_ne, nrhs, R(1),
+                  R(1), st, sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flc, 0.0,
+                  L.max_m, ws, wse);
 }
 
-int solve_all(hps_handle_s& H, const double* f_dev, int nrhs, double* u_dev,
-              hps_solve_info* info) {
-  const Plan& pl = H.plan;
+int solve_all(hps_handle_s& H, const CallPtrs& cp, int nrhs, hps_solve_info* info) {
   cudaStream_t st = H.stream;
-  prepare_solve(H, nrhs);
-  solve_root_scatter(f_dev, H.root_from_f.as<int>(), H.nbnd, nrhs, H.uext.as<double>(),
-                     pl.boxes[0].ext_off, pl.ext_total, st);
+  solve_root_scatter(cp.roots, H.nprob, cp.max_nbnd, nrhs, H.uext.as<double>(),
+                     H.plan.ext_total, st);
   downward(H, nrhs, false);
-  if (H.leaf_f64)
-    leaf_out<double>(H, nrhs, u_dev, false);
-  else
-    leaf_out<float>(H, nrhs, u_dev, false);
+  leaf_out(H, cp, nrhs, false);
   ck(cudaGetLastError());
   if (!H.mixed || H.opt.max_refine == 0) return HPS_OK;
   // ---- iterative refinement against the FP64 residual
   double last = 0.0;
   int it = 0;
   for (it = 1; it <= H.opt.max_refine; ++it) {
-    if (H.leaf_f64)
-      leaf_correction_rhs<double>(H, nrhs, u_dev);
-    else
-      leaf_correction_rhs<float>(H, nrhs, u_dev);
-    for (int h = 1; h <= pl.height; ++h) {
-      if (H.levels[h].f64)
-        up_level<double>(H, h, nrhs);
+    leaf_correction_rhs(H, cp, nrhs);
+    for (auto& L : H.lev) {
+      if (L.f64)
+        up_level<double>(H, L, nrhs);
       else
-        up_level<float>(H, h, nrhs);
+        up_level<float>(H, L, nrhs);
     }
-    // the correction has zero Dirichlet data on Gamma
-    ck(cudaMemset2DAsync(H.uext.as<double>() + pl.boxes[0].ext_off, pl.ext_total * sizeof(double),
-                         0, pl.boxes[0].ne * sizeof(double), nrhs, st));
+    // the correction has zero Dirichlet data on every Gamma (roots from f = null)
+    solve_root_scatter(cp.roots + H.nprob, H.nprob, cp.max_nbnd, nrhs, H.uext.as<double>(),
+                       H.plan.ext_total, st);
     downward(H, nrhs, true);
-    ck(cudaMemsetAsync(H.maxabs.p, 0, 2 * sizeof(unsigned long long), st));
-    if (H.leaf_f64)
-      leaf_out<double>(H, nrhs, u_dev, true);
-    else
-      leaf_out<float>(H, nrhs, u_dev, true);
+    const size_t mb = 2 * (size_t)H.nprob * sizeof(unsigned long long);
+    ck(cudaMemsetAsync(H.maxabs.p, 0, mb, st));
+    leaf_out(H, cp, nrhs, true);
     ck(cudaGetLastError());
-    ck(cudaMemcpyAsync(H.h_maxabs, H.maxabs.p, 2 * sizeof(unsigned long long),
-                       cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(H.h_maxabs, H.maxabs.p, mb, cudaMemcpyDeviceToHost, st));
     ck(cudaStreamSynchronize(st));
-    double dmax, umax;
-    std::memcpy(&dmax, &H.h_maxabs[0], sizeof(double));
-    std::memcpy(&umax, &H.h_maxabs[1], sizeof(double));
+    // the largest relative update over the problems of the batch
     const double prev = last;
-    last = umax > 0 ? dmax / umax : dmax;
+    last = 0.0;
+    for (int k = 0; k < H.nprob; ++k) {
+      double dmax, umax;
+      std::memcpy(&dmax, &H.h_maxabs[2 * k], sizeof(double));
+      std::memcpy(&umax, &H.h_maxabs[2 * k + 1], sizeof(double));
+      const double rel = umax > 0 ? dmax / umax : dmax;
+      last = (rel == rel) ? std::max(last, rel) : rel;
+      if (!(last == last)) break;
+    }
     if (!(last <= 1.0)) break;  // NaN or divergence
     if (last <= H.opt.refine_tol) break;
+    // the error left after this update is about rho * last, rho = last / prev
+    // the observed contraction: stop when that is below the tolerance
+    if (it >= 2 && last * (last / prev) <= 0.1 * H.opt.refine_tol) {
+      last = last * (last / prev);
+      break;
+    }
     // stagnation: the update no longer shrinks, i.e. the iterate has reached
     // the accuracy the FP64 residual can resolve for this conditioning
     if (it >= 3 && last > 0.5 * prev) break;
@@ -833,6 +923,162 @@ int solve_all(hps_handle_s& H, const double* f_dev, int nrhs, double* u_dev,
     return HPS_ENOTCONVERGED;
   }
   return HPS_OK;
+}
+
+// Upload the per-call root descriptors (with f, then with zeros) and the
+// per-leaf output pointers.  f[k] / u[k] are device pointers.
+CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, int nrhs) {
+  const Plan& pl = H.plan;
+  const int nl = pl.n_leaves();
+  H.call_st.begin(stage_bytes<RootDesc>(2 * H.nprob) + stage_bytes<double*>(nl) +
+                      stage_bytes<int64_t>(nl) + 1024,
+                  H.stream);
+  std::vector<RootDesc> rd(2 * H.nprob);
+  std::vector<double*> wp(nl);
+  std::vector<int64_t> wr(nl);
+  CallPtrs cp;
+  for (int k = 0; k < H.nprob; ++k) {
+    const ProbInfo& pi = pl.probs[k];
+    RootDesc r;
+    r.f = f[k];
+    r.rff = H.root_from_f.as<int>() + pi.rff_off;
+    r.root_off = pl.boxes[pi.root].ext_off;
+    r.nbnd = pi.nbnd;
+    rd[k] = r;
+    r.f = nullptr;
+    rd[H.nprob + k] = r;
+    cp.max_nbnd = std::max(cp.max_nbnd, pi.nbnd);
+    const int pp = pi.s.p * pi.s.p;
+    for (int j = 0; j < pi.nl; ++j) {
+      wp[pi.leaf0 + j] = u[k] + (size_t)j * pp;
+      wr[pi.leaf0 + j] = (int64_t)pi.nl * pp;
+    }
+  }
+  cp.roots = H.call_st.push(rd, H.stream);
+  cp.wptr = H.call_st.push(wp, H.stream);
+  cp.wrs = H.call_st.push(wr, H.stream);
+  return cp;
+}
+
+// hps_solve_batch body: device or host pointers per problem.
+int solve_entry(hps_handle_s& H, const double* const* f, int nrhs, double* const* u,
+                int device_ptrs, hps_solve_info* info) {
+  const Plan& pl = H.plan;
+  cudaStream_t st = H.stream;
+  prepare_solve(H, nrhs);
+  std::vector<const double*> fd(H.nprob);
+  std::vector<double*> ud(H.nprob);
+  if (device_ptrs) {
+    for (int k = 0; k < H.nprob; ++k) {
+      fd[k] = f[k];
+      ud[k] = u[k];
+    }
+  } else {
+    size_t fb = 0, ub = 0;
+    for (int k = 0; k < H.nprob; ++k) {
+      fb += (size_t)nrhs * pl.probs[k].nbnd;
+      ub += (size_t)nrhs * pl.probs[k].nl * pl.probs[k].s.p * pl.probs[k].s.p;
+    }
+    if (H.fstage.bytes < fb * sizeof(double)) H.fstage.alloc(fb * sizeof(double), st);
+    if (H.ustage.bytes < ub * sizeof(double)) H.ustage.alloc(ub * sizeof(double), st);
+    size_t fo = 0, uo = 0;
+    for (int k = 0; k < H.nprob; ++k) {
+      const size_t nf = (size_t)nrhs * pl.probs[k].nbnd;
+      const size_t nu = (size_t)nrhs * pl.probs[k].nl * pl.probs[k].s.p * pl.probs[k].s.p;
+      fd[k] = H.fstage.as<double>() + fo;
+      ud[k] = H.ustage.as<double>() + uo;
+      ck(cudaMemcpyAsync(const_cast<double*>(fd[k]), f[k], nf * sizeof(double),
+                         cudaMemcpyHostToDevice, st));
+      fo += nf;
+      uo += nu;
+    }
+  }
+  CallPtrs cp = stage_call(H, fd.data(), ud.data(), nrhs);
+  int rc = solve_all(H, cp, nrhs, info);
+  if (!device_ptrs)
+    for (int k = 0; k < H.nprob; ++k) {
+      const size_t nu = (size_t)nrhs * pl.probs[k].nl * pl.probs[k].s.p * pl.probs[k].s.p;
+      ck(cudaMemcpyAsync(u[k], ud[k], nu * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+  ck(cudaStreamSynchronize(st));
+  return rc;
+}
+
+int build_entry(const hps_problem* probs, int nprob, const hps_options* opt_in, hps_handle* out) {
+  if (!out || !probs || nprob < 1) return HPS_EINVAL;
+  *out = nullptr;
+  std::vector<ProblemSpec> specs(nprob);
+  std::vector<const double*> coef(6 * (size_t)nprob);
+  for (int k = 0; k < nprob; ++k) {
+    const hps_problem& P = probs[k];
+    int v = validate(P.d, P.nx, P.ny, P.p, P.q);
+    if (v != HPS_OK) return v;
+    specs[k] = {P.d.x0, P.d.x1, P.d.y0, P.d.y1, P.nx, P.ny, P.p, P.q};
+    const double* c[6] = {P.c11, P.c12, P.c22, P.c1, P.c2, P.c};
+    for (int i = 0; i < 6; ++i) coef[6 * k + i] = c[i];
+  }
+  hps_options opt;
+  hps_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.precision != HPS_FP64 && opt.precision != HPS_MIXED) return HPS_EINVAL;
+  if (opt.precision == HPS_MIXED &&
+      (!(opt.refine_tol > 0) || opt.max_refine < 0 || opt.fp64_top_levels < 0))
+    return HPS_EINVAL;
+  g_last_error.clear();
+  hps_handle_s* H = nullptr;
+  try {
+    H = new hps_handle_s();
+    H->opt = opt;
+    H->mixed = opt.precision == HPS_MIXED;
+    H->nprob = nprob;
+    H->plan = make_forest(specs);
+    if (opt.stream) {
+      H->stream = (cudaStream_t)opt.stream;
+    } else {
+      ck(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
+      H->own_stream = true;
+    }
+    build_all(*H, coef, opt.device_ptrs != 0);
+    *out = H;
+    return HPS_OK;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    hps_free(H);
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  } catch (int) {
+    hps_free(H);
+    return HPS_ESINGULAR;
+  } catch (std::bad_alloc&) {
+    hps_free(H);
+    return HPS_ENOMEM;
+  } catch (...) {
+    hps_free(H);
+    return HPS_EDEVICE;
+  }
+}
+
+void clear_info(hps_solve_info* info) {
+  if (info) {
+    info->status = HPS_OK;
+    info->iterations = 0;
+    info->last_update = 0.0;
+    info->bad_box = -1;
+  }
+}
+
+int solve_guarded(hps_handle h, const double* const* f, int nrhs, double* const* u,
+                  int device_ptrs, hps_solve_info* info) {
+  try {
+    return solve_entry(*h, f, nrhs, u, device_ptrs, info);
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    if (info) info->status = HPS_EDEVICE;
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  } catch (std::bad_alloc&) {
+    return HPS_ENOMEM;
+  } catch (...) {
+    return HPS_EDEVICE;
+  }
 }
 
 }  // namespace
@@ -868,102 +1114,41 @@ int hps_boundary_nodes_grid(hps_domain d, int nx, int ny, int q, double* xy) {
 
 int hps_build(hps_domain d, int nx, int ny, int p, int q, const double* c11, const double* c12,
               const double* c22, const double* c1, const double* c2, const double* c,
-              const hps_options* opt_in, hps_handle* out) {
+              const hps_options* opt, hps_handle* out) {
+  hps_problem P;
+  P.d = d;
+  P.nx = nx;
+  P.ny = ny;
+  P.p = p;
+  P.q = q;
+  P.c11 = c11;
+  P.c12 = c12;
+  P.c22 = c22;
+  P.c1 = c1;
+  P.c2 = c2;
+  P.c = c;
   if (!out) return HPS_EINVAL;
-  *out = nullptr;
-  int v = validate(d, nx, ny, p, q);
-  if (v != HPS_OK) return v;
-  hps_options opt;
-  hps_default_options(&opt);
-  if (opt_in) opt = *opt_in;
-  if (opt.precision != HPS_FP64 && opt.precision != HPS_MIXED) return HPS_EINVAL;
-  if (opt.precision == HPS_MIXED &&
-      (!(opt.refine_tol > 0) || opt.max_refine < 0 || opt.fp64_top_levels < 0))
-    return HPS_EINVAL;
-  g_last_error.clear();
-  hps_handle_s* H = nullptr;
-  try {
-    H = new hps_handle_s();
-    H->opt = opt;
-    H->mixed = opt.precision == HPS_MIXED;
-    H->plan = make_plan(d.x0, d.x1, d.y0, d.y1, nx, ny, p, q);
-    H->consts = make_consts(p, q);
-    H->ni = (p - 2) * (p - 2);
-    H->nq = 4 * q;
-    H->nl = nx * ny;
-    H->nbnd = 2 * (nx + ny) * q;
-    H->hx = (d.x1 - d.x0) / nx;
-    H->hy = (d.y1 - d.y0) / ny;
-    if (opt.stream) {
-      H->stream = (cudaStream_t)opt.stream;
-    } else {
-      ck(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
-      H->own_stream = true;
-    }
-    const double* coef[6] = {c11, c12, c22, c1, c2, c};
-    build_all(*H, coef, opt.device_ptrs != 0);
-    *out = H;
-    return HPS_OK;
-  } catch (CudaError& e) {
-    cudaGetLastError();
-    hps_free(H);
-    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
-  } catch (int) {
-    hps_free(H);
-    return HPS_ESINGULAR;
-  } catch (std::bad_alloc&) {
-    hps_free(H);
-    return HPS_ENOMEM;
-  } catch (...) {
-    hps_free(H);
-    return HPS_EDEVICE;
-  }
+  return build_entry(&P, 1, opt, out);
+}
+
+int hps_build_batch(const hps_problem* probs, int nprob, const hps_options* opt,
+                    hps_handle* out) {
+  return build_entry(probs, nprob, opt, out);
 }
 
 int hps_boundary_nodes(hps_handle h, double* xy) {
   if (!h || !xy) return HPS_EINVAL;
-  const Plan& pl = h->plan;
-  boundary_node_coords(pl.x0, pl.x1, pl.y0, pl.y1, pl.nx, pl.ny, pl.q, xy);
+  const ProblemSpec& s = h->plan.probs[0].s;
+  boundary_node_coords(s.x0, s.x1, s.y0, s.y1, s.nx, s.ny, s.q, xy);
   return HPS_OK;
 }
 
 int hps_solve_ex(hps_handle h, const double* f, int nrhs, double* u, int device_ptrs,
                  hps_solve_info* info) {
-  if (info) {
-    info->status = HPS_OK;
-    info->iterations = 0;
-    info->last_update = 0.0;
-    info->bad_box = -1;
-  }
-  if (!h || !f || !u || nrhs < 1) return HPS_EINVAL;
+  clear_info(info);
+  if (!h || !f || !u || nrhs < 1 || h->nprob != 1) return HPS_EINVAL;
   g_last_error.clear();
-  try {
-    hps_handle_s& H = *h;
-    cudaStream_t st = H.stream;
-    const size_t fb = (size_t)nrhs * H.nbnd * sizeof(double);
-    const size_t ub = (size_t)nrhs * H.nl * H.plan.p * H.plan.p * sizeof(double);
-    const double* fd = f;
-    double* ud = u;
-    if (!device_ptrs) {
-      if (H.fstage.bytes < fb) H.fstage.alloc(fb, st);
-      if (H.ustage.bytes < ub) H.ustage.alloc(ub, st);
-      ck(cudaMemcpyAsync(H.fstage.p, f, fb, cudaMemcpyHostToDevice, st));
-      fd = H.fstage.as<double>();
-      ud = H.ustage.as<double>();
-    }
-    int rc = solve_all(H, fd, nrhs, ud, info);
-    if (!device_ptrs) ck(cudaMemcpyAsync(u, ud, ub, cudaMemcpyDeviceToHost, st));
-    ck(cudaStreamSynchronize(st));
-    return rc;
-  } catch (CudaError& e) {
-    cudaGetLastError();
-    if (info) info->status = HPS_EDEVICE;
-    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
-  } catch (std::bad_alloc&) {
-    return HPS_ENOMEM;
-  } catch (...) {
-    return HPS_EDEVICE;
-  }
+  return solve_guarded(h, &f, nrhs, &u, device_ptrs, info);
 }
 
 int hps_solve(hps_handle h, const double* f, int nrhs, double* u, hps_solve_info* info) {
@@ -971,25 +1156,40 @@ int hps_solve(hps_handle h, const double* f, int nrhs, double* u, hps_solve_info
   return hps_solve_ex(h, f, nrhs, u, h->opt.device_ptrs, info);
 }
 
+int hps_solve_batch(hps_handle h, const double* const* f, int nrhs, double* const* u,
+                    hps_solve_info* info) {
+  clear_info(info);
+  if (!h || !f || !u || nrhs < 1) return HPS_EINVAL;
+  for (int k = 0; k < h->nprob; ++k)
+    if (!f[k] || !u[k]) return HPS_EINVAL;
+  g_last_error.clear();
+  return solve_guarded(h, f, nrhs, u, h->opt.device_ptrs, info);
+}
+
 int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_t* device_bytes) {
   if (!h) return HPS_EINVAL;
-  if (n_leaves) *n_leaves = h->nl;
-  if (p) *p = h->plan.p;
-  if (q) *q = h->plan.q;
-  if (nbnd) *nbnd = h->nbnd;
+  if (n_leaves) *n_leaves = h->plan.n_leaves();
+  if (p) *p = h->plan.probs[0].s.p;
+  if (q) *q = h->plan.probs[0].s.q;
+  if (nbnd) {
+    int64_t b = 0;
+    for (const auto& pi : h->plan.probs) b += pi.nbnd;
+    *nbnd = b;
+  }
   if (device_bytes) {
     int64_t b = 0;
-    for (const PoolBuf* x : {&h->Y, &h->coef, &h->maps, &h->uext, &h->u3, &h->hpool, &h->rleaf,
-                             &h->zleaf, &h->fstage, &h->ustage, &h->split_ws, &h->keep.dev,
-                             &h->solve_st.dev})
+    for (const PoolBuf* x : {&h->coef, &h->maps, &h->uext, &h->u3, &h->hpool, &h->fstage,
+                             &h->ustage, &h->split_ws, &h->keep.dev, &h->solve_st.dev})
       b += (int64_t)x->bytes;
-    for (const auto& L : h->levels) b += (int64_t)(L.S->bytes + L.Cw->bytes);
-    for (const auto& z : h->zlev) b += (int64_t)z->bytes;
-    for (const auto& r : h->rlev) b += (int64_t)r->bytes;
+    for (const auto& G : h->lg) b += (int64_t)(G.Y->bytes + G.rleaf->bytes + G.zleaf->bytes);
+    for (const auto& L : h->lev)
+      b += (int64_t)(L.S->bytes + L.Cw->bytes + L.rlev->bytes + L.zlev->bytes);
     *device_bytes = b;
   }
   return HPS_OK;
 }
+
+int hps_batch_size(hps_handle h) { return h ? h->nprob : 0; }
 
 int hps_free(hps_handle h) {
   if (!h) return HPS_OK;
@@ -1060,7 +1260,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double* u) {
-  if (!h || !f || !u || nrhs < 1) return HPS_EINVAL;
+  if (!h || !f || !u || nrhs < 1 || h->nprob != 1) return HPS_EINVAL;
   g_last_error.clear();
   hps_handle_s& H = *h;
   if (H.mixed) {
@@ -1068,12 +1268,14 @@ extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double*
     return HPS_EINVAL;
   }
   const Plan& pl = H.plan;
-  // carve the static array: exterior-value pool, u3 pool, GEMM descriptors
+  const ProbInfo& pi = pl.probs[0];
+  const int nl = pl.n_leaves();
+  // carve the static array: exterior-value pool, u3 pool, descriptors
   const size_t b_uext = align256((size_t)nrhs * pl.ext_total * sizeof(double));
   const size_t b_u3 = align256((size_t)nrhs * std::max<int64_t>(H.u3_total, 1) * sizeof(double));
-  size_t b_desc = 0;
-  for (int hh = 1; hh <= pl.height; ++hh)
-    b_desc += align256(H.levels[hh].boxes.size() * sizeof(GemmDesc<double>));
+  size_t b_desc = align256(sizeof(RootDesc)) + align256((size_t)nl * sizeof(double*)) +
+                  align256((size_t)nl * sizeof(int64_t));
+  for (auto& L : H.lev) b_desc += align256(L.boxes.size() * sizeof(GemmDesc<double>));
   if (b_uext + b_u3 + b_desc > kStaticScratchBytes || b_desc > kStaticHostBytes) {
     g_last_error = "hps_solve_static: needs " + std::to_string(b_uext + b_u3 + b_desc) +
                    " bytes of scratch, the static array holds " +
@@ -1098,13 +1300,38 @@ extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double*
     double* u3 = reinterpret_cast<double*>(base + b_uext);
     unsigned char* dd = base + b_uext + b_u3;
     cudaStream_t st = H.stream;
-    // descriptors of the downward GEMMs, staged in static host memory; the
-    // earlier call's copies have completed (each call ends synchronised)
-    GemmDesc<double>* dptr[128] = {};  // tree heights stay far below 128 (nx * ny <= 2^26)
-    if (pl.height >= 128) return HPS_EINVAL;
+    // descriptors staged in static host memory; the earlier call's copies have
+    // completed (each call ends synchronised)
     size_t off = 0;
-    for (int hh = 1; hh <= pl.height; ++hh) {
-      LevelOps& L = H.levels[hh];
+    auto stage = [&](const void* src, size_t n) {
+      if (src != g_static_host + off) std::memcpy(g_static_host + off, src, n);
+      ck(cudaMemcpyAsync(dd + off, g_static_host + off, n, cudaMemcpyHostToDevice, st));
+      void* dst = dd + off;
+      off += align256(n);
+      return dst;
+    };
+    RootDesc rd;
+    rd.f = f;
+    rd.rff = H.root_from_f.as<int>() + pi.rff_off;
+    rd.root_off = pl.boxes[pi.root].ext_off;
+    rd.nbnd = pi.nbnd;
+    RootDesc* droot = static_cast<RootDesc*>(stage(&rd, sizeof(rd)));
+    // per-leaf output pointers, written straight into the staging block
+    {
+      const int pp = pi.s.p * pi.s.p;
+      double** wp = reinterpret_cast<double**>(g_static_host + off);
+      for (int j = 0; j < nl; ++j) wp[j] = u + (size_t)j * pp;
+    }
+    double* const* dwp = static_cast<double* const*>(stage(g_static_host + off, nl * sizeof(double*)));
+    {
+      int64_t* wr = reinterpret_cast<int64_t*>(g_static_host + off);
+      for (int j = 0; j < nl; ++j) wr[j] = (int64_t)nl * pi.s.p * pi.s.p;
+    }
+    const int64_t* dwr = static_cast<const int64_t*>(stage(g_static_host + off, nl * sizeof(int64_t)));
+    GemmDesc<double>* dptr[256] = {};
+    if (H.lev.size() > 256) return HPS_EINVAL;
+    for (size_t li = 0; li < H.lev.size(); ++li) {
+      LevelGroup& L = H.lev[li];
       GemmDesc<double>* hs = reinterpret_cast<GemmDesc<double>*>(g_static_host + off);
       for (size_t i = 0; i < L.boxes.size(); ++i) {
         const int b = L.boxes[i];
@@ -1120,25 +1347,23 @@ extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double*
         g.ldb = (int)pl.ext_total;
         g.ldc = (int)H.u3_total;
       }
-      const size_t n = L.boxes.size() * sizeof(GemmDesc<double>);
-      ck(cudaMemcpyAsync(dd + off, g_static_host + off, n, cudaMemcpyHostToDevice, st));
-      dptr[hh] = reinterpret_cast<GemmDesc<double>*>(dd + off);
-      off += align256(n);
+      dptr[li] = static_cast<GemmDesc<double>*>(
+          stage(g_static_host + off, L.boxes.size() * sizeof(GemmDesc<double>)));
     }
     // nothing in the array has to start at zero: every exterior value and every
     // u3 entry is written (root scatter, GEMMs with beta = 0, child scatters)
     // before it is read
-    solve_root_scatter(f, H.root_from_f.as<int>(), H.nbnd, nrhs, uext, pl.boxes[0].ext_off,
-                       pl.ext_total, st);
-    for (int hh = pl.height; hh >= 1; --hh) {
-      LevelOps& L = H.levels[hh];
+    solve_root_scatter(droot, 1, pi.nbnd, nrhs, uext, pl.ext_total, st);
+    for (int li = (int)H.lev.size() - 1; li >= 0; --li) {
+      LevelGroup& L = H.lev[li];
       const int nm = (int)L.boxes.size();
-      gemm_batched<double>(dptr[hh], nm, L.max_m, nrhs, 1.0, 0.0, st, "gemm_solve_static<f64>",
+      gemm_batched<double>(dptr[li], nm, L.max_m, nrhs, 1.0, 0.0, st, "gemm_solve_static<f64>",
                            0.0, 0.0);
       solve_child_scatter(L.scatter, nm, L.max_nanb, u3, H.u3_total, uext, pl.ext_total, nrhs, st);
     }
-    leaf_post<double>(H.Y.as<double>(), H.ys, uext, H.leaf_off.as<int64_t>(), pl.ext_total, H.nl,
-                      pl.p, pl.q, nrhs, H.dPg2c.as<double>(), u, st);
+    for (auto& G : H.lg)
+      leaf_post<double>(G.Y->as<double>(), G.ys, G.l0, uext, H.leaf_off.as<int64_t>(),
+                        pl.ext_total, G.nl, G.p, G.q, nrhs, G.dPg2c->as<double>(), dwp, dwr, st);
     ck(cudaGetLastError());
     ck(cudaStreamSynchronize(st));
     return HPS_OK;

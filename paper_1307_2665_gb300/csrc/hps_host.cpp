@@ -197,65 +197,92 @@ MergeShape make_shape(int split, int abx, int aby, int bbx, int bby, int q) {
 
 }  // namespace
 
-Plan make_plan(double x0, double x1, double y0, double y1, int nx, int ny, int p, int q) {
+Plan make_forest(const std::vector<ProblemSpec>& specs) {
   Plan pl;
-  pl.x0 = x0;
-  pl.x1 = x1;
-  pl.y0 = y0;
-  pl.y1 = y1;
-  pl.nx = nx;
-  pl.ny = ny;
-  pl.p = p;
-  pl.q = q;
-  pl.leaf_box.assign((size_t)nx * ny, -1);
-  std::map<std::tuple<int, int, int, int, int>, int> shape_ids;
-  // Breadth-first construction keeps parent index < child index (Section 2).
-  Box root;
-  root.ix0 = 0;
-  root.iy0 = 0;
-  root.bx = nx;
-  root.by = ny;
-  pl.boxes.push_back(root);
-  for (size_t b = 0; b < pl.boxes.size(); ++b) {
-    Box cur = pl.boxes[b];
-    if (cur.bx == 1 && cur.by == 1) {
-      pl.boxes[b].leaf = cur.iy0 * nx + cur.ix0;
-      pl.leaf_box[pl.boxes[b].leaf] = (int)b;
-      continue;
+  std::map<std::tuple<int, int, int, int, int, int>, int> shape_ids;
+  int leaf0 = 0;
+  int64_t rff = 0;
+  for (size_t k = 0; k < specs.size(); ++k) {
+    const ProblemSpec& sp = specs[k];
+    ProbInfo pi;
+    pi.s = sp;
+    pi.leaf0 = leaf0;
+    pi.nl = sp.nx * sp.ny;
+    pi.nbnd = 2 * (sp.nx + sp.ny) * sp.q;
+    pi.hx = (sp.x1 - sp.x0) / sp.nx;
+    pi.hy = (sp.y1 - sp.y0) / sp.ny;
+    pi.rff_off = rff;
+    pi.root = (int)pl.boxes.size();
+    leaf0 += pi.nl;
+    rff += pi.nbnd;
+    pl.leaf_box.resize(leaf0, -1);
+    pl.leaf_prob.resize(leaf0, (int)k);
+    // breadth-first construction keeps parent index < child index (Section 2)
+    Box root;
+    root.ix0 = 0;
+    root.iy0 = 0;
+    root.bx = sp.nx;
+    root.by = sp.ny;
+    root.prob = (int)k;
+    pl.boxes.push_back(root);
+    for (size_t b = pi.root; b < pl.boxes.size(); ++b) {
+      Box cur = pl.boxes[b];
+      if (cur.bx == 1 && cur.by == 1) {
+        pl.boxes[b].leaf = pi.leaf0 + cur.iy0 * sp.nx + cur.ix0;
+        pl.leaf_box[pl.boxes[b].leaf] = (int)b;
+        continue;
+      }
+      Box a, c;
+      int split = (cur.bx >= cur.by) ? 0 : 1;  // split the longer side; ties split x
+      if (split == 0) {
+        int h = cur.bx / 2;
+        a = {cur.ix0, cur.iy0, h, cur.by};
+        c = {cur.ix0 + h, cur.iy0, cur.bx - h, cur.by};
+      } else {
+        int h = cur.by / 2;
+        a = {cur.ix0, cur.iy0, cur.bx, h};
+        c = {cur.ix0, cur.iy0 + h, cur.bx, cur.by - h};
+      }
+      a.parent = c.parent = (int)b;
+      a.prob = c.prob = (int)k;
+      pl.boxes[b].split = split;
+      pl.boxes[b].child[0] = (int)pl.boxes.size();
+      pl.boxes.push_back(a);
+      pl.boxes[b].child[1] = (int)pl.boxes.size();
+      pl.boxes.push_back(c);
     }
-    Box a, c;
-    int split = (cur.bx >= cur.by) ? 0 : 1;  // split the longer side; ties split x
-    if (split == 0) {
-      int h = cur.bx / 2;
-      a = {cur.ix0, cur.iy0, h, cur.by};
-      c = {cur.ix0 + h, cur.iy0, cur.bx - h, cur.by};
-    } else {
-      int h = cur.by / 2;
-      a = {cur.ix0, cur.iy0, cur.bx, h};
-      c = {cur.ix0, cur.iy0 + h, cur.bx, cur.by - h};
+    // heights bottom-up within this problem (children have larger indices)
+    for (int b = (int)pl.boxes.size() - 1; b >= pi.root; --b) {
+      Box& x = pl.boxes[b];
+      x.ne = 2 * (x.bx + x.by) * sp.q;
+      if (x.child[0] >= 0)
+        x.height = 1 + std::max(pl.boxes[x.child[0]].height, pl.boxes[x.child[1]].height);
     }
-    a.parent = c.parent = (int)b;
-    pl.boxes[b].split = split;
-    pl.boxes[b].child[0] = (int)pl.boxes.size();
-    pl.boxes.push_back(a);
-    pl.boxes[b].child[1] = (int)pl.boxes.size();
-    pl.boxes.push_back(c);
+    pi.height = pl.boxes[pi.root].height;
+    pl.height = std::max(pl.height, pi.height);
+    // root exterior (S, E, N, W increasing) from f (counter-clockwise from (x0,y0))
+    std::vector<int> m(pi.nbnd);
+    Sides R(sp.nx, sp.ny, sp.q);
+    const int nx = sp.nx, ny = sp.ny, q = sp.q;
+    for (int kk = 0; kk < nx * q; ++kk) {
+      m[R.S + kk] = kk;
+      m[R.N + kk] = (nx + ny) * q + (nx * q - 1 - kk);
+    }
+    for (int kk = 0; kk < ny * q; ++kk) {
+      m[R.E + kk] = nx * q + kk;
+      m[R.W + kk] = (2 * nx + ny) * q + (ny * q - 1 - kk);
+    }
+    pl.root_from_f.insert(pl.root_from_f.end(), m.begin(), m.end());
+    pl.probs.push_back(pi);
   }
-  // heights bottom-up (children have larger indices)
-  for (int b = (int)pl.boxes.size() - 1; b >= 0; --b) {
-    Box& x = pl.boxes[b];
-    x.ne = 2 * (x.bx + x.by) * q;
-    if (x.child[0] >= 0)
-      x.height = 1 + std::max(pl.boxes[x.child[0]].height, pl.boxes[x.child[1]].height);
-  }
-  pl.height = pl.boxes[0].height;
   pl.levels.assign(pl.height + 1, {});
   for (int b = 0; b < (int)pl.boxes.size(); ++b) {
     Box& x = pl.boxes[b];
     if (x.child[0] < 0) continue;
     const Box& A = pl.boxes[x.child[0]];
     const Box& B = pl.boxes[x.child[1]];
-    auto key = std::make_tuple(x.split, A.bx, A.by, B.bx, B.by);
+    const int q = specs[x.prob].q;
+    auto key = std::make_tuple(x.split, A.bx, A.by, B.bx, B.by, q);
     auto it = shape_ids.find(key);
     if (it == shape_ids.end()) {
       pl.shapes.push_back(make_shape(x.split, A.bx, A.by, B.bx, B.by, q));
@@ -270,18 +297,6 @@ Plan make_plan(double x0, double x1, double y0, double y1, int nx, int ny, int p
     off += x.ne;
   }
   pl.ext_total = off;
-  // root exterior (S, E, N, W increasing) from f (counter-clockwise from (x0,y0))
-  const int nb = 2 * (nx + ny) * q;
-  pl.root_from_f.assign(nb, 0);
-  Sides R(nx, ny, q);
-  for (int k = 0; k < nx * q; ++k) {
-    pl.root_from_f[R.S + k] = k;
-    pl.root_from_f[R.N + k] = (nx + ny) * q + (nx * q - 1 - k);
-  }
-  for (int k = 0; k < ny * q; ++k) {
-    pl.root_from_f[R.E + k] = nx * q + k;
-    pl.root_from_f[R.W + k] = (2 * nx + ny) * q + (ny * q - 1 - k);
-  }
   return pl;
 }
 

@@ -34,6 +34,24 @@ struct Consts {
 Consts make_consts(int p, int q);
 
 // --------------------------------------------------------------------- plan
+// One plan may hold several independent problems (a forest): every problem
+// has its own tree, and the leaves / merges of all problems at the same height
+// are processed by the same batched launches.
+struct ProblemSpec {
+  double x0, x1, y0, y1;
+  int nx, ny, p, q;
+};
+
+struct ProbInfo {
+  ProblemSpec s;
+  int root = 0;           // box index of the problem's root
+  int leaf0 = 0, nl = 0;  // global leaf range (leaf l = leaf0 + iy*nx + ix)
+  int height = 0;
+  int nbnd = 0;
+  int64_t rff_off = 0;    // offset of this problem's map in root_from_f
+  double hx = 0, hy = 0;
+};
+
 struct Box {
   int ix0, iy0, bx, by;  // leaf extent
   int parent = -1;
@@ -41,13 +59,14 @@ struct Box {
   int split = -1;        // 0: children share a vertical edge (west alpha, east beta)
                          // 1: children share a horizontal edge (south alpha, north beta)
   int height = 0;        // 0 for a leaf
-  int leaf = -1;         // leaf index l = iy*nx + ix for a leaf box
+  int leaf = -1;         // global leaf index for a leaf box
+  int prob = 0;          // problem this box belongs to
   int ne = 0;            // exterior size 2*(bx+by)*q
   int shape = -1;        // merge shape index (parents only)
   int64_t ext_off = 0;   // offset (in nodes) of this box in the exterior-value pool
 };
 
-// Geometry of one merge, shared by all merges with equal child extents.
+// Geometry of one merge, shared by all merges with equal child extents and q.
 struct MergeShape {
   int split, m, ne, na, nb;  // |J3|, parent / alpha / beta exterior sizes
   int j3a, j3b;              // first J3 position in alpha's / beta's exterior
@@ -57,17 +76,18 @@ struct MergeShape {
 };
 
 struct Plan {
-  double x0, x1, y0, y1;
-  int nx, ny, p, q;
-  std::vector<Box> boxes;           // boxes[0] is the root
-  std::vector<int> leaf_box;        // leaf l -> box
+  std::vector<ProbInfo> probs;
+  std::vector<Box> boxes;
+  std::vector<int> leaf_box;        // global leaf -> box
+  std::vector<int> leaf_prob;       // global leaf -> problem
   std::vector<MergeShape> shapes;
-  std::vector<std::vector<int>> levels;  // levels[h] (h >= 1): parent boxes of height h
-  int height = 0;                   // root height
+  std::vector<std::vector<int>> levels;  // levels[h] (h >= 1): parent boxes of height h, all problems
+  int height = 0;                   // largest root height
   int64_t ext_total = 0;            // sum of ne over boxes
-  std::vector<int> root_from_f;     // root exterior position -> index into f
+  std::vector<int> root_from_f;     // per problem: root exterior position -> index into its f
+  int n_leaves() const { return (int)leaf_box.size(); }
 };
-Plan make_plan(double x0, double x1, double y0, double y1, int nx, int ny, int p, int q);
+Plan make_forest(const std::vector<ProblemSpec>& specs);
 
 void cheb_node_coords(double x0, double x1, double y0, double y1, int nx, int ny, int p,
                       double* xy);

@@ -80,38 +80,50 @@ template <typename R>
 void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrhs, int mode,
                       int* d_status, cudaStream_t st, const int* h_m, const int* h_nrhs);
 // name / flops / bytes: launch accounting (algorithmic work of this launch).
-// ws / ws_elems (optional): scratch of element type R; when the launch would
-// occupy few SMs and K is long, the K range is split across CTAs, partial
-// products go to ws and a second kernel sums them in a fixed order (so results
-// do not depend on the split or on other launches).  max_K: largest K.
+// ws / ws_elems (optional): scratch of element type R.  With a scratch, a
+// launch whose largest K exceeds kSplitK splits K into chunks of kSplitK across
+// CTAs, writes the partial products to ws and sums them in a fixed order; the
+// split of a product depends only on its own K, so its result does not depend
+// on what else the launch holds.  Needs nd * ceil(max_K / kSplitK) * max_M *
+// max_N elements (split_ws_elems); with less, the launch does not split.
+constexpr int kSplitK = 512;
+inline size_t split_ws_elems(int nd, int max_M, int max_N, int max_K) {
+  return max_K > kSplitK ? (size_t)nd * ((max_K + kSplitK - 1) / kSplitK) * max_M * max_N : 0;
+}
 template <typename R, typename TA, typename TB, typename TC>
 void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
                   R beta, cudaStream_t st, const char* name, double flops, double bytes,
                   int max_K = 0, R* ws = nullptr, size_t ws_elems = 0);
 
 // ---- leaf kernels (hps_leaf.cu)
-// Y of leaf l starts at Y + l*ys (ni x 4q, ld ni); with_identity also writes
-// an ni x ni identity after it so that the leaf solve returns A_ii^{-1} as well.
+// Leaf kernels run on a group of leaves with one (p, q): group-local leaf j is
+// global leaf l0 + j.  Per global leaf: hsc[l] = (2/hx, 2/hy) of its problem;
+// wptr[l] / wrs[l] = base pointer and right-hand-side stride of its p x p block
+// in the caller's u array.  Y of group leaf j starts at Y + j*ys (ni x 4q, ld
+// ni); with_identity also writes an ni x ni identity after it, so that the leaf
+// solve returns A_ii^{-1} as well.  Coefficient arrays start at the group's first leaf (group-local index j).
 template <typename R>
-void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double hx, double hy,
-                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, int64_t ys,
-                   int with_identity, cudaStream_t st);
+void leaf_assemble(const double* const* coef, int l0, int nleaves, int p, int q,
+                   const double2* hsc, const double* d_D, const double* d_Pg2c, R* Aii, R* Y,
+                   int64_t ys, int with_identity, cudaStream_t st);
 template <typename R>
-void leaf_dtn(const R* Y, int64_t ys, int nleaves, int p, int q, double hx, double hy,
+void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2* hsc,
               const double* d_D, const double* d_Pg2c, const double* d_Pc2g, R* T,
               cudaStream_t st);
 template <typename R>
-void leaf_post(const R* Y, int64_t ys, const double* uext, const int64_t* leaf_ext_off,
+void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
-               double* u, cudaStream_t st, const R* z = nullptr, int accumulate = 0,
-               unsigned long long* maxabs = nullptr);
+               double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z = nullptr,
+               int accumulate = 0, unsigned long long* maxabs = nullptr,
+               const int* leaf_prob = nullptr);
 template <typename R>
-void leaf_residual(const double* const* coef, int nl, int p, double hx, double hy,
-                   const double* d_D, const double* w, int nrhs, R* rbuf, cudaStream_t st);
+void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
+                   const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
+                   cudaStream_t st);
 template <typename R>
-void leaf_flux(const double* w, const R* z, int nl, int p, int q, int nrhs, double hx, double hy,
-               const double* d_D, const double* d_Pc2g, const int64_t* leaf_off,
-               int64_t ext_total, double* hp, cudaStream_t st);
+void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int nl, int p, int q,
+               int nrhs, const double2* hsc, const double* d_D, const double* d_Pc2g,
+               const int64_t* leaf_off, int64_t ext_total, double* hp, cudaStream_t st);
 
 // ---- merge / solve kernels (hps_merge.cu)
 template <typename R>
@@ -125,8 +137,16 @@ void merge_hpar(const BodyDesc* d, int nd, int max_ne, double* hp, int64_t ext_t
 template <typename R>
 void z_to_u3(const BodyDesc* d, int nd, int max_m, const R* zlev, double* u3, int64_t u3_total,
              int nrhs, cudaStream_t st);
-void solve_root_scatter(const double* f, const int* root_from_f, int nbnd, int nrhs,
-                        double* uext, int64_t root_off, int64_t ext_total, cudaStream_t st);
+// Root exterior values of every problem from its Dirichlet data f (or zeros
+// when f is null): uext[r*ext_total + root_off + k] = f[r*nbnd + rff[k]].
+struct RootDesc {
+  const double* f;
+  const int* rff;
+  int64_t root_off;
+  int nbnd;
+};
+void solve_root_scatter(const RootDesc* d, int nprob, int max_nbnd, int nrhs, double* uext,
+                        int64_t ext_total, cudaStream_t st);
 void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, const double* u3,
                          int64_t u3_total, double* uext, int64_t ext_total, int nrhs,
                          cudaStream_t st);

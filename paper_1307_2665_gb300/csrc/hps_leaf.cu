@@ -41,8 +41,9 @@ const char* tname(const char* f64, const char* f32) {
 
 // One CTA per leaf.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q, double sx,
-                                                       double sy, const double* __restrict__ gD,
+__global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int l0, int p, int q,
+                                                       const double2* __restrict__ hsc,
+                                                       const double* __restrict__ gD,
                                                        const double* __restrict__ gPg2c,
                                                        R* __restrict__ Aii, R* __restrict__ Y,
                                                        int64_t ys, int with_identity) {
@@ -53,17 +54,18 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q
   double* Pg = D2 + pp;       // p x q
   double* G = Pg + p * q;     // p x q : G[b][k] = sum_d D[b][d] w(d) Pg[d][k]
   double* cf = G + p * q;     // 6 x pp coefficient samples
-  const int l = blockIdx.x;
+  const int j = blockIdx.x, l = l0 + j;  // group-local and global leaf
+  const double sx = hsc[l].x, sy = hsc[l].y;
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
   for (int k = 0; k < 6; ++k)
     for (int e = threadIdx.x; e < pp; e += blockDim.x)
-      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)l * pp + e] : 0.0;
+      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)j * pp + e] : 0.0;
   __syncthreads();
   for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-    int i = e / p, j = e % p;
+    int i = e / p, jj = e % p;
     double s = 0.0;
-    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + j], s);
+    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + jj], s);
     D2[e] = s;
   }
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q
   const double* c2 = cf + 4 * pp;
   const double* c0 = cf + 5 * pp;
   const bool has12 = cp.c[1] != nullptr;
-  R* Al = Aii + (size_t)l * ni * ni;
+  R* Al = Aii + (size_t)j * ni * ni;
   // A_ii(ri, ci), ri = (a-1)*(p-2) + (b-1), ci = (c-1)*(p-2) + (d-1)
   for (int e = threadIdx.x; e < ni * ni; e += blockDim.x) {
     const int ri = e % ni, ci = e / ni;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q
   // B = -A_ie L1 (ni x 4q).  For an interior row (a, b) only the boundary nodes
   // of row a / column b are reached by the pure x / pure y terms; the mixed term
   // reaches every node of a side, collapsed through G.
-  R* Yl = Y + (size_t)l * ys;
+  R* Yl = Y + (size_t)j * ys;
   if (with_identity)  // columns nq .. nq+ni-1: the identity, so the solve also returns A_ii^{-1}
     for (int e = threadIdx.x; e < ni * ni; e += blockDim.x)
       Yl[(size_t)ni * nq + e] = (e % ni == e / ni) ? R(1) : R(0);
@@ -123,9 +125,9 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int p, int q
 }
 
 template <typename R>
-void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double hx, double hy,
-                   const double* d_D, const double* d_Pg2c, R* Aii, R* Y, int64_t ys,
-                   int with_identity, cudaStream_t st) {
+void leaf_assemble(const double* const* coef, int l0, int nleaves, int p, int q,
+                   const double2* hsc, const double* d_D, const double* d_Pg2c, R* Aii, R* Y,
+                   int64_t ys, int with_identity, cudaStream_t st) {
   if (nleaves <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
@@ -143,16 +145,16 @@ void leaf_assemble(const double* const* coef, int nleaves, int p, int q, double 
   prof::Scope sc(tname<R>("leaf_assemble<f64>", "leaf_assemble<f32>"), st,
                  (double)nleaves * (ni * ni * 8.0 + ni * 4.0 * q * 6.0),
                  (double)nleaves * ((ni * ni + ni * 4.0 * q) * sizeof(R) + ncoef * p * p * 8.0));
-  k_leaf_assemble<R><<<nleaves, 256, smem, st>>>(cp, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, Aii,
-                                                 Y, ys, with_identity);
+  k_leaf_assemble<R><<<nleaves, 256, smem, st>>>(cp, l0, p, q, hsc, d_D, d_Pg2c, Aii, Y, ys,
+                                                 with_identity);
 }
 
 // ------------------------------------------------------------------ leaf DtN
 // One CTA per leaf; the 4q columns of W are processed in chunks of CH.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64_t ys, int p,
-                                                  int q, double sx,
-                                                  double sy, const double* __restrict__ gD,
+__global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64_t ys, int l0,
+                                                  int p, int q, const double2* __restrict__ hsc,
+                                                  const double* __restrict__ gD,
                                                   const double* __restrict__ gPg2c,
                                                   const double* __restrict__ gPc2g,
                                                   R* __restrict__ T) {
@@ -164,7 +166,8 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
   double* Pc = Pg + p * q;      // q x p
   double* W = Pc + q * p;       // pp x CH
   double* F = W + pp * CH;      // 4p x CH side fluxes at Chebyshev points
-  const int l = blockIdx.x;
+  const int l = blockIdx.x;      // group-local leaf
+  const double sx = hsc[l0 + l].x, sy = hsc[l0 + l].y;
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
     Pg[e] = gPg2c[e];
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
 }
 
 template <typename R>
-void leaf_dtn(const R* Y, int64_t ys, int nleaves, int p, int q, double hx, double hy,
+void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2* hsc,
               const double* d_D, const double* d_Pg2c, const double* d_Pc2g, R* T,
               cudaStream_t st) {
   if (nleaves <= 0) return;
@@ -241,8 +244,7 @@ void leaf_dtn(const R* Y, int64_t ys, int nleaves, int p, int q, double hx, doub
   prof::Scope sc(tname<R>("leaf_dtn<f64>", "leaf_dtn<f32>"), st,
                  (double)nleaves * nq * (8.0 * p * p + 2.0 * nq * p),
                  (double)nleaves * (ni * nq + nq * nq) * sizeof(R));
-  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, ys, p, q, 2.0 / hx, 2.0 / hy, d_D, d_Pg2c, d_Pc2g,
-                                            T);
+  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, ys, l0, p, q, hsc, d_D, d_Pg2c, d_Pc2g, T);
 }
 
 // ------------------------------------------------------------ post-process
@@ -250,25 +252,30 @@ void leaf_dtn(const R* Y, int64_t ys, int nleaves, int p, int q, double hx, doub
 // element type R of Y, right-hand sides in chunks of RC.
 // u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or has it added in
 // FP64 (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior values
-// (ld ni).  maxabs (optional) receives max |w_full| (slot 0) and, after
-// accumulation, max |u| (slot 1), as the bit patterns of non-negative doubles.
+// (ld ni).  maxabs (optional) receives, for problem k = leaf_prob[leaf],
+// max |w_full| (slot 2k) and, after accumulation, max |u| (slot 2k+1), as the
+// bit patterns of non-negative doubles; a NaN counts as +inf.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int64_t ys,
+__global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int64_t ys, int l0,
                                                    const double* __restrict__ uext,
                                                    const int64_t* __restrict__ leaf_off,
-                                                   int64_t ext_total, int nl, int p, int q,
-                                                   int nrhs, const double* __restrict__ gPg2c,
+                                                   int64_t ext_total, int p, int q, int nrhs,
+                                                   const double* __restrict__ gPg2c,
                                                    const R* __restrict__ z, int accumulate,
                                                    unsigned long long* maxabs,
-                                                   double* __restrict__ u) {
+                                                   const int* __restrict__ leaf_prob,
+                                                   double* const* __restrict__ wptr,
+                                                   const int64_t* __restrict__ wrs) {
   constexpr int RC = 16;
   extern __shared__ __align__(16) double smd[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
   double* Pg = smd;                               // p x q
   double* ued = Pg + p * q;                       // nq x RC, FP64 (boundary rows)
   R* uer = reinterpret_cast<R*>(ued + nq * RC);   // nq x RC, element type of Y (interior rows)
-  const int l = blockIdx.x;
-  const int64_t off = leaf_off[l];
+  const int l = blockIdx.x;  // group-local leaf
+  const int64_t off = leaf_off[l0 + l];
+  double* const wl = wptr[l0 + l];
+  const int64_t wstride = wrs[l0 + l];
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
   const R* Yl = Y + (size_t)l * ys;
   const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
@@ -320,11 +327,11 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
         }
       }
       for (int rr = 0; rr < nr; ++rr) {
-        double* up = u + ((size_t)(r0 + rr) * nl + l) * pp + node;
+        double* up = wl + (size_t)(r0 + rr) * wstride + node;
         double v = out[rr];
-        mdw = fmax(mdw, fabs(v));
+        mdw = (v == v) ? fmax(mdw, fabs(v)) : INFINITY;
         if (accumulate) v += *up;
-        mu = fmax(mu, fabs(v));
+        mu = (v == v) ? fmax(mu, fabs(v)) : INFINITY;
         *up = v;
       }
     }
@@ -335,17 +342,18 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
       mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
     }
     if ((threadIdx.x & 31) == 0) {
-      atomicMax(&maxabs[0], (unsigned long long)__double_as_longlong(mdw));
-      atomicMax(&maxabs[1], (unsigned long long)__double_as_longlong(mu));
+      unsigned long long* slot = maxabs + 2 * leaf_prob[l0 + l];
+      atomicMax(&slot[0], (unsigned long long)__double_as_longlong(mdw));
+      atomicMax(&slot[1], (unsigned long long)__double_as_longlong(mu));
     }
   }
 }
 
 template <typename R>
-void leaf_post(const R* Y, int64_t ys, const double* uext, const int64_t* leaf_ext_off,
+void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
-               double* u, cudaStream_t st, const R* z, int accumulate,
-               unsigned long long* maxabs) {
+               double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z,
+               int accumulate, unsigned long long* maxabs, const int* leaf_prob) {
   if (nleaves <= 0 || nrhs <= 0) return;
   size_t smem = (size_t)(p * q + 4 * q * 16) * sizeof(double) + (size_t)4 * q * 16 * sizeof(R);
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
@@ -353,8 +361,9 @@ void leaf_post(const R* Y, int64_t ys, const double* uext, const int64_t* leaf_e
                  (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
                  (double)nleaves * (ni * nq * sizeof(R) +
                                     nrhs * (nq + (double)p * p * (accumulate ? 2 : 1)) * 8.0));
-  k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, ys, uext, leaf_ext_off, ext_total, nleaves, p, q,
-                                             nrhs, d_Pg2c, z, accumulate, maxabs, u);
+  k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, ys, l0, uext, leaf_ext_off, ext_total, p, q, nrhs,
+                                             d_Pg2c, z, accumulate, maxabs, leaf_prob, wptr,
+                                             wrs);
 }
 
 // ------------------------------------------------------------ FP64 residual
@@ -363,9 +372,11 @@ void leaf_post(const R* Y, int64_t ys, const double* uext, const int64_t* leaf_e
 //   A w = -c11 Dxx w - 2 c12 Dy (Dx w) - c22 Dyy w + c1 Dx w + c2 Dy w + c w.
 // Output rbuf[l*ni*nrhs + i + r*ni] in the element type of the correction solve.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int nl, int p, double sx,
-                                                       double sy, const double* __restrict__ gD,
-                                                       const double* __restrict__ w, int nrhs,
+__global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int p,
+                                                       const double2* __restrict__ hsc,
+                                                       const double* __restrict__ gD,
+                                                       double* const* __restrict__ wptr,
+                                                       const int64_t* __restrict__ wrs, int nrhs,
                                                        R* __restrict__ rbuf) {
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi;
@@ -374,23 +385,26 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int nl, int 
   double* cf = D2 + pp;     // 6 x pp
   double* W = cf + 6 * pp;  // pp
   double* Wx = W + pp;      // pp: Dx w
-  const int l = blockIdx.x;
+  const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
+  const double sx = hsc[l].x, sy = hsc[l].y;
+  const double* wl = wptr[l];
+  const int64_t wstride = wrs[l];
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
   for (int k = 0; k < 6; ++k)
     for (int e = threadIdx.x; e < pp; e += blockDim.x)
-      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)l * pp + e] : 0.0;
+      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)jl * pp + e] : 0.0;
   __syncthreads();
   for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-    int i = e / p, j = e % p;
+    int i = e / p, jj = e % p;
     double s = 0.0;
-    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + j], s);
+    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + jj], s);
     D2[e] = s;
   }
-  R* rl = rbuf + (size_t)l * ni * nrhs;
+  R* rl = rbuf + (size_t)jl * ni * nrhs;
   const bool has12 = cp.c[1] != nullptr, has2 = cp.c[4] != nullptr;
   for (int r = 0; r < nrhs; ++r) {
     __syncthreads();
-    for (int e = threadIdx.x; e < pp; e += blockDim.x) W[e] = w[((size_t)r * nl + l) * pp + e];
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) W[e] = wl[(size_t)r * wstride + e];
     __syncthreads();
     for (int e = threadIdx.x; e < pp; e += blockDim.x) {
       int a = e / p, b = e % p;
@@ -423,8 +437,9 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int nl, int 
 }
 
 template <typename R>
-void leaf_residual(const double* const* coef, int nl, int p, double hx, double hy,
-                   const double* d_D, const double* w, int nrhs, R* rbuf, cudaStream_t st) {
+void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
+                   const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
+                   cudaStream_t st) {
   if (nl <= 0 || nrhs <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
@@ -439,7 +454,7 @@ void leaf_residual(const double* const* coef, int nl, int p, double hx, double h
   const double pp = (double)p * p, ni = (double)(p - 2) * (p - 2);
   prof::Scope sc("leaf_residual<f64>", st, (double)nl * nrhs * (2.0 * pp * p + 8.0 * ni * p),
                  (double)nl * (nrhs * (pp * 8.0 + ni * sizeof(R)) + 6.0 * pp * 8.0));
-  k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, nl, p, 2.0 / hx, 2.0 / hy, d_D, w, nrhs, rbuf);
+  k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, l0, p, hsc, d_D, wptr, wrs, nrhs, rbuf);
 }
 
 // ------------------------------------------------- flux offsets of the leaves
@@ -447,9 +462,10 @@ void leaf_residual(const double* const* coef, int nl, int p, double hx, double h
 // of the current iterate plus the interior particular solution z = A_ii^{-1} r.
 // Written to the leaf's exterior slot of the flux pool hp (FP64).
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_flux(const double* __restrict__ w,
-                                                   const R* __restrict__ z, int nl, int p, int q,
-                                                   int nrhs, double sx, double sy,
+__global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ wptr,
+                                                   const int64_t* __restrict__ wrs,
+                                                   const R* __restrict__ z, int l0, int p, int q,
+                                                   int nrhs, const double2* __restrict__ hsc,
                                                    const double* __restrict__ gD,
                                                    const double* __restrict__ gPc2g,
                                                    const int64_t* __restrict__ leaf_off,
@@ -460,16 +476,19 @@ __global__ void __launch_bounds__(256) k_leaf_flux(const double* __restrict__ w,
   double* Pc = D + pp;   // q x p
   double* V = Pc + q * p;
   double* F = V + pp;    // 4p
-  const int l = blockIdx.x;
+  const int l = blockIdx.x;  // group-local leaf
+  const double sx = hsc[l0 + l].x, sy = hsc[l0 + l].y;
+  const double* wl = wptr[l0 + l];
+  const int64_t wstride = wrs[l0 + l];
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
   for (int e = threadIdx.x; e < q * p; e += blockDim.x) Pc[e] = gPc2g[e];
   const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
-  const int64_t off = leaf_off[l];
+  const int64_t off = leaf_off[l0 + l];
   for (int r = 0; r < nrhs; ++r) {
     __syncthreads();
     for (int e = threadIdx.x; e < pp; e += blockDim.x) {
       const int a = e / p, b = e % p;
-      double v = w[((size_t)r * nl + l) * pp + e];
+      double v = wl[(size_t)r * wstride + e];
       if (zl && a > 0 && a < p - 1 && b > 0 && b < p - 1)
         v += (double)zl[(a - 1) * pi + (b - 1) + (size_t)r * ni];
       V[e] = v;
@@ -500,32 +519,33 @@ __global__ void __launch_bounds__(256) k_leaf_flux(const double* __restrict__ w,
 }
 
 template <typename R>
-void leaf_flux(const double* w, const R* z, int nl, int p, int q, int nrhs, double hx, double hy,
-               const double* d_D, const double* d_Pc2g, const int64_t* leaf_off,
-               int64_t ext_total, double* hp, cudaStream_t st) {
+void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int nl, int p, int q,
+               int nrhs, const double2* hsc, const double* d_D, const double* d_Pc2g,
+               const int64_t* leaf_off, int64_t ext_total, double* hp, cudaStream_t st) {
   if (nl <= 0 || nrhs <= 0) return;
   size_t smem = (size_t)(2 * p * p + q * p + 4 * p) * sizeof(double);
   prof::Scope sc("leaf_flux<f64>", st, (double)nl * nrhs * (8.0 * p * p + 8.0 * q * p),
                  (double)nl * nrhs * ((double)p * p * 8.0 + (p - 2.0) * (p - 2.0) * sizeof(R) +
                                       4.0 * q * 8.0));
-  k_leaf_flux<R><<<nl, 256, smem, st>>>(w, z, nl, p, q, nrhs, 2.0 / hx, 2.0 / hy, d_D, d_Pc2g,
-                                        leaf_off, ext_total, hp);
+  k_leaf_flux<R><<<nl, 256, smem, st>>>(wptr, wrs, z, l0, p, q, nrhs, hsc, d_D, d_Pc2g, leaf_off,
+                                        ext_total, hp);
 }
 
 #define HPS_INST_LEAF(R)                                                                        \
-  template void leaf_assemble<R>(const double* const*, int, int, int, double, double,           \
+  template void leaf_assemble<R>(const double* const*, int, int, int, int, const double2*,       \
                                  const double*, const double*, R*, R*, int64_t, int,            \
                                  cudaStream_t);                                                 \
-  template void leaf_dtn<R>(const R*, int64_t, int, int, int, double, double, const double*,    \
+  template void leaf_dtn<R>(const R*, int64_t, int, int, int, int, const double2*, const double*, \
                             const double*, const double*, R*, cudaStream_t);                    \
-  template void leaf_post<R>(const R*, int64_t, const double*, const int64_t*, int64_t, int,    \
-                             int, int, int, const double*, double*, cudaStream_t, const R*, int, \
-                             unsigned long long*);                                              \
-  template void leaf_residual<R>(const double* const*, int, int, double, double, const double*, \
-                                 const double*, int, R*, cudaStream_t);                         \
-  template void leaf_flux<R>(const double*, const R*, int, int, int, int, double, double,       \
-                             const double*, const double*, const int64_t*, int64_t, double*,    \
-                             cudaStream_t);
+  template void leaf_post<R>(const R*, int64_t, int, const double*, const int64_t*, int64_t, int, \
+                             int, int, int, const double*, double* const*, const int64_t*,      \
+                             cudaStream_t, const R*, int, unsigned long long*, const int*);     \
+  template void leaf_residual<R>(const double* const*, int, int, int, const double2*,           \
+                                 const double*, double* const*, const int64_t*, int, R*,        \
+                                 cudaStream_t);                                                 \
+  template void leaf_flux<R>(double* const*, const int64_t*, const R*, int, int, int, int, int,  \
+                             const double2*, const double*, const double*, const int64_t*,      \
+                             int64_t, double*, cudaStream_t);
 HPS_INST_LEAF(double)
 HPS_INST_LEAF(float)
 

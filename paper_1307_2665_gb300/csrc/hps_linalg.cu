@@ -191,18 +191,14 @@ static void launch_gemm(const GemmDesc<TA, TB, TC>* d, int nd, int max_M, int ma
   if (nd <= 0 || tpm <= 0 || tpn <= 0) return;
   long long tiles = (long long)nd * tpm * tpn;
   prof::Scope sc(name, st, flops, bytes);
-  int splits = 1;
-  if (ws && tiles < 2 * 152 && max_K >= 512) {
-    splits = (int)std::min<long long>((2 * 152 + tiles - 1) / tiles, max_K / 128);
-    long long fit = (long long)(ws_elems / ((size_t)nd * max_M * max_N));
-    splits = (int)std::min<long long>(splits, fit);
-  }
-  if (splits < 2) {
+  // split K in fixed chunks of kSplitK: the split of a product depends only on
+  // its own K, never on the other products of the launch
+  const int splits = (ws && max_K > kSplitK) ? (max_K + kSplitK - 1) / kSplitK : 1;
+  if (splits < 2 || (size_t)nd * splits * max_M * max_N > ws_elems) {
     k_gemm<R, TL, TA, TB, TC><<<(unsigned)tiles, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
     return;
   }
-  int kc = (max_K + splits - 1) / splits;
-  kc = ((kc + TL::BK - 1) / TL::BK) * TL::BK;
+  const int kc = kSplitK;
   k_gemm_split<R, TL, TA, TB, TC><<<(unsigned)(tiles * splits), TL::NT, TL::SMEM, st>>>(
       d, tpm, tpn, splits, kc, ws, max_M, max_N);
   int chunks = (int)std::min<long long>(((long long)max_M * max_N + 255) / 256, 256);

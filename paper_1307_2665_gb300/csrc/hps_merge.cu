@@ -155,26 +155,26 @@ void z_to_u3(const BodyDesc* d, int nd, int max_m, const R* zlev, double* u3, in
 
 // ----------------------------------------------------------- downward pass
 // Exterior-value pool: uext[r*ext_total + box.ext_off + i] for right-hand side r.
-__global__ void k_root_scatter(const double* __restrict__ f, const int* __restrict__ root_from_f,
-                               int nbnd, int nrhs, double* __restrict__ uext, int64_t root_off,
-                               int64_t ext_total) {
-  int64_t n = (int64_t)nbnd * nrhs;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    int k = (int)(e % nbnd);
-    int64_t r = e / nbnd;
-    uext[r * ext_total + root_off + k] = f[r * nbnd + root_from_f[k]];
+__global__ void k_root_scatter(const RootDesc* __restrict__ d, int chunks, int nrhs,
+                               double* __restrict__ uext, int64_t ext_total) {
+  const RootDesc g = d[blockIdx.x / chunks];
+  const int64_t n = (int64_t)g.nbnd * nrhs;
+  for (int64_t e = (int64_t)(blockIdx.x % chunks) * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)chunks * blockDim.x) {
+    const int k = (int)(e % g.nbnd);
+    const int64_t r = e / g.nbnd;
+    uext[r * ext_total + g.root_off + k] = g.f ? g.f[r * g.nbnd + g.rff[k]] : 0.0;
   }
 }
 
-void solve_root_scatter(const double* f, const int* root_from_f, int nbnd, int nrhs,
-                        double* uext, int64_t root_off, int64_t ext_total, cudaStream_t st) {
-  int64_t n = (int64_t)nbnd * nrhs;
-  int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  if (blocks > 0) {
-    prof::Scope sc("root_scatter", st, 0.0, 2.0 * n * 8.0);
-    k_root_scatter<<<blocks, 256, 0, st>>>(f, root_from_f, nbnd, nrhs, uext, root_off, ext_total);
-  }
+void solve_root_scatter(const RootDesc* d, int nprob, int max_nbnd, int nrhs, double* uext,
+                        int64_t ext_total, cudaStream_t st) {
+  if (nprob <= 0) return;
+  int chunks = (int)std::min<int64_t>(((int64_t)max_nbnd * nrhs + 255) / 256, 64);
+  if (chunks < 1) return;
+  prof::Scope sc("root_scatter", st, 0.0, 16.0 * nprob * (double)max_nbnd * nrhs);
+  k_root_scatter<<<(unsigned)((int64_t)nprob * chunks), 256, 0, st>>>(d, chunks, nrhs, uext,
+                                                                      ext_total);
 }
 
 // children's exterior values from the parent's and u3 = S u_parent

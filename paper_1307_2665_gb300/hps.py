@@ -31,7 +31,7 @@ EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes", "hps_solve",
            "hps_solve_ex", "hps_query", "hps_free", "hps_status_string", "hps_kernel_launches",
            "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error",
-           "hps_solve_static")
+           "hps_solve_static", "hps_build_batch", "hps_solve_batch", "hps_batch_size")
 
 
 class HpsError(RuntimeError):
@@ -52,6 +52,13 @@ class Options(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
                 ("form_root_dtn", ctypes.c_int)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("d", Domain), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("p", ctypes.c_int),
+                ("q", ctypes.c_int), ("c11", ctypes.c_void_p), ("c12", ctypes.c_void_p),
+                ("c22", ctypes.c_void_p), ("c1", ctypes.c_void_p), ("c2", ctypes.c_void_p),
+                ("c", ctypes.c_void_p)]
 
 
 class KernelStat(ctypes.Structure):
@@ -97,6 +104,14 @@ def lib():
     L.hps_profile_reset.restype = None
     L.hps_profile_read.argtypes = [ctypes.POINTER(KernelStat), ctypes.c_int]
     L.hps_profile_read.restype = ctypes.c_int
+    L.hps_build_batch.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Options),
+                                  ctypes.POINTER(vp)]
+    L.hps_build_batch.restype = ctypes.c_int
+    L.hps_solve_batch.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                  ctypes.POINTER(SolveInfo)]
+    L.hps_solve_batch.restype = ctypes.c_int
+    L.hps_batch_size.argtypes = [vp]
+    L.hps_batch_size.restype = ctypes.c_int
     L.hps_solve_static.argtypes = [vp, vp, ctypes.c_int, vp]
     L.hps_solve_static.restype = ctypes.c_int
     L.hps_last_error.argtypes = []
@@ -176,6 +191,77 @@ class Handle:
             self.close()
         except Exception:
             pass
+
+
+def _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
+             form_root_dtn):
+    opt = default_options()
+    opt.precision = precision
+    opt.device_ptrs = 1 if device_ptrs else 0
+    opt.stream = stream
+    opt.form_root_dtn = 1 if form_root_dtn else 0
+    if refine_tol is not None:
+        opt.refine_tol = refine_tol
+    if max_refine is not None:
+        opt.max_refine = max_refine
+    if fp64_top_levels is not None:
+        opt.fp64_top_levels = fp64_top_levels
+    return opt
+
+
+class BatchHandle:
+    """Owns a batch hps_handle; frees it on close() or garbage collection."""
+
+    def __init__(self, ptr, problems, device_ptrs):
+        self.ptr = ptr
+        self.problems = problems  # list of (domain, nx, ny, p, q)
+        self.device_ptrs = device_ptrs
+
+    def close(self):
+        if self.ptr:
+            lib().hps_free(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hps_build_batch(problems, precision=HPS_FP64, device_ptrs=False, stream=None,
+                    refine_tol=None, max_refine=None, fp64_top_levels=None, form_root_dtn=False,
+                    check=True):
+    """Batch build.  problems: list of dicts with keys domain, nx, ny, p, q, coeffs."""
+    opt = _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
+                   form_root_dtn)
+    arr = (Problem * len(problems))()
+    for i, pr in enumerate(problems):
+        arr[i].d = _domain(pr["domain"])
+        arr[i].nx, arr[i].ny, arr[i].p, arr[i].q = pr["nx"], pr["ny"], pr["p"], pr["q"]
+        for k in COEFF_NAMES:
+            setattr(arr[i], k, _ptr(pr["coeffs"].get(k)))
+    out = ctypes.c_void_p()
+    st = lib().hps_build_batch(arr, len(problems), ctypes.byref(opt), ctypes.byref(out))
+    if st != HPS_OK:
+        if check:
+            raise HpsError(st, "hps_build_batch")
+        return st
+    return BatchHandle(out.value, [(pr["domain"], pr["nx"], pr["ny"], pr["p"], pr["q"])
+                                   for pr in problems], device_ptrs)
+
+
+def hps_solve_batch(h: BatchHandle, fs, us, info=None, check=True):
+    """Batch solve: fs[k] of shape (nrhs, nbnd_k), us[k] of shape (nrhs, nl_k, p_k, p_k)."""
+    nrhs = fs[0].shape[0]
+    fa = (ctypes.c_void_p * len(fs))(*[_ptr(f) for f in fs])
+    ua = (ctypes.c_void_p * len(us))(*[_ptr(u) for u in us])
+    inf = SolveInfo() if info is None else info
+    st = lib().hps_solve_batch(h.ptr, fa, nrhs, ua, ctypes.byref(inf))
+    inf.status = st
+    if st != HPS_OK and check:
+        raise HpsError(st, "hps_solve_batch")
+    return us
 
 
 def hps_build(domain, nx, ny, p, q, coeffs, precision=HPS_FP64, device_ptrs=False, stream=None,
