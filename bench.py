@@ -1,17 +1,26 @@
 #!/usr/bin/env python
 """Throughput of the composite spectral direct solver on GB300.
 
-One step = the whole hot path on one problem: hps_build (leaf DtN maps and all
-merges, Algorithm 1) followed by hps_solve of 16 right-hand sides (Algorithm 2
-and the leaf post-process; in mixed precision also the iterative refinement
-against the FP64 residual), on the convection-diffusion workload of 64 x 64
-leaves, p = 16, q = 14 (1 048 576 collocation nodes).  Both precisions are
-timed; the mixed one is the headline and the FP64 one is reported beside it.  Inputs (coefficients
-and boundary data) are resident in HBM when the timed region starts; L2 is
-flushed (a 512 MiB write) before every timed step.  Timing uses CUDA events on
-the library's stream, max over ranks.  With --gpus N (torchrun), every rank
-solves its own independent problem (replicas; weak scaling): there is no data
-exchange between problems.
+One step = the whole hot path on one batch of input: hps_build (leaf DtN maps
+and all merges, Algorithm 1) followed by the solve of every right-hand side
+(Algorithm 2 and the leaf post-process; in mixed precision also the iterative
+refinement against the FP64 residual).  Workloads (--workload):
+
+  convdiff64    (default) convection-diffusion on [0,1]^2, 64 x 64 leaves,
+                p = 16, q = 14 (1 048 576 collocation nodes), 16 right-hand sides
+  helmholtz256  variable-speed Helmholtz, kappa = 80, 256 x 256 leaves, p = 16,
+                q = 14 (16.8 M nodes), 64 right-hand sides
+  batch64       64 independent problems of uneven size (n log-uniform in
+                [8, 128]) and order (p in {12, 16, 20}, q = p - 2) with random
+                smooth coefficient fields, 16 right-hand sides each, one batched
+                build and solve
+
+Both precisions are timed; the mixed one is the headline and the FP64 one is
+reported beside it.  Inputs (coefficients and boundary data) are resident in
+HBM when the timed region starts; L2 is flushed (a 512 MiB write) before every
+timed step.  Timing uses CUDA events on the library's stream, max over ranks.
+With --gpus N (torchrun), every rank solves its own independent input
+(replicas; weak scaling): there is no data exchange between problems.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
 (the only reference implementation of this method), on a bounded sample.
@@ -33,29 +42,82 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "build DOF/s and solves/s at rel err ≤1e-10: mixed+refine vs plain FP64, same GB300"
-DOMAIN = (0.0, 1.0, 0.0, 1.0)
-NX = NY = 64
-P, Q, NRHS = 16, 14, 16
-DOF = NX * NY * P * P
+UNIT_SQ = (0.0, 1.0, 0.0, 1.0)
 FP64_DFMA_PER_SM_CLK = 2
+FP32_FFMA_PER_SM_CLK = 128
 N_SM = 152
+MAX_REFINE = 30  # refinement cap (tolerance 1e-11, Anderson depth 3: the library defaults)
 
 
-def workload_config(precision="fp64"):
-    return {"workload": f"convection-diffusion c1=-100cos(4pi y), c2=100sin(4pi x) on [0,1]^2, "
-                        f"{NX}x{NY} leaves, p={P}, q={Q}, {NRHS} RHS (20-mode Fourier data), "
-                        f"build+solve, {precision}",
-            "leaves": f"{NX}x{NY}", "p": P, "q": Q, "nrhs": NRHS, "dof": DOF,
-            "precision": precision, "l2": "flushed before every timed step (512 MiB write)"}
+# ------------------------------------------------------------- workloads
+class Workload:
+    """A list of problems (domain, nx, ny, p, q, host coefficients, host f)
+    plus a description.  One problem goes through hps_build / hps_solve, more
+    through hps_build_batch / hps_solve_batch."""
+
+    def __init__(self, name, desc, probs, nrhs, oracle_fn):
+        self.name, self.desc, self.probs, self.nrhs = name, desc, probs, nrhs
+        self.oracle_fn = oracle_fn  # coefficient function of the oracle sample
+        self.dof = sum(pr["nx"] * pr["ny"] * pr["p"] ** 2 for pr in probs)
+        self.leaves = sum(pr["nx"] * pr["ny"] for pr in probs)
+
+    def config(self, precision):
+        return dict(self.desc, precision=precision, dof=self.dof, nrhs=self.nrhs,
+                    problems=len(self.probs), leaves_total=self.leaves,
+                    l2="flushed before every timed step (512 MiB write)",
+                    refinement="tol 1e-11 per RHS, Anderson depth 3, cap 30")
 
 
-def make_inputs(nx=NX, ny=NY, p=P, q=Q, nrhs=NRHS, seed0=0, xy=None, bxy=None):
-    from paper_1307_2665_gb300 import inputs as I
-    co = I.convection_diffusion(xy[..., 0], xy[..., 1])
-    co = {k: (None if v is None else np.ascontiguousarray(v, dtype=np.float64)) for k, v in co.items()}
-    f = np.ascontiguousarray(np.stack([I.fourier_boundary(seed0 + s, bxy[:, 0], bxy[:, 1], DOMAIN)
+def _problem(hps, I, dom, nx, ny, p, q, fn, nrhs, seed0):
+    xy = hps.hps_cheb_nodes(dom, nx, ny, p)
+    xs = xy[:nx, 0, :, 0].reshape(-1)
+    ys = xy[::nx, :, 0, 1].reshape(-1)
+    co = I.sample_on_leaf_grid(fn, xs, ys, nx, ny, p)
+    del xy
+    bxy = hps.hps_boundary_nodes_grid(dom, nx, ny, q)
+    f = np.ascontiguousarray(np.stack([I.fourier_boundary(seed0 + s, bxy[:, 0], bxy[:, 1], dom)
                                        for s in range(nrhs)]))
-    return co, f
+    return dict(domain=dom, nx=nx, ny=ny, p=p, q=q, coeffs=co, f=f)
+
+
+def make_workload(name, leaves, rank):
+    from paper_1307_2665_gb300 import hps
+    from paper_1307_2665_gb300 import inputs as I
+    if name == "convdiff64":
+        n = leaves or 64
+        nrhs = 16
+        pr = _problem(hps, I, UNIT_SQ, n, n, 16, 14, I.convection_diffusion, nrhs, nrhs * rank)
+        desc = {"workload": f"convection-diffusion c1=-100cos(4pi y), c2=100sin(4pi x) on [0,1]^2, "
+                            f"{n}x{n} leaves, p=16, q=14, {nrhs} RHS (20-mode Fourier data), "
+                            f"build+solve", "leaves": f"{n}x{n}", "p": 16, "q": 14}
+        return Workload(name, desc, [pr], nrhs, I.convection_diffusion)
+    if name == "helmholtz256":
+        n = leaves or 256
+        nrhs = 64
+        pr = _problem(hps, I, UNIT_SQ, n, n, 16, 14, I.gaussian_bump_helmholtz, nrhs, nrhs * rank)
+        desc = {"workload": f"variable-speed Helmholtz -Lap u - 80^2 (1 - 0.5 exp(-|x-c|^2/0.02)) u = 0 "
+                            f"on [0,1]^2, {n}x{n} leaves, p=16, q=14, {nrhs} RHS (20-mode Fourier "
+                            f"data), build+solve", "leaves": f"{n}x{n}", "p": 16, "q": 14}
+        return Workload(name, desc, [pr], nrhs, I.gaussian_bump_helmholtz)
+    if name == "batch64":
+        nprob = 64
+        nmax = leaves or 128
+        nrhs = 16
+        rng = np.random.Generator(np.random.PCG64(20240 + rank))
+        probs = []
+        for k in range(nprob):
+            n = int(round(np.exp(rng.uniform(np.log(8), np.log(nmax)))))
+            p = int(rng.choice([12, 16, 20]))
+            seed = 1000 * rank + k
+            fn = (lambda s: (lambda x, y: I.random_smooth_operator(s, x, y)))(seed)
+            probs.append(_problem(hps, I, UNIT_SQ, n, n, p, p - 2, fn, nrhs, 100 * seed))
+        desc = {"workload": f"{nprob} independent problems, n x n leaves with n log-uniform in "
+                            f"[8, {nmax}], p in {{12, 16, 20}}, q = p - 2, random smooth c11, c22, "
+                            f"c12, c1, c2 (c = 0), {nrhs} RHS each, one batched build+solve",
+                "sizes": [pr["nx"] for pr in probs], "orders": [pr["p"] for pr in probs]}
+        return Workload(name, desc, probs, nrhs,
+                        lambda x, y: I.random_smooth_operator(0, x, y))
+    raise ValueError(name)
 
 
 # ---------------------------------------------------------------- clocks
@@ -110,43 +172,43 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_step(n, nrhs=NRHS):
-    """One oracle solve (static condensation + sparse LU, FP64) of the same
-    workload restricted to n x n leaves; returns seconds and DOF."""
+def oracle_step(n, fn, nrhs=16):
+    """One oracle solve (static condensation + sparse LU, FP64) of the
+    workload's coefficient field on n x n leaves, p = 16, q = 14; returns
+    seconds and DOF."""
     from oracle import hps_oracle as O
     from paper_1307_2665_gb300 import inputs as I
-    prob = O.make_problem(DOMAIN, n, n, P, Q, I.convection_diffusion)
+    prob = O.make_problem(UNIT_SQ, n, n, 16, 14, fn)
     bxy = O.boundary_points(prob)
-    f = np.stack([I.fourier_boundary(s, bxy[:, 0], bxy[:, 1], DOMAIN) for s in range(nrhs)], axis=1)
+    f = np.stack([I.fourier_boundary(s, bxy[:, 0], bxy[:, 1], UNIT_SQ) for s in range(nrhs)],
+                 axis=1)
     t0 = time.perf_counter()
     O.solve_condensed(prob, f)
-    return time.perf_counter() - t0, n * n * P * P
+    return time.perf_counter() - t0, n * n * 16 * 16
 
 
-def cpu_baseline(n=32, reps=1):
-    ts = []
-    dof = 0
-    for _ in range(reps):
-        t, dof = oracle_step(n)
-        ts.append(t)
-    t = min(ts)
+def cpu_baseline(fn, n=32, nrhs=16):
+    t, dof = oracle_step(n, fn, nrhs)
     return {"value": dof / t, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n}x{n} leaves of the same field, p={P}, q={Q}, {NRHS} RHS: FP64 static "
-                      f"condensation (per-leaf dense solves, BLAS on all cores) + SuperLU of the "
-                      f"edge system (single-threaded); {t:.2f} s per solve"}
+            "sample": f"{n}x{n} leaves of the workload's coefficient field, p=16, q=14, {nrhs} "
+                      f"RHS: FP64 static condensation (per-leaf dense solves, BLAS on all cores) "
+                      f"+ SuperLU of the edge system (single-threaded); {t:.2f} s per solve"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from paper_1307_2665_gb300 import inputs as I
+    fn = {"convdiff64": I.convection_diffusion, "helmholtz256": I.gaussian_bump_helmholtz,
+          "batch64": lambda x, y: I.random_smooth_operator(0, x, y)}[args.workload]
     n = args.ref_leaves
     for _ in range(args.warmup):
-        oracle_step(n)
+        oracle_step(n, fn)
     ts = []
     dof = 0
     for _ in range(args.steps):
-        t, dof = oracle_step(n)
+        t, dof = oracle_step(n, fn)
         ts.append(t)
     tot = sum(ts)
     value = dof * args.steps / tot
@@ -154,7 +216,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(workload_config(), sample_leaves=f"{n}x{n}"),
+            "config": {"workload": args.workload, "sample_leaves": f"{n}x{n}", "p": 16, "q": 14,
+                       "nrhs": 16},
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{n}x{n} leaves of the workload's field per step"},
@@ -168,9 +231,6 @@ def run_reference(args):
 # ALU peaks of a GB300 at a given SM clock: FP64 is 2 DFMA per SM per clock
 # (measured 1.198 TFLOP/s with 152 SMs at 1987 MHz), FP32 128 FFMA per SM per
 # clock (measured 74.8 TFLOP/s at the same clock).
-FP32_FFMA_PER_SM_CLK = 128
-
-
 def alu_peak_tflops(name, sm_mhz):
     per = FP64_DFMA_PER_SM_CLK if "f64" in name else FP32_FFMA_PER_SM_CLK
     return N_SM * per * 2 * sm_mhz * 1e6 / 1e12, per
@@ -189,6 +249,45 @@ def roofline_of(stats, t_total_ms, sm_mhz):
                            f"per-clock rate measured by an FMA probe on this pool)",
             "flops_per_launch": per_launch_flops, "launches": st["launches"],
             "ms_per_launch": per_launch_s * 1e3, "share_of_step": st["ms"] / max(t_total_ms, 1e-9)}
+
+
+class Runner:
+    """Build and solve of a workload through the public binding."""
+
+    def __init__(self, hps, W, dev):
+        import torch
+        self.hps, self.W = hps, W
+        self.single = len(W.probs) == 1
+        self.co_d = [{k: (None if v is None else torch.from_numpy(v).to(dev))
+                      for k, v in pr["coeffs"].items()} for pr in W.probs]
+        self.f_d = [torch.from_numpy(pr["f"]).to(dev) for pr in W.probs]
+        self.u_d = [torch.empty((W.nrhs, pr["nx"] * pr["ny"], pr["p"], pr["p"]),
+                                dtype=torch.float64, device=dev) for pr in W.probs]
+
+    def build(self, prec, sp, host=False):
+        hps, W = self.hps, self.W
+        cos = [pr["coeffs"] for pr in W.probs] if host else self.co_d
+        if self.single:
+            pr = W.probs[0]
+            return hps.hps_build(pr["domain"], pr["nx"], pr["ny"], pr["p"], pr["q"], cos[0],
+                                 precision=prec, device_ptrs=not host, stream=sp,
+                                 max_refine=MAX_REFINE)
+        plist = [dict(pr, coeffs=c) for pr, c in zip(W.probs, cos)]
+        return hps.hps_build_batch(plist, precision=prec, device_ptrs=not host, stream=sp,
+                                   max_refine=MAX_REFINE)
+
+    def solve(self, h, info, host=False):
+        hps, W = self.hps, self.W
+        if host:
+            us = [np.empty((W.nrhs, pr["nx"] * pr["ny"], pr["p"], pr["p"])) for pr in W.probs]
+            fs = [pr["f"] for pr in W.probs]
+        else:
+            us, fs = self.u_d, self.f_d
+        if self.single:
+            hps.hps_solve(h, fs[0], us[0], info=info, check=False)
+        else:
+            hps.hps_solve_batch(h, fs, us, info=info, check=False)
+        return us
 
 
 def run_native(args):
@@ -210,11 +309,8 @@ def run_native(args):
         dist.barrier()
     build()  # no-op when up to date
 
-    xy = hps.hps_cheb_nodes(DOMAIN, NX, NY, P)
-    bxy = hps.hps_boundary_nodes_grid(DOMAIN, NX, NY, Q)
-    co_h, f_h = make_inputs(xy=xy, bxy=bxy, seed0=NRHS * rank)
-    co_d = {k: (None if v is None else torch.from_numpy(v).to(dev)) for k, v in co_h.items()}
-    f_d = torch.from_numpy(f_h).to(dev)
+    W = make_workload(args.workload, args.leaves, rank)
+    run = Runner(hps, W, dev)
     stream = torch.cuda.Stream(device=dev)
     sp = stream.cuda_stream
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -222,13 +318,13 @@ def run_native(args):
     if args.precision != "both":
         modes = {args.precision: modes[args.precision]}
 
-    def step(prec, u_d, events=None, info=None):
+    def step(prec, events=None, info=None):
         if events:
             events[0].record(stream)
-        h = hps.hps_build(DOMAIN, NX, NY, P, Q, co_d, precision=prec, device_ptrs=True, stream=sp)
+        h = run.build(prec, sp)
         if events:
             events[1].record(stream)
-        hps.hps_solve(h, f_d, u_d, info=info, check=False)
+        run.solve(h, info)
         if events:
             events[2].record(stream)
         return h
@@ -238,10 +334,9 @@ def run_native(args):
     if rank == 0:
         sampler.start()
     for mname, prec in modes.items():
-        u_d = torch.empty((NRHS, NX * NY, P, P), dtype=torch.float64, device=dev)
         torch.cuda.synchronize()
         for _ in range(args.warmup):
-            step(prec, u_d).close()
+            step(prec).close()
         torch.cuda.synchronize()
         hps.hps_profile_reset()
         hps.hps_profile_enable(True)
@@ -256,9 +351,9 @@ def run_native(args):
                 flush.fill_(1.0)
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             info = hps.SolveInfo()
-            h = step(prec, u_d, ev, info)
+            h = step(prec, ev, info)
             stream.synchronize()
-            if info.status not in (hps.HPS_OK,):
+            if info.status != hps.HPS_OK:
                 raise RuntimeError(f"{mname} solve status {info.status} (last update {info.last_update})")
             iters.append(info.iterations)
             t_build += ev[0].elapsed_time(ev[1])
@@ -275,7 +370,7 @@ def run_native(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             t_build, t_solve = t.tolist()
         results[mname] = {"t_build": t_build, "t_solve": t_solve, "iters": iters, "stats": stats,
-                          "launches": launches, "u": u_d}
+                          "launches": launches, "u": [u.clone() for u in run.u_d]}
     clocks = sampler.stop() if rank == 0 else None
     head = "mixed" if "mixed" in results else "fp64"
     R = results[head]
@@ -283,8 +378,9 @@ def run_native(args):
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_steps = max(1, min(args.steps, 3))
     t_e2e = 0.0
-    h2d = sum(v.nbytes for v in co_h.values() if v is not None) + f_h.nbytes
-    d2h = NRHS * NX * NY * P * P * 8
+    h2d = sum(v.nbytes for pr in W.probs for v in pr["coeffs"].values() if v is not None)
+    h2d += sum(pr["f"].nbytes for pr in W.probs)
+    d2h = W.nrhs * W.dof * 8
     for _ in range(e2e_steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)
@@ -292,9 +388,8 @@ def run_native(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = hps.hps_build(DOMAIN, NX, NY, P, Q, co_h, precision=modes[head], device_ptrs=False,
-                          stream=sp)
-        u_h = hps.hps_solve(h, f_h, device_ptrs=False)
+        h = run.build(modes[head], sp, host=True)
+        u_h = run.solve(h, None, host=True)
         e1.record(stream)
         stream.synchronize()
         t_e2e += e0.elapsed_time(e1)
@@ -303,11 +398,11 @@ def run_native(args):
         t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_e2e = t.item()
-    assert np.isfinite(u_h).all()
+    assert all(np.isfinite(u).all() for u in u_h)
     rel_diff = None
     if "mixed" in results and "fp64" in results:
-        a, b = results["mixed"]["u"], results["fp64"]["u"]
-        rel_diff = float((a - b).abs().max() / b.abs().max())
+        rel_diff = max(float((a - b).abs().max() / b.abs().max())
+                       for a, b in zip(results["mixed"]["u"], results["fp64"]["u"]))
 
     if rank != 0:
         if world > 1:
@@ -317,9 +412,9 @@ def run_native(args):
 
     def summary(r):
         tt = r["t_build"] + r["t_solve"]
-        return {"dof_per_s": world * DOF * args.steps / (tt / 1e3),
-                "build_dof_per_s": world * DOF * args.steps / (r["t_build"] / 1e3),
-                "solves_per_s": world * NRHS * args.steps / (r["t_solve"] / 1e3),
+        return {"dof_per_s": world * W.dof * args.steps / (tt / 1e3),
+                "build_dof_per_s": world * W.dof * args.steps / (r["t_build"] / 1e3),
+                "solves_per_s": world * W.nrhs * len(W.probs) * args.steps / (r["t_solve"] / 1e3),
                 "build_ms": r["t_build"] / args.steps, "solve_ms": r["t_solve"] / args.steps,
                 "refine_iterations": r["iters"],
                 "gpu_launches": int(r["launches"] // args.steps),
@@ -336,11 +431,11 @@ def run_native(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64 (FP32 leaves/lower merges, FP64 top merges and residual)"
             if head == "mixed" else "f64",
-            "data": "synthetic", "config": workload_config(head),
+            "data": "synthetic", "config": W.config(head),
             "build_dof_per_s": H["build_dof_per_s"], "solves_per_s": H["solves_per_s"],
             "build_ms": H["build_ms"], "solve_ms": H["solve_ms"],
             "clocks": clocks, "gpu_launches": H["gpu_launches"],
-            "e2e": {"value": world * DOF * e2e_steps / (t_e2e / 1e3), "unit": "DOF/s",
+            "e2e": {"value": world * W.dof * e2e_steps / (t_e2e / 1e3), "unit": "DOF/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": H["roofline"]}
     if "fp64" in summ and head != "fp64":
@@ -355,7 +450,7 @@ def run_native(args):
     line["refine_iterations"] = H["refine_iterations"]
     line["kernels"] = H["kernels"]
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.ref_leaves)
+        line["cpu_baseline"] = cpu_baseline(W.oracle_fn, args.ref_leaves)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -368,18 +463,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="convdiff64",
+                    choices=["convdiff64", "helmholtz256", "batch64"])
     ap.add_argument("--ref-leaves", type=int, default=32,
                     help="leaves per side of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
                     help="both: time FP64 and mixed, report mixed as the headline")
-    ap.add_argument("--leaves", type=int, default=64,
-                    help="leaves per side (64 is the benchmarked workload; smaller values are "
-                         "for profiling captures)")
+    ap.add_argument("--leaves", type=int, default=0,
+                    help="leaves per side (batch64: largest side); 0 = the workload's own size. "
+                         "Smaller values are for profiling captures")
     args = ap.parse_args()
-    global NX, NY, DOF
-    NX = NY = args.leaves
-    DOF = NX * NY * P * P
     if args.impl == "reference":
         return run_reference(args)
     return run_native(args)

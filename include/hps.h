@@ -72,12 +72,15 @@ typedef struct {
   int device_ptrs;        /* 1: coefficient / f / u pointers are device pointers */
   void* stream;           /* cudaStream_t to run on; NULL: the library's own stream */
   int form_root_dtn;      /* 1: also form the root DtN T^1 (not needed by hps_solve) */
+  int refine_depth;       /* mixed mode: Anderson history length of the refinement, 0..8
+                             (default 3; 0: plain refinement u += delta) */
 } hps_options;
 
 typedef struct {
   int status;             /* HPS_OK or the failing status */
-  int iterations;         /* refinement iterations run (0 in FP64 mode) */
-  double last_update;     /* max|delta| / max|u| of the last correction (mixed mode) */
+  int iterations;         /* refinement corrections computed, the most over all
+                             right-hand sides (0 in FP64 mode) */
+  double last_update;     /* largest over right-hand sides of the last max|delta| / max|u| */
   int bad_box;            /* box index of a singular pivot, or -1 */
 } hps_solve_info;
 
@@ -148,16 +151,20 @@ int hps_boundary_nodes(hps_handle h, double* xy);
  * iterative refinement against the FP64 residual of the global collocation
  * system: each step solves the correction equation (interior residual as a
  * body load, flux jumps at the interior Gauss nodes) with the low-precision
- * factors and adds the correction in FP64.  It stops when the correction's
- * max-norm relative to u's is at most refine_tol, or when the error it leaves
- * (that correction times the observed contraction ratio of the last two
- * corrections) is below refine_tol / 10 (HPS_OK; info->last_update then holds
- * that estimate), or after
- * max_refine steps, or once the correction stops shrinking by half per step
- * (the iterate has reached the accuracy the FP64 residual resolves for this
- * conditioning); the latter two return HPS_ENOTCONVERGED with u holding the
- * last iterate and info->last_update its relative correction.  info may be
- * NULL.  f and u follow options.device_ptrs of the build. */
+ * factors, giving a correction delta of the iterate u in FP64.  With
+ * refine_depth m > 0 the step is Anderson-accelerated: the new iterate is
+ * u + delta minus the least-squares combination of the last m differences of
+ * corrections and iterates that best cancels delta (the GMRES iterate of the
+ * same Krylov space, for this linear map); with m = 0 it is u + delta.  Every
+ * right-hand side of every problem is refined on its own: it stops when its
+ * max|delta| <= refine_tol * max|u| (then u += delta), when delta no longer
+ * shrinks to half of the smaller of the two previous ones (the iterate has
+ * reached the accuracy the FP64 residual resolves for this conditioning), or
+ * after max_refine corrections, and its result does not depend on the other
+ * right-hand sides or problems solved with it.  HPS_ENOTCONVERGED if any
+ * right-hand side stopped above refine_tol (u holds the last iterates;
+ * info->last_update the largest relative correction).  info may be NULL.
+ * f and u follow options.device_ptrs of the build. */
 int hps_solve(hps_handle h, const double* f, int nrhs, double* u, hps_solve_info* info);
 
 /* Same as hps_solve with an explicit pointer kind: device_ptrs 0 (host arrays,

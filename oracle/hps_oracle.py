@@ -586,6 +586,69 @@ def residual(prob: Problem, sol: Solution, f, F=None, G=None):
     return r1, r2
 
 
+def sampled_residual(prob: Problem, w, f, leaves):
+    """Leaf-local check of a candidate solution given only its per-leaf values
+    w_full (nrhs, n_leaves, p, p), on a subset of leaves, for problems too
+    large to solve here.  For each listed leaf it evaluates
+
+      e1     (A w_full)_i at the interior Chebyshev nodes (E1, Section 3.1),
+             scaled by ||A_ii-rows||_inf ||w||_inf;
+      e2     flux mismatch L4 L3 w^alpha - L4 L3 w^beta on its east and north
+             edges (E2), scaled by ||L4 L3||_inf ||w||_inf;
+      cont   the two leaves' values at the non-corner Chebyshev points of a
+             shared side, which both come from the same Gauss values through
+             L1 (Section 3.2, Step 1) and must agree, scaled by ||w||_inf;
+      gamma  on sides lying on Gamma, the non-corner Chebyshev values against
+             L1 f of that side (Step 1 with the Dirichlet data), same scale.
+
+    f: (nrhs, nbnd) in the order of boundary_points.  Returns the maxima."""
+    p, q = prob.p, prob.q
+    ops = LeafOps(p, q, prob.hx, prob.hy)
+    en = EdgeNumbering(prob)
+    gpos = -np.ones(en.N, dtype=np.int64)
+    gpos[en.gamma_order()] = np.arange(len(en.gamma_order()))
+    f = np.atleast_2d(np.asarray(f, np.float64))
+    w = np.asarray(w, np.float64)
+    nrhs = w.shape[0]
+    inner = np.arange(1, p - 1)
+    rows = {"S": inner, "N": (p - 1) * p + inner, "W": inner * p, "E": inner * p + p - 1}
+    fscale = np.max(np.sum(np.abs(ops.F), axis=1))
+    out = {"e1": 0.0, "e2": 0.0, "cont": 0.0, "gamma": 0.0}
+
+    def full(l):
+        return w[:, l].reshape(nrhs, p * p).T
+
+    for l in leaves:
+        iy, ix = divmod(int(l), prob.nx)
+        W = full(l)
+        wmax = max(np.max(np.abs(W)), 1e-300)
+        A = ops.operator(_leaf_coef(prob, l))[ops.Ji]
+        out["e1"] = max(out["e1"], np.max(np.abs(A @ W)) / (np.max(np.sum(np.abs(A), 1)) * wmax))
+        Fl = ops.F @ W
+        for dx, dy, mine, theirs, rm, rt in ((1, 0, slice(q, 2 * q), slice(3 * q, 4 * q), "E", "W"),
+                                              (0, 1, slice(2 * q, 3 * q), slice(0, q), "N", "S")):
+            jx, jy = ix + dx, iy + dy
+            if jx >= prob.nx or jy >= prob.ny:
+                continue
+            Wn = full(jy * prob.nx + jx)
+            sc = max(wmax, np.max(np.abs(Wn)))
+            out["e2"] = max(out["e2"], np.max(np.abs(Fl[mine] - (ops.F @ Wn)[theirs])) / (fscale * sc))
+            out["cont"] = max(out["cont"], np.max(np.abs(W[rows[rm]] - Wn[rows[rt]])) / sc)
+        sides = []
+        if iy == 0:
+            sides.append(("S", en.h(0, ix)))
+        if iy == prob.ny - 1:
+            sides.append(("N", en.h(prob.ny, ix)))
+        if ix == 0:
+            sides.append(("W", en.v(0, iy)))
+        if ix == prob.nx - 1:
+            sides.append(("E", en.v(prob.nx, iy)))
+        for side, gids in sides:
+            want = ops.Pg2c[1:p - 1] @ f[:, gpos[gids]].T
+            out["gamma"] = max(out["gamma"], np.max(np.abs(W[rows[side]] - want)) / wmax)
+    return out
+
+
 def point_values(prob: Problem, w, x, y, tol=1e-12):
     """Values of the per-leaf solution w (n_leaves, p, p) at the point (x, y)
     from every leaf whose Chebyshev grid contains it (a leaf corner belongs to

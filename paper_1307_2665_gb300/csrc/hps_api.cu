@@ -204,18 +204,19 @@ struct hps_handle_s {
   int nprob = 0;
   std::vector<LeafGroup> lg;
   std::vector<LevelGroup> lev;      // in increasing height
-  PoolBuf maps, root_from_f, leaf_off, leaf_prob, hsc, status, coef;
+  PoolBuf maps, root_from_f, leaf_off, hsc, status, coef;
   std::vector<int64_t> src_off, cma_off, cmb_off, u3_off;
   int64_t u3_total = 0;
   Stager keep;                      // descriptors that live as long as the handle
   // solve workspace and descriptors, cached for one nrhs
   int cache_nrhs = 0;
-  PoolBuf uext, u3, hpool, split_ws, maxabs, fstage, ustage;
+  PoolBuf uext, u3, hpool, split_ws, fstage, ustage;
   Stager solve_st, call_st;
-  unsigned long long* h_maxabs = nullptr;  // pinned, 2 per problem
+  double* h_aa = nullptr;           // pinned: refinement sums and weights per column
+  size_t h_aa_cap = 0;
   ~hps_handle_s() {
     if (stream) cudaStreamSynchronize(stream);
-    if (h_maxabs) cudaFreeHost(h_maxabs);
+    if (h_aa) cudaFreeHost(h_aa);
   }
 };
 
@@ -497,7 +498,6 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
       hs[l] = make_double2(2.0 / pi.hx, 2.0 / pi.hy);
     }
     up(H.leaf_off, lo.data(), lo.size() * sizeof(int64_t));
-    up(H.leaf_prob, pl.leaf_prob.data(), pl.leaf_prob.size() * sizeof(int));
     up(H.hsc, hs.data(), hs.size() * sizeof(double2));
     ck(cudaStreamSynchronize(st));  // the pageable sources above go out of scope
   }
@@ -751,8 +751,6 @@ void prepare_solve(hps_handle_s& H, int nrhs) {
       L.rlev->alloc(n, st);
       L.zlev->alloc(n, st);
     }
-    H.maxabs.alloc(2 * (size_t)H.nprob * sizeof(unsigned long long), st);
-    if (!H.h_maxabs) ck(cudaMallocHost(&H.h_maxabs, 2 * (size_t)H.nprob * sizeof(unsigned long long)));
   }
   for (auto& L : H.lev) {
     if (L.f64) {
@@ -800,24 +798,33 @@ void downward(hps_handle_s& H, int nrhs, bool with_z) {
 
 struct CallPtrs {           // per solve call: where f comes from and u goes
   RootDesc* roots = nullptr;
-  double* const* wptr = nullptr;
-  const int64_t* wrs = nullptr;
+  double* const* wptr = nullptr;  // per leaf: its first node of u (right-hand side 0)
+  const int64_t* wrs = nullptr;   // per leaf: stride between right-hand sides
   int max_nbnd = 0;
+  // refinement (mixed mode): per leaf pointers into the correction vector F,
+  // and the columns (problem, right-hand side) of the accelerated update
+  double* const* fptr = nullptr;
+  AaCol* cols = nullptr;
+  int ncol = 0;
+  int64_t nchunks = 0, nu = 0;
 };
 
-void leaf_out(hps_handle_s& H, const CallPtrs& cp, int nrhs, bool correction) {
+// Refinement work vectors of one solve call (pool memory, released with it).
+struct RefineBufs {
+  PoolBuf F, Fprev, dWlast, dF, G, part, colsum, coef;
+};
+
+void leaf_out(hps_handle_s& H, double* const* wptr, const int64_t* wrs, int nrhs,
+              bool correction) {
   for (auto& G : H.lg) {
     if (H.mixed)
       leaf_post<float>(G.Y->as<float>(), G.ys, G.l0, H.uext.as<double>(), H.leaf_off.as<int64_t>(),
-                       H.plan.ext_total, G.nl, G.p, G.q, nrhs, G.dPg2c->as<double>(), cp.wptr,
-                       cp.wrs, H.stream, correction ? G.zleaf->as<float>() : nullptr,
-                       correction ? 1 : 0,
-                       correction ? H.maxabs.as<unsigned long long>() : nullptr,
-                       H.leaf_prob.as<int>());
+                       H.plan.ext_total, G.nl, G.p, G.q, nrhs, G.dPg2c->as<double>(), wptr, wrs,
+                       H.stream, correction ? G.zleaf->as<float>() : nullptr);
     else
       leaf_post<double>(G.Y->as<double>(), G.ys, G.l0, H.uext.as<double>(),
                         H.leaf_off.as<int64_t>(), H.plan.ext_total, G.nl, G.p, G.q, nrhs,
-                        G.dPg2c->as<double>(), cp.wptr, cp.wrs, H.stream);
+                        G.dPg2c->as<double>(), wptr, wrs, H.stream);
   }
 }
 
@@ -862,18 +869,87 @@ void up_level(hps_handle_s& H, LevelGroup& L, int nrhs) {
                   L.max_m, ws, wse);
 }
 
-int solve_all(hps_handle_s& H, const CallPtrs& cp, int nrhs, hps_solve_info* info) {
+// Least-squares weights of one column: minimise ||F - sum_s g_s dF_s|| over
+// the valid history slots through the normal equations (Cholesky); a slot
+// whose pivot falls below 1e-12 of the largest diagonal entry is dropped,
+// oldest first, and the system is solved again without it.
+void anderson_weights(const double* A, const double* bvec, int m, int nslots, int newest,
+                      double* g) {
+  for (int s = 0; s < kAaMaxDepth; ++s) g[s] = 0.0;
+  std::vector<int> use;  // slots, newest first
+  for (int k = 0; k < nslots; ++k) use.push_back(((newest - k) % m + m) % m);
+  while (!use.empty()) {
+    const int n = (int)use.size();
+    double L[kAaMaxDepth][kAaMaxDepth] = {};
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) dmax = std::max(dmax, A[use[i] * m + use[i]]);
+    bool ok = dmax > 0.0;
+    for (int i = 0; i < n && ok; ++i) {
+      for (int k = 0; k <= i; ++k) {
+        double v = A[use[i] * m + use[k]];
+        for (int t = 0; t < k; ++t) v -= L[i][t] * L[k][t];
+        if (k == i) {
+          if (!(v > 1e-12 * dmax)) {
+            ok = false;
+            break;
+          }
+          L[i][i] = std::sqrt(v);
+        } else {
+          L[i][k] = v / L[k][k];
+        }
+      }
+    }
+    if (ok) {
+      double y[kAaMaxDepth], x[kAaMaxDepth];
+      for (int i = 0; i < n; ++i) {
+        double v = bvec[use[i]];
+        for (int t = 0; t < i; ++t) v -= L[i][t] * y[t];
+        y[i] = v / L[i][i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double v = y[i];
+        for (int t = i + 1; t < n; ++t) v -= L[t][i] * x[t];
+        x[i] = v / L[i][i];
+      }
+      for (int i = 0; i < n; ++i) g[use[i]] = x[i];
+      return;
+    }
+    use.pop_back();  // drop the oldest slot
+  }
+}
+
+// Per column refinement state kept on the host.
+struct ColState {
+  int mode = 1;          // 1 active, 0 finished
+  bool converged = false, failed = false;
+  int iters = 0;
+  double rel = 0.0, rel1 = 0.0, rel2 = 0.0;  // this and the two previous relative corrections
+  std::vector<double> A, b;                    // Gram matrix and right-hand side by slot
+};
+
+int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
+              hps_solve_info* info) {
   cudaStream_t st = H.stream;
   solve_root_scatter(cp.roots, H.nprob, cp.max_nbnd, nrhs, H.uext.as<double>(),
                      H.plan.ext_total, st);
   downward(H, nrhs, false);
-  leaf_out(H, cp, nrhs, false);
+  leaf_out(H, cp.wptr, cp.wrs, nrhs, false);
   ck(cudaGetLastError());
   if (!H.mixed || H.opt.max_refine == 0) return HPS_OK;
-  // ---- iterative refinement against the FP64 residual
-  double last = 0.0;
-  int it = 0;
-  for (it = 1; it <= H.opt.max_refine; ++it) {
+  // ---- iterative refinement against the FP64 residual, Anderson-accelerated
+  // per column (problem, right-hand side); columns finish independently
+  const int m = H.opt.refine_depth;
+  const int ncol = cp.ncol;
+  std::vector<ColState> cs(ncol);
+  for (auto& c : cs) {
+    c.A.assign((size_t)std::max(m, 1) * std::max(m, 1), 0.0);
+    c.b.assign(std::max(m, 1), 0.0);
+  }
+  const size_t stride = kAaMaxDepth + 1;
+  double* h_sum = H.h_aa;                          // ncol * kAaQ
+  double* h_coef = H.h_aa + (size_t)ncol * kAaQ;   // ncol * stride
+  int active = ncol;
+  for (int j = 0; j < H.opt.max_refine && active > 0; ++j) {
     leaf_correction_rhs(H, cp, nrhs);
     for (auto& L : H.lev) {
       if (L.f64)
@@ -885,58 +961,118 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, int nrhs, hps_solve_info* inf
     solve_root_scatter(cp.roots + H.nprob, H.nprob, cp.max_nbnd, nrhs, H.uext.as<double>(),
                        H.plan.ext_total, st);
     downward(H, nrhs, true);
-    const size_t mb = 2 * (size_t)H.nprob * sizeof(unsigned long long);
-    ck(cudaMemsetAsync(H.maxabs.p, 0, mb, st));
-    leaf_out(H, cp, nrhs, true);
+    leaf_out(H, cp.fptr, cp.wrs, nrhs, true);  // F_j, the correction at w_j
+    const int nslots = m > 0 ? std::min(j, m) : 0;
+    const int slot_new = (m > 0 && j >= 1) ? (j - 1) % m : -1;
+    aa_reduce(cp.cols, ncol, cp.nchunks, rb->F.as<double>(), rb->Fprev.as<double>(),
+              rb->dWlast.as<double>(), rb->dF.as<float>(), rb->G.as<double>(), cp.nu,
+              m > 0 ? j : 0, slot_new, nslots, rb->part.as<double>(), rb->colsum.as<double>(), st);
     ck(cudaGetLastError());
-    ck(cudaMemcpyAsync(H.h_maxabs, H.maxabs.p, mb, cudaMemcpyDeviceToHost, st));
+    ck(cudaMemcpyAsync(h_sum, rb->colsum.p, (size_t)ncol * kAaQ * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
     ck(cudaStreamSynchronize(st));
-    // the largest relative update over the problems of the batch
-    const double prev = last;
-    last = 0.0;
-    for (int k = 0; k < H.nprob; ++k) {
-      double dmax, umax;
-      std::memcpy(&dmax, &H.h_maxabs[2 * k], sizeof(double));
-      std::memcpy(&umax, &H.h_maxabs[2 * k + 1], sizeof(double));
-      const double rel = umax > 0 ? dmax / umax : dmax;
-      last = (rel == rel) ? std::max(last, rel) : rel;
-      if (!(last == last)) break;
+    for (int c = 0; c < ncol; ++c) {
+      ColState& S = cs[c];
+      double* cf = h_coef + (size_t)c * stride;
+      for (size_t t = 0; t < stride; ++t) cf[t] = 0.0;
+      if (S.mode == 0) continue;
+      const double* q = h_sum + (size_t)c * kAaQ;
+      const double fmax_ = q[0], wmax = q[1];
+      S.rel2 = S.rel1;
+      S.rel1 = S.rel;
+      S.rel = wmax > 0 ? fmax_ / wmax : fmax_;
+      S.iters = j + 1;
+      if (m > 0 && j >= 1) {
+        for (int t = 0; t < nslots; ++t) {
+          const double v = q[2 + kAaMaxDepth + t];
+          S.A[t * m + slot_new] = v;
+          S.A[slot_new * m + t] = v;
+        }
+      }
+      for (int t = 0; t < nslots; ++t) S.b[t] = q[2 + t];
+      int mode = 1;
+      bool done = false;
+      if (!(S.rel <= 1e300) || (j >= 2 && S.rel > 1.0)) {  // NaN, inf or growing corrections
+        S.failed = true;
+        mode = 0;
+        done = true;
+      } else if (S.rel <= H.opt.refine_tol) {
+        S.converged = true;
+        mode = 2;
+        done = true;
+      } else if (j >= 3 && S.rel > 0.5 * std::min(S.rel1, S.rel2)) {
+        // no longer shrinking: the iterate has reached the accuracy the FP64
+        // residual resolves for this conditioning
+        mode = 2;
+        done = true;
+      } else if (j == H.opt.max_refine - 1) {
+        done = true;
+      }
+      if (mode == 1 && m > 0 && nslots > 0)
+        anderson_weights(S.A.data(), S.b.data(), m, nslots, slot_new, cf + 1);
+      if (mode == 1 && m == 0) mode = 2;
+      cf[0] = mode;
+      if (done) {
+        S.mode = 0;
+        --active;
+      }
     }
-    if (!(last <= 1.0)) break;  // NaN or divergence
-    if (last <= H.opt.refine_tol) break;
-    // the error left after this update is about rho * last, rho = last / prev
-    // the observed contraction: stop when that is below the tolerance
-    if (it >= 2 && last * (last / prev) <= 0.1 * H.opt.refine_tol) {
-      last = last * (last / prev);
-      break;
-    }
-    // stagnation: the update no longer shrinks, i.e. the iterate has reached
-    // the accuracy the FP64 residual can resolve for this conditioning
-    if (it >= 3 && last > 0.5 * prev) break;
+    ck(cudaMemcpyAsync(rb->coef.p, h_coef, (size_t)ncol * stride * sizeof(double),
+                       cudaMemcpyHostToDevice, st));
+    aa_update(cp.cols, ncol, cp.nchunks, rb->F.as<double>(), rb->dWlast.as<double>(),
+              rb->G.as<double>(), cp.nu, nslots, rb->coef.as<double>(), st);
+    ck(cudaGetLastError());
+  }
+  int iters = 0;
+  double worst = 0.0;
+  bool ok = true;
+  for (const auto& S : cs) {
+    iters = std::max(iters, S.iters);
+    worst = (S.rel == S.rel) ? std::max(worst, S.rel) : S.rel;
+    if (!S.converged) ok = false;
   }
   if (info) {
-    info->iterations = std::min(it, H.opt.max_refine);
-    info->last_update = last;
+    info->iterations = iters;
+    info->last_update = worst;
   }
-  if (!(last <= H.opt.refine_tol)) {
+  if (!ok) {
     if (info) info->status = HPS_ENOTCONVERGED;
     return HPS_ENOTCONVERGED;
   }
   return HPS_OK;
 }
 
-// Upload the per-call root descriptors (with f, then with zeros) and the
-// per-leaf output pointers.  f[k] / u[k] are device pointers.
-CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, int nrhs) {
+// Upload the per-call root descriptors (with f, then with zeros), the per-leaf
+// output pointers and, in mixed mode, the refinement layout.  f[k] / u[k] are
+// device pointers.
+CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, int nrhs,
+                    RefineBufs* rb) {
   const Plan& pl = H.plan;
   const int nl = pl.n_leaves();
-  H.call_st.begin(stage_bytes<RootDesc>(2 * H.nprob) + stage_bytes<double*>(nl) +
-                      stage_bytes<int64_t>(nl) + 1024,
+  const bool refine = H.mixed && H.opt.max_refine > 0;
+  const int ncol = H.nprob * nrhs;
+  H.call_st.begin(stage_bytes<RootDesc>(2 * H.nprob) + 2 * stage_bytes<double*>(nl) +
+                      stage_bytes<int64_t>(nl) + (refine ? stage_bytes<AaCol>(ncol) : 0) + 1024,
                   H.stream);
   std::vector<RootDesc> rd(2 * H.nprob);
-  std::vector<double*> wp(nl);
+  std::vector<double*> wp(nl), fp;
   std::vector<int64_t> wr(nl);
+  std::vector<AaCol> cols;
   CallPtrs cp;
+  int64_t nu = 0;  // refinement vector length: every column of every problem
+  for (int k = 0; k < H.nprob; ++k) nu += (int64_t)nrhs * pl.probs[k].nl * pl.probs[k].s.p * pl.probs[k].s.p;
+  if (refine) {
+    const int m = H.opt.refine_depth;
+    rb->F.alloc((size_t)nu * sizeof(double), H.stream);
+    rb->Fprev.alloc((size_t)nu * sizeof(double), H.stream);
+    if (m > 0) {
+      rb->dWlast.alloc((size_t)nu * sizeof(double), H.stream);
+      rb->dF.alloc((size_t)m * nu * sizeof(float), H.stream);
+      rb->G.alloc((size_t)m * nu * sizeof(double), H.stream);
+    }
+    fp.resize(nl);
+  }
+  int64_t fo = 0, ch = 0;
   for (int k = 0; k < H.nprob; ++k) {
     const ProbInfo& pi = pl.probs[k];
     RootDesc r;
@@ -949,14 +1085,48 @@ CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, i
     rd[H.nprob + k] = r;
     cp.max_nbnd = std::max(cp.max_nbnd, pi.nbnd);
     const int pp = pi.s.p * pi.s.p;
+    const int64_t len = (int64_t)pi.nl * pp;
     for (int j = 0; j < pi.nl; ++j) {
       wp[pi.leaf0 + j] = u[k] + (size_t)j * pp;
-      wr[pi.leaf0 + j] = (int64_t)pi.nl * pp;
+      wr[pi.leaf0 + j] = len;
+      if (refine) fp[pi.leaf0 + j] = rb->F.as<double>() + fo + (size_t)j * pp;
     }
+    if (refine)
+      for (int r2 = 0; r2 < nrhs; ++r2) {
+        AaCol c;
+        c.w = u[k] + (size_t)r2 * len;
+        c.off = fo + (int64_t)r2 * len;
+        c.len = len;
+        c.ch0 = ch;
+        ch += (len + kAaChunk - 1) / kAaChunk;
+        cols.push_back(c);
+      }
+    fo += (int64_t)nrhs * len;
   }
   cp.roots = H.call_st.push(rd, H.stream);
   cp.wptr = H.call_st.push(wp, H.stream);
   cp.wrs = H.call_st.push(wr, H.stream);
+  if (refine) {
+    cp.fptr = H.call_st.push(fp, H.stream);
+    cp.cols = H.call_st.push(cols, H.stream);
+    cp.ncol = ncol;
+    cp.nchunks = ch;
+    cp.nu = nu;
+    rb->part.alloc((size_t)ch * kAaQ * sizeof(double), H.stream);
+    rb->colsum.alloc((size_t)ncol * kAaQ * sizeof(double), H.stream);
+    rb->coef.alloc((size_t)ncol * (kAaMaxDepth + 1) * sizeof(double), H.stream);
+    const size_t need = (size_t)ncol * (kAaQ + kAaMaxDepth + 1);
+    if (H.h_aa_cap < need) {
+      if (H.h_aa) {
+        ck(cudaStreamSynchronize(H.stream));
+        cudaFreeHost(H.h_aa);
+        H.h_aa = nullptr;
+        H.h_aa_cap = 0;
+      }
+      ck(cudaMallocHost(&H.h_aa, need * sizeof(double)));
+      H.h_aa_cap = need;
+    }
+  }
   return cp;
 }
 
@@ -993,8 +1163,9 @@ int solve_entry(hps_handle_s& H, const double* const* f, int nrhs, double* const
       uo += nu;
     }
   }
-  CallPtrs cp = stage_call(H, fd.data(), ud.data(), nrhs);
-  int rc = solve_all(H, cp, nrhs, info);
+  RefineBufs rb;
+  CallPtrs cp = stage_call(H, fd.data(), ud.data(), nrhs, &rb);
+  int rc = solve_all(H, cp, &rb, nrhs, info);
   if (!device_ptrs)
     for (int k = 0; k < H.nprob; ++k) {
       const size_t nu = (size_t)nrhs * pl.probs[k].nl * pl.probs[k].s.p * pl.probs[k].s.p;
@@ -1022,7 +1193,8 @@ int build_entry(const hps_problem* probs, int nprob, const hps_options* opt_in, 
   if (opt_in) opt = *opt_in;
   if (opt.precision != HPS_FP64 && opt.precision != HPS_MIXED) return HPS_EINVAL;
   if (opt.precision == HPS_MIXED &&
-      (!(opt.refine_tol > 0) || opt.max_refine < 0 || opt.fp64_top_levels < 0))
+      (!(opt.refine_tol > 0) || opt.max_refine < 0 || opt.fp64_top_levels < 0 ||
+       opt.refine_depth < 0 || opt.refine_depth > kAaMaxDepth))
     return HPS_EINVAL;
   g_last_error.clear();
   hps_handle_s* H = nullptr;
@@ -1096,6 +1268,7 @@ void hps_default_options(hps_options* opt) {
   opt->device_ptrs = 0;
   opt->stream = nullptr;
   opt->form_root_dtn = 0;
+  opt->refine_depth = 3;
 }
 
 int64_t hps_boundary_count(int nx, int ny, int q) { return 2LL * (nx + ny) * q; }

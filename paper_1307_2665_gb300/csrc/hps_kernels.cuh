@@ -114,8 +114,7 @@ template <typename R>
 void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
                double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z = nullptr,
-               int accumulate = 0, unsigned long long* maxabs = nullptr,
-               const int* leaf_prob = nullptr);
+               int accumulate = 0);
 template <typename R>
 void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
                    const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
@@ -150,5 +149,27 @@ void solve_root_scatter(const RootDesc* d, int nprob, int max_nbnd, int nrhs, do
 void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, const double* u3,
                          int64_t u3_total, double* uext, int64_t ext_total, int nrhs,
                          cudaStream_t st);
+
+// ---- accelerated refinement (hps_refine.cu)
+constexpr int kAaMaxDepth = 8;               // longest Anderson history
+constexpr int kAaChunk = 8192;               // elements per reduction chunk
+constexpr int kAaQ = 2 + 2 * kAaMaxDepth;    // partials per chunk
+// One right-hand side of one problem: w (the iterate, the caller's u) and the
+// column's range [off, off + len) in the work vectors; its chunks are
+// ch0 .. ch0 + ceil(len / kAaChunk) - 1.
+struct AaCol {
+  double* w;
+  int64_t off, len, ch0;
+};
+// Forms dF_new = F - Fprev and G_new = dWlast + dF_new in ring slot slot_new
+// (j >= 1), sets Fprev = F, and reduces per column: colsum[c*kAaQ + q] with
+// q = 0 max|F|, 1 max|w|, 2 + s <dF_s, F>, 2 + kAaMaxDepth + s <dF_s, dF_new>.
+void aa_reduce(const AaCol* cols, int ncol, int64_t nchunks, const double* F, double* Fprev,
+               const double* dWlast, float* dF, double* G, int64_t nu, int j, int slot_new,
+               int nslots, double* part, double* colsum, cudaStream_t st);
+// w += F - sum_s gamma_s G_s (mode 1, also dWlast = that update), w += F
+// (mode 2) or nothing (mode 0), per column from coef[c*(kAaMaxDepth+1) ...].
+void aa_update(const AaCol* cols, int ncol, int64_t nchunks, const double* F, double* dWlast,
+               const double* G, int64_t nu, int nslots, const double* coef, cudaStream_t st);
 
 }  // namespace hps

@@ -248,13 +248,16 @@ void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const d
 }
 
 // ------------------------------------------------------------ post-process
-// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 4.3), computed in the
-// element type R of Y, right-hand sides in chunks of RC.
+// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 4.3), right-hand sides in
+// chunks of RC.  The interior rows Y u_e (+ z) run in the element type R of Y.
+// The boundary rows L1 u_e run in FP64: they are the values that neighbouring
+// leaves share and must stay consistent between them.  They are formed first,
+// side by side for all threads (4 p values per right-hand side, each a q-term
+// dot product), then read back per node: a corner is the mean of its two
+// sides' values (Section 3.2, Step 1).
 // u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or has it added in
 // FP64 (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior values
-// (ld ni).  maxabs (optional) receives, for problem k = leaf_prob[leaf],
-// max |w_full| (slot 2k) and, after accumulation, max |u| (slot 2k+1), as the
-// bit patterns of non-negative doubles; a NaN counts as +inf.
+// (ld ni).
 template <typename R>
 __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int64_t ys, int l0,
                                                    const double* __restrict__ uext,
@@ -262,8 +265,6 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
                                                    int64_t ext_total, int p, int q, int nrhs,
                                                    const double* __restrict__ gPg2c,
                                                    const R* __restrict__ z, int accumulate,
-                                                   unsigned long long* maxabs,
-                                                   const int* __restrict__ leaf_prob,
                                                    double* const* __restrict__ wptr,
                                                    const int64_t* __restrict__ wrs) {
   constexpr int RC = 16;
@@ -271,7 +272,8 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
   double* Pg = smd;                               // p x q
   double* ued = Pg + p * q;                       // nq x RC, FP64 (boundary rows)
-  R* uer = reinterpret_cast<R*>(ued + nq * RC);   // nq x RC, element type of Y (interior rows)
+  double* bnd = ued + nq * RC;                    // 4 sides x p points x RC: L1 u_e per side
+  R* uer = reinterpret_cast<R*>(bnd + 4 * p * RC);  // nq x RC, element type of Y (interior rows)
   const int l = blockIdx.x;  // group-local leaf
   const int64_t off = leaf_off[l0 + l];
   double* const wl = wptr[l0 + l];
@@ -279,7 +281,6 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
   const R* Yl = Y + (size_t)l * ys;
   const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
-  double mdw = 0.0, mu = 0.0;
   for (int r0 = 0; r0 < nrhs; r0 += RC) {
     const int nr = min(RC, nrhs - r0);
     __syncthreads();
@@ -288,6 +289,14 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
       const double v = rr < nr ? uext[(size_t)(r0 + rr) * ext_total + off + g] : 0.0;
       ued[g * RC + rr] = v;
       uer[g * RC + rr] = (R)v;
+    }
+    __syncthreads();
+    // side values: bnd[(sd*p + j)*RC + rr] = sum_k Pg[j][k] u_e[sd*q + k]
+    for (int e = threadIdx.x; e < 4 * p * RC; e += blockDim.x) {
+      const int rr = e % RC, j = (e / RC) % p, sd = e / (RC * p);
+      double v = 0.0;
+      for (int k = 0; k < q; ++k) v = fma(Pg[j * q + k], ued[(sd * q + k) * RC + rr], v);
+      bnd[e] = v;
     }
     __syncthreads();
     for (int node = threadIdx.x; node < pp; node += blockDim.x) {
@@ -309,42 +318,30 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
 #pragma unroll
         for (int rr = 0; rr < RC; ++rr) out[rr] = (double)acc[rr];
       } else {
-        // boundary: L1 u_e in FP64 (the boundary values are defined by the Gauss
-        // values and must stay consistent between neighbouring leaves)
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) out[rr] = 0.0;
+        // boundary: the side value (S row a = 0 and N row a = p-1 indexed by b,
+        // E column b = p-1 and W column b = 0 indexed by a), a corner the mean
+        // of its two sides
         const int sides[4][2] = {{0, b}, {2, b}, {1, a}, {3, a}};
         const bool on[4] = {a == 0, a == p - 1, b == p - 1, b == 0};
-        for (int t = 0; t < 4; ++t) {
-          if (!on[t]) continue;
-          const int sd = sides[t][0], j = sides[t][1];
-          const double w = (j == 0 || j == p - 1) ? 0.5 : 1.0;
-          for (int k = 0; k < q; ++k) {
-            const double c = w * Pg[j * q + k];
-#pragma unroll
-            for (int rr = 0; rr < RC; ++rr) out[rr] = fma(c, ued[(sd * q + k) * RC + rr], out[rr]);
+        int s1 = -1, s2 = -1;
+        for (int t = 0; t < 4; ++t)
+          if (on[t]) {
+            const int idx = sides[t][0] * p + sides[t][1];
+            if (s1 < 0)
+              s1 = idx;
+            else
+              s2 = idx;
           }
-        }
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr)
+          out[rr] = s2 < 0 ? bnd[s1 * RC + rr] : 0.5 * (bnd[s1 * RC + rr] + bnd[s2 * RC + rr]);
       }
       for (int rr = 0; rr < nr; ++rr) {
         double* up = wl + (size_t)(r0 + rr) * wstride + node;
         double v = out[rr];
-        mdw = (v == v) ? fmax(mdw, fabs(v)) : INFINITY;
         if (accumulate) v += *up;
-        mu = (v == v) ? fmax(mu, fabs(v)) : INFINITY;
         *up = v;
       }
-    }
-  }
-  if (maxabs) {
-    for (int o = 16; o > 0; o >>= 1) {
-      mdw = fmax(mdw, __shfl_xor_sync(0xffffffffu, mdw, o));
-      mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      unsigned long long* slot = maxabs + 2 * leaf_prob[l0 + l];
-      atomicMax(&slot[0], (unsigned long long)__double_as_longlong(mdw));
-      atomicMax(&slot[1], (unsigned long long)__double_as_longlong(mu));
     }
   }
 }
@@ -353,17 +350,24 @@ template <typename R>
 void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
                double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z,
-               int accumulate, unsigned long long* maxabs, const int* leaf_prob) {
+               int accumulate) {
   if (nleaves <= 0 || nrhs <= 0) return;
-  size_t smem = (size_t)(p * q + 4 * q * 16) * sizeof(double) + (size_t)4 * q * 16 * sizeof(R);
+  const size_t smem = (size_t)(p * q + 4 * q * 16 + 4 * p * 16) * sizeof(double) +
+                      (size_t)4 * q * 16 * sizeof(R);
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_leaf_post<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024) != cudaSuccess)
+      return;
+    attr = true;
+  }
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
   prof::Scope sc(tname<R>("leaf_post<f64>", "leaf_post<f32>"), st,
                  (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
                  (double)nleaves * (ni * nq * sizeof(R) +
                                     nrhs * (nq + (double)p * p * (accumulate ? 2 : 1)) * 8.0));
   k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, ys, l0, uext, leaf_ext_off, ext_total, p, q, nrhs,
-                                             d_Pg2c, z, accumulate, maxabs, leaf_prob, wptr,
-                                             wrs);
+                                             d_Pg2c, z, accumulate, wptr, wrs);
 }
 
 // ------------------------------------------------------------ FP64 residual
@@ -401,24 +405,35 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
     D2[e] = s;
   }
   R* rl = rbuf + (size_t)jl * ni * nrhs;
-  const bool has12 = cp.c[1] != nullptr, has2 = cp.c[4] != nullptr;
+  const bool has12 = cp.c[1] != nullptr, has1 = cp.c[3] != nullptr, has2 = cp.c[4] != nullptr,
+             has0 = cp.c[5] != nullptr;
   for (int r = 0; r < nrhs; ++r) {
     __syncthreads();
     for (int e = threadIdx.x; e < pp; e += blockDim.x) W[e] = wl[(size_t)r * wstride + e];
     __syncthreads();
-    for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-      int a = e / p, b = e % p;
-      double s = 0.0;
-      for (int d = 0; d < p; ++d) s = fma(D[b * p + d], W[a * p + d], s);
-      Wx[e] = sx * s;
+    if (has12) {  // Dx w at every node: the mixed term differentiates it along y
+      for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+        int a = e / p, b = e % p;
+        double s = 0.0;
+        for (int d = 0; d < p; ++d) s = fma(D[b * p + d], W[a * p + d], s);
+        Wx[e] = sx * s;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int ri = threadIdx.x; ri < ni; ri += blockDim.x) {
       const int a = ri / pi + 1, b = ri % pi + 1, node = a * p + b;
-      double dxx = 0.0, dyy = 0.0, dy = 0.0, dxy = 0.0;
+      double dxx = 0.0, dyy = 0.0, dx = 0.0, dy = 0.0, dxy = 0.0;
       for (int k = 0; k < p; ++k) {
         dxx = fma(D2[b * p + k], W[a * p + k], dxx);
         dyy = fma(D2[a * p + k], W[k * p + b], dyy);
+      }
+      if (has1) {
+        if (has12) {
+          dx = Wx[node];
+        } else {
+          for (int k = 0; k < p; ++k) dx = fma(D[b * p + k], W[a * p + k], dx);
+          dx *= sx;
+        }
       }
       if (has2)
         for (int k = 0; k < p; ++k) dy = fma(D[a * p + k], W[k * p + b], dy);
@@ -428,9 +443,11 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
       dyy *= sy * sy;
       dy *= sy;
       dxy *= sy;
-      const double Aw = -cf[node] * dxx - 2.0 * cf[pp + node] * dxy - cf[2 * pp + node] * dyy +
-                        cf[3 * pp + node] * Wx[node] + cf[4 * pp + node] * dy +
-                        cf[5 * pp + node] * W[node];
+      double Aw = -cf[node] * dxx - cf[2 * pp + node] * dyy;
+      if (has12) Aw -= 2.0 * cf[pp + node] * dxy;
+      if (has1) Aw += cf[3 * pp + node] * dx;
+      if (has2) Aw += cf[4 * pp + node] * dy;
+      if (has0) Aw += cf[5 * pp + node] * W[node];
       rl[ri + (size_t)r * ni] = (R)(-Aw);
     }
   }
@@ -452,7 +469,13 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
     attr = true;
   }
   const double pp = (double)p * p, ni = (double)(p - 2) * (p - 2);
-  prof::Scope sc("leaf_residual<f64>", st, (double)nl * nrhs * (2.0 * pp * p + 8.0 * ni * p),
+  // FP64 flops actually issued: Dxx, Dyy at the interior nodes, plus the terms
+  // of the coefficients present (Dx w everywhere only for the mixed term)
+  double per = 4.0 * ni * p;
+  if (coef[1]) per += 2.0 * pp * p + 2.0 * ni * p;
+  else if (coef[3]) per += 2.0 * ni * p;
+  if (coef[4]) per += 2.0 * ni * p;
+  prof::Scope sc("leaf_residual<f64>", st, (double)nl * nrhs * per,
                  (double)nl * (nrhs * (pp * 8.0 + ni * sizeof(R)) + 6.0 * pp * 8.0));
   k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, l0, p, hsc, d_D, wptr, wrs, nrhs, rbuf);
 }
@@ -539,7 +562,7 @@ void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int 
                             const double*, const double*, R*, cudaStream_t);                    \
   template void leaf_post<R>(const R*, int64_t, int, const double*, const int64_t*, int64_t, int, \
                              int, int, int, const double*, double* const*, const int64_t*,      \
-                             cudaStream_t, const R*, int, unsigned long long*, const int*);     \
+                             cudaStream_t, const R*, int);                                      \
   template void leaf_residual<R>(const double* const*, int, int, int, const double2*,           \
                                  const double*, double* const*, const int64_t*, int, R*,        \
                                  cudaStream_t);                                                 \

@@ -51,7 +51,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("form_root_dtn", ctypes.c_int)]
+                ("form_root_dtn", ctypes.c_int), ("refine_depth", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -194,7 +194,7 @@ class Handle:
 
 
 def _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
-             form_root_dtn):
+             form_root_dtn, refine_depth=None):
     opt = default_options()
     opt.precision = precision
     opt.device_ptrs = 1 if device_ptrs else 0
@@ -206,6 +206,8 @@ def _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_le
         opt.max_refine = max_refine
     if fp64_top_levels is not None:
         opt.fp64_top_levels = fp64_top_levels
+    if refine_depth is not None:
+        opt.refine_depth = refine_depth
     return opt
 
 
@@ -231,10 +233,10 @@ class BatchHandle:
 
 def hps_build_batch(problems, precision=HPS_FP64, device_ptrs=False, stream=None,
                     refine_tol=None, max_refine=None, fp64_top_levels=None, form_root_dtn=False,
-                    check=True):
+                    refine_depth=None, check=True):
     """Batch build.  problems: list of dicts with keys domain, nx, ny, p, q, coeffs."""
     opt = _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
-                   form_root_dtn)
+                   form_root_dtn, refine_depth)
     arr = (Problem * len(problems))()
     for i, pr in enumerate(problems):
         arr[i].d = _domain(pr["domain"])
@@ -266,20 +268,11 @@ def hps_solve_batch(h: BatchHandle, fs, us, info=None, check=True):
 
 def hps_build(domain, nx, ny, p, q, coeffs, precision=HPS_FP64, device_ptrs=False, stream=None,
               refine_tol=None, max_refine=None, fp64_top_levels=None, form_root_dtn=False,
-              check=True):
+              refine_depth=None, check=True):
     """Build stage.  coeffs: dict name -> array of nx*ny*p*p values (or None).
     Returns a Handle, or raises HpsError (returns the status when check=False)."""
-    opt = default_options()
-    opt.precision = precision
-    opt.device_ptrs = 1 if device_ptrs else 0
-    opt.stream = stream
-    opt.form_root_dtn = 1 if form_root_dtn else 0
-    if refine_tol is not None:
-        opt.refine_tol = refine_tol
-    if max_refine is not None:
-        opt.max_refine = max_refine
-    if fp64_top_levels is not None:
-        opt.fp64_top_levels = fp64_top_levels
+    opt = _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
+                   form_root_dtn, refine_depth)
     arrs = [coeffs.get(k) for k in COEFF_NAMES]
     out = ctypes.c_void_p()
     st = lib().hps_build(_domain(domain), nx, ny, p, q, *[_ptr(a) for a in arrs],

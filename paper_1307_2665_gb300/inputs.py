@@ -181,3 +181,23 @@ def fourier_boundary(seed, x, y, domain, nmodes=20):
 def sample_coefficients(fn, xy):
     """Evaluate a coefficient function at node coordinates xy[..., 2]."""
     return fn(xy[..., 0], xy[..., 1])
+
+
+def sample_on_leaf_grid(fn, xs, ys, nx, ny, p):
+    """Coefficient samples of fn at every leaf's Chebyshev grid, evaluated on
+    the tensor-product grid: xs (nx*p,) holds the x coordinates of the columns
+    of leaves ix = 0..nx-1 in turn, ys (ny*p,) the y coordinates of the rows.
+    Returns {name: (ny*nx, p, p) or None}, leaf l = iy*nx + ix, row index along
+    y.  For large grids this evaluates each factor of a separable field once per
+    grid line instead of once per node."""
+    out = fn(np.asarray(xs, np.float64)[None, :], np.asarray(ys, np.float64)[:, None])
+    res = {}
+    for k in COEFF_NAMES:
+        v = out.get(k)
+        if v is None:
+            res[k] = None
+            continue
+        g = np.broadcast_to(np.asarray(v, np.float64), (ny * p, nx * p))
+        res[k] = np.ascontiguousarray(g.reshape(ny, p, nx, p).transpose(0, 2, 1, 3)
+                                      .reshape(ny * nx, p, p))
+    return res

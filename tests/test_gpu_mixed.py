@@ -87,3 +87,41 @@ def test_not_converged_is_reported():
     u, info = run(UNIT, 4, 4, 12, 10, co, f, max_refine=1, refine_tol=1e-15)
     assert info.status == hps.HPS_ENOTCONVERGED and info.iterations == 1
     assert np.all(np.isfinite(u))
+
+
+@pytest.mark.parametrize("depth", [0, 1, 3, 8])
+def test_refinement_depths_match_oracle(depth):
+    """Plain refinement (depth 0) and Anderson histories of 1, 3 and 8 all reach
+    the FP64 solution."""
+    co, f = setup(SKEW, 6, 4, 12, 10, varcoef)
+    u, info = run(SKEW, 6, 4, 12, 10, co, f, refine_depth=depth)
+    assert info.status == hps.HPS_OK, (info.iterations, info.last_update)
+    sol = O.solve_condensed(O.make_problem(SKEW, 6, 4, 12, 10, varcoef), f.T)
+    assert np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w)) < TOL
+
+
+def test_acceleration_needs_fewer_corrections():
+    """kappa = 80 on 32 x 32 leaves: the FP32 factors leave a slowly decaying
+    error mode; the accelerated iteration removes it in fewer corrections than
+    plain refinement, and both reach the oracle."""
+    co, f = setup(UNIT, 32, 32, 16, 14, I.gaussian_bump_helmholtz, seeds=(3,))
+    u0, i0 = run(UNIT, 32, 32, 16, 14, co, f, refine_depth=0, max_refine=30)
+    u3, i3 = run(UNIT, 32, 32, 16, 14, co, f, refine_depth=3, max_refine=30)
+    assert i0.status == hps.HPS_OK and i3.status == hps.HPS_OK
+    assert i3.iterations < i0.iterations, (i3.iterations, i0.iterations)
+    sol = O.solve_condensed(O.make_problem(UNIT, 32, 32, 16, 14, I.gaussian_bump_helmholtz), f.T)
+    for u in (u0, u3):
+        assert np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w)) < TOL
+
+
+@pytest.mark.parametrize("precision", [hps.HPS_FP64, hps.HPS_MIXED])
+def test_each_rhs_is_independent_of_the_others(precision):
+    """Every right-hand side is eliminated and refined on its own, so solving
+    it alone or among others gives the same bits."""
+    co, f = setup(SKEW, 5, 4, 12, 10, varcoef, seeds=(0, 1, 2))
+    h = hps.hps_build(SKEW, 5, 4, 12, 10, co, precision=precision)
+    together = hps.hps_solve(h, f)
+    for r in range(f.shape[0]):
+        alone = hps.hps_solve(h, np.ascontiguousarray(f[r:r + 1]))
+        assert np.array_equal(alone[0], together[r]), r
+    h.close()
