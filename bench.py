@@ -457,6 +457,120 @@ def run_native(args):
     return 0
 
 
+# ------------------------------------------------------------- serving
+def run_serve(args):
+    """Request stream of the serving loop: Poisson arrivals, builds and solves
+    on resident operators; reports latency percentiles and solves/s."""
+    import threading
+
+    import torch
+    from paper_1307_2665_gb300 import hps
+    from paper_1307_2665_gb300 import inputs as I
+    from paper_1307_2665_gb300.build import build
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank != 0:  # replicas: each GPU would serve its own stream; one is measured
+        return 0
+    torch.cuda.set_device(local)
+    build()
+    nreq, rate = args.requests, args.rate
+    rng = np.random.Generator(np.random.PCG64(7))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    kinds = (rng.random(nreq) < 0.1).astype(int)  # 1 = build
+    kinds[:4] = 1  # the stream opens with builds
+    nmax = args.leaves or 128
+    builds, ops_inputs = [], []
+    for i in np.nonzero(kinds)[0]:
+        n = int(round(np.exp(rng.uniform(np.log(16), np.log(nmax)))))
+        helm = len(builds) % 2 == 1
+        kappa = float(rng.uniform(10, 60))
+        fn = (lambda k: (lambda x, y: I.constant_helmholtz(x, y, k)))(kappa) if helm else I.laplace
+        xy = hps.hps_cheb_nodes(UNIT_SQ, n, n, 16)
+        co = I.sample_on_leaf_grid(fn, xy[:n, 0, :, 0].reshape(-1), xy[::n, :, 0, 1].reshape(-1),
+                                   n, n, 16)
+        del xy
+        bxy = hps.hps_boundary_nodes_grid(UNIT_SQ, n, n, 14)
+        bank = I.fourier_boundary_bank(1000 + len(builds), bxy[:, 0], bxy[:, 1], UNIT_SQ, 256)
+        builds.append(int(i))
+        ops_inputs.append((dict(domain=UNIT_SQ, nx=n, ny=n, p=16, q=14, coeffs=co), bank,
+                           "helmholtz kappa=%.1f" % kappa if helm else "laplace"))
+    nrhs_of = np.maximum(1, np.round(np.exp(rng.uniform(0, np.log(256), nreq)))).astype(int)
+    pick = rng.random(nreq)
+    prec = hps.HPS_MIXED if args.serve_precision == "mixed" else hps.HPS_FP64
+    srv = hps.Server(workers=args.workers, max_rhs_per_solve=256)
+    ids = [None] * nreq
+    op_of_build = {}
+    t0 = time.perf_counter()
+
+    def submitter():
+        done_builds = []
+        bi = 0
+        for i in range(nreq):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if kinds[i]:
+                pr, bank, _ = ops_inputs[bi]
+                ids[i] = srv.submit_build(pr, precision=prec, max_refine=MAX_REFINE)
+                op_of_build[bi] = ids[i]
+                bi += 1
+            else:
+                # a uniformly chosen resident operator (built and not evicted);
+                # before the first build completes, any submitted one
+                done_builds[:] = [b for b in op_of_build
+                                  if srv.wait(op_of_build[b], 0.0).status == hps.HPS_OK]
+                cand = done_builds or list(op_of_build)
+                b = cand[int(pick[i] * len(cand))]
+                bank = ops_inputs[b][1]
+                k = int(nrhs_of[i])
+                s0 = int((pick[i] * 7919) % (257 - k))
+                ids[i] = srv.submit_solve(op_of_build[b], bank[s0:s0 + k])
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat_b, lat_s, rhs_done, t_last, failed, batched = [], [], 0, 0.0, 0, 0
+    t_first = None
+    iters = []
+    for i in range(nreq):
+        while ids[i] is None:
+            time.sleep(0.0005)
+        info = srv.wait(ids[i])
+        lat = info.t_end - (info.t_submit)
+        if info.status not in (hps.HPS_OK,):
+            failed += 1
+        if kinds[i]:
+            lat_b.append(lat)
+        else:
+            lat_s.append(lat)
+            rhs_done += info.nrhs
+            batched += info.batch_rhs > info.nrhs
+            iters.append(info.iterations)
+            srv.release(ids[i])
+        t_last = max(t_last, info.t_end)
+        t_first = info.t_submit if t_first is None else min(t_first, info.t_submit)
+    th.join()
+    stats = srv.stats()
+    srv.close()
+    span = t_last - t_first  # server clock: first submission to last completion
+    pct = lambda v, q: float(np.percentile(np.asarray(v) * 1e3, q)) if v else None
+    line = {"metric": "serving: solves/s and p50/p99 latency (arrival to result), Poisson stream",
+            "value": rhs_done / span, "unit": "RHS/s", "n_gpus": 1, "higher_is_better": True,
+            "data": "synthetic",
+            "dtype": "f32+f64 (mixed, refined to 1e-11)" if prec == hps.HPS_MIXED else "f64",
+            "config": {"workload": f"{nreq} requests at {rate}/s, 10% builds (n log-uniform in "
+                                   f"[16, {nmax}], p=16, q=14, Laplace / Helmholtz kappa~U[10,60]), "
+                                   f"90% solves with nrhs log-uniform in [1, 256]",
+                       "workers": args.workers, "max_rhs_per_solve": 256},
+            "latency_ms": {"solve_p50": pct(lat_s, 50), "solve_p99": pct(lat_s, 99),
+                           "build_p50": pct(lat_b, 50), "build_p99": pct(lat_b, 99),
+                           "all_p50": pct(lat_s + lat_b, 50), "all_p99": pct(lat_s + lat_b, 99)},
+            "requests_per_s": nreq / span, "span_s": span, "failed": failed,
+            "coalesced_requests": int(batched), "refine_iterations_median": float(np.median(iters)),
+            "server": stats}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,7 +578,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="convdiff64",
-                    choices=["convdiff64", "helmholtz256", "batch64"])
+                    choices=["convdiff64", "helmholtz256", "batch64", "serve"])
+    ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
+    ap.add_argument("--workers", type=int, default=4, help="serve: concurrent device jobs")
+    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--ref-leaves", type=int, default=32,
                     help="leaves per side of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -476,6 +594,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_native(args)
 
 

@@ -177,6 +177,20 @@ int hps_solve_ex(hps_handle h, const double* f, int nrhs, double* u, int device_
  * total nbnd, bytes of device memory held.  Any output pointer may be NULL. */
 int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_t* device_bytes);
 
+/* Device memory estimates from the plan alone (no device work): build_peak,
+ * the most held during hps_build / hps_build_batch of these problems with
+ * these options; resident, what the handle keeps afterwards (S and Y, and in
+ * mixed mode W, [T13; T23] and the coefficients); solve, the workspace one
+ * solve with nrhs right-hand sides adds while it runs (u excluded).  Any
+ * output pointer may be NULL.  The serving loop admits work by these. */
+int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* opt, int nrhs,
+                       int64_t* build_peak, int64_t* resident, int64_t* solve);
+
+/* Release the solve workspace a handle caches between solves (exterior-value
+ * pools, refinement buffers, staging); the next solve allocates it again.
+ * Must not overlap a solve on the same handle. */
+int hps_release_workspace(hps_handle h);
+
 /* Release every resource of the handle (NULL is accepted). */
 int hps_free(hps_handle h);
 

@@ -20,7 +20,7 @@ CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libhps.so"
 SOURCES = ["hps_host.cpp", "hps_prof.cpp", "hps_linalg.cu", "hps_leaf.cu", "hps_merge.cu",
-           "hps_refine.cu", "hps_api.cu"]
+           "hps_refine.cu", "hps_api.cu", "hps_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(ROOT / "include")]
 
@@ -40,7 +40,8 @@ def _digest():
     for name in sorted(os.listdir(CSRC)):
         h.update(name.encode())
         h.update((CSRC / name).read_bytes())
-    h.update((ROOT / "include" / "hps.h").read_bytes())
+    for hdr in sorted((ROOT / "include").glob("*.h")):
+        h.update(hdr.read_bytes())
     h.update(" ".join(ARCH + CFLAGS).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
@@ -71,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = OUT_DIR / "libhps.so.tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcudart"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs), "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1339,6 +1339,93 @@ int hps_solve_batch(hps_handle h, const double* const* f, int nrhs, double* cons
   return solve_guarded(h, f, nrhs, u, h->opt.device_ptrs, info);
 }
 
+int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* opt_in, int nrhs,
+                       int64_t* build_peak, int64_t* resident, int64_t* solve) {
+  if (!probs || nprob < 1 || nrhs < 0) return HPS_EINVAL;
+  hps_options opt;
+  hps_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  std::vector<ProblemSpec> specs(nprob);
+  int64_t coef_bytes = 0;
+  for (int k = 0; k < nprob; ++k) {
+    const hps_problem& P = probs[k];
+    const int v = validate(P.d, P.nx, P.ny, P.p, P.q);
+    if (v != HPS_OK) return v;
+    specs[k] = {P.d.x0, P.d.x1, P.d.y0, P.d.y1, P.nx, P.ny, P.p, P.q};
+    const double* c[6] = {P.c11, P.c12, P.c22, P.c1, P.c2, P.c};
+    for (int i = 0; i < 6; ++i)
+      if (c[i]) coef_bytes += (int64_t)P.nx * P.ny * P.p * P.p * 8;
+  }
+  try {
+    const Plan pl = make_forest(specs);
+    const bool mixed = opt.precision == HPS_MIXED;
+    const int top = std::max(0, opt.fp64_top_levels);
+    const int64_t bl = mixed ? 4 : 8;
+    int64_t y = 0, leaf_tmp = 0, dof = 0, nint = 0;
+    for (const auto& pi : pl.probs) {
+      const int64_t ni = (int64_t)(pi.s.p - 2) * (pi.s.p - 2), nq = 4LL * pi.s.q;
+      y += pi.nl * ni * (nq + (mixed ? ni : 0)) * bl;
+      leaf_tmp += pi.nl * (ni * ni + nq * nq) * bl;
+      dof += (int64_t)pi.nl * pi.s.p * pi.s.p;
+      nint += pi.nl * ni;
+    }
+    // per height: stored S (+ W, [T13; T23] in mixed mode), transient T, A_w
+    std::vector<int64_t> t_at(pl.height + 1, 0), tmp_at(pl.height + 1, 0);
+    int64_t sres = 0, u3_rows = 0, max_level_rows = 0;
+    t_at[0] = 0;
+    for (const auto& pi : pl.probs) t_at[0] += pi.nl * 16LL * pi.s.q * pi.s.q * bl;
+    for (int h = 1; h <= pl.height; ++h) {
+      int64_t rows = 0;
+      for (int b : pl.levels[h]) {
+        const Box& B = pl.boxes[b];
+        const MergeShape& sh = pl.shapes[B.shape];
+        const int ph = pl.probs[B.prob].height;
+        const int64_t bm = (!mixed || h > ph - top) ? 8 : 4;
+        sres += (int64_t)sh.m * (sh.ne + (mixed ? sh.m : 0)) * bm;
+        if (mixed) sres += (int64_t)sh.ne * sh.m * bm;
+        if (B.parent >= 0 || opt.form_root_dtn) t_at[h] += (int64_t)sh.ne * sh.ne * bm;
+        tmp_at[h] += (int64_t)sh.m * sh.m * bm + (mixed ? 0 : (int64_t)sh.ne * sh.m * bm);
+        u3_rows += sh.m;
+        rows += sh.m;
+      }
+      max_level_rows = std::max(max_level_rows, rows);
+    }
+    const int64_t res = y + sres + (mixed ? coef_bytes : 0);
+    int64_t peak = leaf_tmp;
+    for (int h = 1; h <= pl.height; ++h) peak = std::max(peak, t_at[h - 1] + t_at[h] + tmp_at[h]);
+    peak += y + sres + coef_bytes;
+    int64_t work = (int64_t)nrhs * (pl.ext_total + u3_rows) * 8 + 2 * (int64_t)nrhs * max_level_rows * 8;
+    if (mixed && opt.max_refine > 0) {
+      const int64_t m = std::max(0, opt.refine_depth);
+      work += (int64_t)nrhs * pl.ext_total * 8 + 2 * nint * nrhs * 4 + 2 * u3_rows * nrhs * 8;
+      work += (int64_t)nrhs * dof * (24 + (m > 0 ? 12 * m : -16));
+    }
+    if (build_peak) *build_peak = peak;
+    if (resident) *resident = res;
+    if (solve) *solve = work;
+  } catch (...) {
+    return HPS_ENOMEM;
+  }
+  return HPS_OK;
+}
+
+int hps_release_workspace(hps_handle h) {
+  if (!h) return HPS_EINVAL;
+  for (PoolBuf* x : {&h->uext, &h->u3, &h->hpool, &h->split_ws, &h->fstage, &h->ustage,
+                     &h->solve_st.dev, &h->call_st.dev})
+    x->release();
+  for (auto& G : h->lg) {
+    G.rleaf->release();
+    G.zleaf->release();
+  }
+  for (auto& L : h->lev) {
+    L.rlev->release();
+    L.zlev->release();
+  }
+  h->cache_nrhs = 0;
+  return HPS_OK;
+}
+
 int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_t* device_bytes) {
   if (!h) return HPS_EINVAL;
   if (n_leaves) *n_leaves = h->plan.n_leaves();

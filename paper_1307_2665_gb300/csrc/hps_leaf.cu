@@ -132,13 +132,8 @@ void leaf_assemble(const double* const* coef, int l0, int nleaves, int p, int q,
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
   size_t smem = (size_t)(2 * p * p + 2 * p * q + 6 * p * p) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_leaf_assemble<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
-      return;  // reported by the caller's launch check
-    attr = true;
-  }
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_assemble<R>), 200 * 1024))
+    return;  // reported by the caller's launch check
   const double ni = (double)(p - 2) * (p - 2);
   int ncoef = 0;
   for (int k = 0; k < 6; ++k) ncoef += coef[k] != nullptr;
@@ -233,13 +228,8 @@ void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const d
               cudaStream_t st) {
   if (nleaves <= 0) return;
   size_t smem = (size_t)(p * p + 2 * p * q + p * p * 8 + 4 * p * 8) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_leaf_dtn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
-      return;  // reported by the caller's launch check
-    attr = true;
-  }
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_dtn<R>), 200 * 1024))
+    return;  // reported by the caller's launch check
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
   prof::Scope sc(tname<R>("leaf_dtn<f64>", "leaf_dtn<f32>"), st,
                  (double)nleaves * nq * (8.0 * p * p + 2.0 * nq * p),
@@ -354,13 +344,8 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
   if (nleaves <= 0 || nrhs <= 0) return;
   const size_t smem = (size_t)(p * q + 4 * q * 16 + 4 * p * 16) * sizeof(double) +
                       (size_t)4 * q * 16 * sizeof(R);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_leaf_post<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
-      return;
-    attr = true;
-  }
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_post<R>), 200 * 1024))
+    return;  // reported by the caller's launch check
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
   prof::Scope sc(tname<R>("leaf_post<f64>", "leaf_post<f32>"), st,
                  (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
@@ -461,13 +446,8 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
   size_t smem = (size_t)(10 * p * p) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_leaf_residual<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024) != cudaSuccess)
-      return;
-    attr = true;
-  }
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_residual<R>), 200 * 1024))
+    return;  // reported by the caller's launch check
   const double pp = (double)p * p, ni = (double)(p - 2) * (p - 2);
   // FP64 flops actually issued: Dxx, Dyy at the interior nodes, plus the terms
   // of the coefficients present (Dx w everywhere only for the mixed term)

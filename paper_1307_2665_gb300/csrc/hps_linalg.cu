@@ -521,13 +521,8 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
   // per-CTA maximum less the kernel's static shared arrays (taller panels are
   // factored in global memory)
   const int smem_max = 224 * 1024;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_lu_panel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-    if (e != cudaSuccess) return;  // reported by the caller's launch check
-    attr_done = true;
-  }
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel<R>), smem_max))
+    return;  // reported by the caller's launch check
   const int cols_per_cta = 64;
   for (int k0 = 0; k0 < max_m; k0 += kNB) {
     if (factor) {

@@ -78,25 +78,27 @@ int64_t launches() {
   return n_launches;
 }
 
-Scope::Scope(const char* name, cudaStream_t st, double flops, double bytes) : st_(st) {
+Scope::Scope(const char* name, cudaStream_t st, double flops, double bytes)
+    : name_(name), st_(st), flops_(flops), bytes_(bytes) {
   std::lock_guard<std::mutex> g(mu);
   ++n_launches;
   if (!on) return;
-  Rec r;
-  r.name = name;
-  r.a = get_event();
-  r.b = get_event();
-  r.flops = flops;
-  r.bytes = bytes;
-  cudaEventRecord(r.a, st);
-  pending.push_back(r);
-  slot_ = (int)pending.size() - 1;
+  a_ = get_event();
+  b_ = get_event();
+  cudaEventRecord(a_, st);
 }
 
 Scope::~Scope() {
-  if (slot_ < 0) return;
+  if (!a_) return;
+  cudaEventRecord(b_, st_);
   std::lock_guard<std::mutex> g(mu);
-  if (slot_ < (int)pending.size()) cudaEventRecord(pending[slot_].b, st_);
+  Rec r;
+  r.name = name_;
+  r.a = a_;
+  r.b = b_;
+  r.flops = flops_;
+  r.bytes = bytes_;
+  pending.push_back(r);
 }
 
 int read(Stat* out, int max_out) {
@@ -118,4 +120,20 @@ int read(Stat* out, int max_out) {
 }
 
 }  // namespace prof
+
+bool opt_in_smem(const void* kernel, int bytes) {
+  static std::mutex m;
+  static std::map<std::pair<const void*, int>, bool> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> g(m);
+  auto key = std::make_pair(kernel, dev);
+  auto it = done.find(key);
+  if (it != done.end()) return it->second;
+  const bool ok =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+  done[key] = ok;
+  return ok;
+}
+
 }  // namespace hps

@@ -14,15 +14,21 @@ void set_enabled(bool on);
 void reset();
 int64_t launches();
 
-// Bracket one launch: construct before the launch, destroy after it.
+// Bracket one launch: construct before the launch, destroy after it.  Each
+// scope owns its pair of events, so scopes on different threads and streams do
+// not interfere.
 class Scope {
  public:
   Scope(const char* name, cudaStream_t st, double flops, double bytes);
   ~Scope();
+  Scope(const Scope&) = delete;
+  Scope& operator=(const Scope&) = delete;
 
  private:
-  int slot_ = -1;
+  const char* name_;
   cudaStream_t st_;
+  double flops_, bytes_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
 
 struct Stat {
@@ -36,4 +42,10 @@ struct Stat {
 int read(Stat* out, int max_out);
 
 }  // namespace prof
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per (kernel,
+// device), thread-safe; false if the device refused (the launch then fails and
+// the caller's launch check reports it).
+bool opt_in_smem(const void* kernel, int bytes);
+
 }  // namespace hps

@@ -31,7 +31,13 @@ EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes", "hps_solve",
            "hps_solve_ex", "hps_query", "hps_free", "hps_status_string", "hps_kernel_launches",
            "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error",
-           "hps_solve_static", "hps_build_batch", "hps_solve_batch", "hps_batch_size")
+           "hps_solve_static", "hps_build_batch", "hps_solve_batch", "hps_batch_size",
+           "hps_estimate_bytes", "hps_release_workspace",
+           # include/hps_serve.h
+           "hps_server_default_options", "hps_server_create", "hps_server_destroy",
+           "hps_server_submit_build", "hps_server_submit_solve", "hps_server_wait",
+           "hps_server_result", "hps_server_release", "hps_server_release_operator",
+           "hps_server_get_stats")
 
 
 class HpsError(RuntimeError):
@@ -69,6 +75,24 @@ class KernelStat(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
                 ("last_update", ctypes.c_double), ("bad_box", ctypes.c_int)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("workers", ctypes.c_int),
+                ("max_rhs_per_solve", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("kind", ctypes.c_int), ("op", ctypes.c_int64),
+                ("nrhs", ctypes.c_int), ("batch_rhs", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "submitted", "completed", "failed", "builds", "solves", "solve_calls", "rhs_solved",
+        "resident_ops", "evicted_ops", "bytes_in_use", "peak_bytes_in_use", "budget")]
 
 
 def lib():
@@ -118,6 +142,27 @@ def lib():
     L.hps_last_error.restype = ctypes.c_char_p
     L.hps_status_string.argtypes = [ctypes.c_int]
     L.hps_status_string.restype = ctypes.c_char_p
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.hps_estimate_bytes.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Options),
+                                     ctypes.c_int, i64p, i64p, i64p]
+    L.hps_release_workspace.argtypes = [vp]
+    L.hps_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
+    L.hps_server_default_options.restype = None
+    L.hps_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
+    L.hps_server_destroy.argtypes = [vp]
+    L.hps_server_submit_build.argtypes = [vp, ctypes.POINTER(Problem), ctypes.POINTER(Options)]
+    L.hps_server_submit_build.restype = ctypes.c_int64
+    L.hps_server_submit_solve.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_int]
+    L.hps_server_submit_solve.restype = ctypes.c_int64
+    L.hps_server_wait.argtypes = [vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(RequestInfo)]
+    L.hps_server_result.argtypes = [vp, ctypes.c_int64, vp]
+    L.hps_server_release.argtypes = [vp, ctypes.c_int64]
+    L.hps_server_release_operator.argtypes = [vp, ctypes.c_int64]
+    L.hps_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    for name in ("hps_estimate_bytes", "hps_release_workspace", "hps_server_create",
+                 "hps_server_destroy", "hps_server_wait", "hps_server_result", "hps_server_release",
+                 "hps_server_release_operator", "hps_server_get_stats"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("hps_cheb_nodes", "hps_boundary_nodes_grid", "hps_build", "hps_boundary_nodes",
                  "hps_solve", "hps_solve_ex", "hps_query", "hps_free"):
         getattr(L, name).restype = ctypes.c_int
@@ -352,3 +397,94 @@ def hps_profile_read(max_out=64):
     return {arr[i].name.decode(): {"launches": arr[i].launches, "ms": arr[i].ms,
                                    "flops": arr[i].flops, "bytes": arr[i].bytes}
             for i in range(min(n, max_out))}
+
+
+def _problem_struct(pr):
+    P = Problem()
+    P.d = _domain(pr["domain"])
+    P.nx, P.ny, P.p, P.q = pr["nx"], pr["ny"], pr["p"], pr["q"]
+    for k in COEFF_NAMES:
+        setattr(P, k, _ptr(pr.get("coeffs", {}).get(k)))
+    return P
+
+
+def hps_estimate_bytes(problems, nrhs=1, precision=HPS_FP64, **kw):
+    """(build_peak, resident, solve_workspace) in bytes for a list of problem dicts."""
+    opt = _options(precision, False, None, kw.get("refine_tol"), kw.get("max_refine"),
+                   kw.get("fp64_top_levels"), kw.get("form_root_dtn", False), kw.get("refine_depth"))
+    arr = (Problem * len(problems))(*[_problem_struct(pr) for pr in problems])
+    out = [ctypes.c_int64() for _ in range(3)]
+    st = lib().hps_estimate_bytes(arr, len(problems), ctypes.byref(opt), nrhs,
+                                  *[ctypes.byref(x) for x in out])
+    if st != HPS_OK:
+        raise HpsError(st, "hps_estimate_bytes")
+    return tuple(x.value for x in out)
+
+
+class Server:
+    """The request loop of include/hps_serve.h."""
+
+    def __init__(self, hbm_budget=0, workers=4, max_rhs_per_solve=256, device=0):
+        o = ServerOptions()
+        lib().hps_server_default_options(ctypes.byref(o))
+        o.hbm_budget, o.workers, o.max_rhs_per_solve, o.device = (hbm_budget, workers,
+                                                                  max_rhs_per_solve, device)
+        out = ctypes.c_void_p()
+        st = lib().hps_server_create(ctypes.byref(o), ctypes.byref(out))
+        if st != HPS_OK:
+            raise HpsError(st, "hps_server_create")
+        self.ptr = out.value
+        self.shapes = {}  # operator id -> (nl, p, nbnd)
+
+    def submit_build(self, pr, precision=HPS_FP64, **kw):
+        """pr: dict with domain, nx, ny, p, q and host coefficient arrays in 'coeffs'."""
+        opt = _options(precision, False, None, kw.get("refine_tol"), kw.get("max_refine"),
+                       kw.get("fp64_top_levels"), False, kw.get("refine_depth"))
+        P = _problem_struct(pr)
+        rid = lib().hps_server_submit_build(self.ptr, ctypes.byref(P), ctypes.byref(opt))
+        if rid < 0:
+            raise HpsError(int(rid), "hps_server_submit_build")
+        self.shapes[rid] = (pr["nx"] * pr["ny"], pr["p"], hps_boundary_count(pr["nx"], pr["ny"], pr["q"]))
+        return rid
+
+    def submit_solve(self, op, f):
+        f = np.ascontiguousarray(np.atleast_2d(f), dtype=np.float64)
+        rid = lib().hps_server_submit_solve(self.ptr, op, f.ctypes.data, f.shape[0])
+        if rid < 0:
+            raise HpsError(int(rid), "hps_server_submit_solve")
+        return rid
+
+    def wait(self, rid, timeout=-1.0):
+        info = RequestInfo()
+        lib().hps_server_wait(self.ptr, rid, timeout, ctypes.byref(info))
+        return info
+
+    def result(self, rid, op, nrhs):
+        nl, p, _ = self.shapes[op]
+        u = np.empty((nrhs, nl, p, p))
+        st = lib().hps_server_result(self.ptr, rid, u.ctypes.data)
+        if st != HPS_OK:
+            raise HpsError(st, "hps_server_result")
+        return u
+
+    def release(self, rid):
+        return lib().hps_server_release(self.ptr, rid)
+
+    def release_operator(self, op):
+        return lib().hps_server_release_operator(self.ptr, op)
+
+    def stats(self):
+        s = ServerStats()
+        lib().hps_server_get_stats(self.ptr, ctypes.byref(s))
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.ptr:
+            lib().hps_server_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

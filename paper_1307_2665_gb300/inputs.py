@@ -201,3 +201,17 @@ def sample_on_leaf_grid(fn, xs, ys, nx, ny, p):
         res[k] = np.ascontiguousarray(g.reshape(ny, p, nx, p).transpose(0, 2, 1, 3)
                                       .reshape(ny * nx, p, p))
     return res
+
+
+def fourier_boundary_bank(seed, x, y, domain, nrhs, nmodes=20):
+    """nrhs data sets of the form of fourier_boundary (a_k, b_k ~ N(0,1), drawn
+    row by row from one PCG64(seed) stream), evaluated as one matrix product:
+    returns (nrhs, len(x))."""
+    x0, x1, y0, y1 = domain
+    per = 2 * ((x1 - x0) + (y1 - y0))
+    s = boundary_arclength(x, y, domain)
+    k = np.arange(1, nmodes + 1)[:, None]
+    basis = np.concatenate([np.cos(2 * np.pi * k * s / per), np.sin(2 * np.pi * k * s / per)])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ab = rng.standard_normal((nrhs, 2 * nmodes))
+    return np.ascontiguousarray(ab @ basis)

@@ -1,5 +1,5 @@
-"""The C-ABI library: it builds, loads, exports every symbol include/hps.h
-declares, and its host-only entry points (node coordinates, options, status
+"""The C-ABI library: it builds, loads, exports every symbol the headers in
+include/ declare, and its host-only entry points (node coordinates, options, status
 text, argument validation) behave as documented.  No GPU needed."""
 import ctypes
 import re
@@ -21,9 +21,11 @@ def _built():
 
 
 def _declared():
-    txt = (ROOT / "include" / "hps.h").read_text()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(hps_[a-z_]+)\s*\(", txt)))
+    names = set()
+    for hdr in sorted((ROOT / "include").glob("*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
+        names |= set(re.findall(r"\b(hps_[a-z_]+)\s*\(", txt))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported():
@@ -80,3 +82,29 @@ def test_null_pointer_arguments():
     assert L.hps_free(None) == hps.HPS_OK
     assert L.hps_solve(None, None, 1, None, None) == hps.HPS_EINVAL
     assert L.hps_cheb_nodes(hps.Domain(0, 1, 0, 1), 2, 2, 8, None) == hps.HPS_EINVAL
+
+
+def test_estimate_bytes_host_only():
+    """hps_estimate_bytes works from the plan alone: the build peak covers the
+    resident operator, the resident FP64 operator holds at least Y and S, and
+    the solve workspace grows linearly with the number of right-hand sides."""
+    pr = dict(domain=(0, 1, 0, 1), nx=16, ny=16, p=16, q=14, coeffs={})
+    peak, res, w1 = hps.hps_estimate_bytes([pr], nrhs=1)
+    _, _, w2 = hps.hps_estimate_bytes([pr], nrhs=2)
+    _, _, w3 = hps.hps_estimate_bytes([pr], nrhs=3)
+    y = 256 * 196 * 56 * 8
+    assert res > y and peak >= res and w1 > 0
+    assert w3 - w2 == w2 - w1
+    peak_m, res_m, wm = hps.hps_estimate_bytes([pr], nrhs=1, precision=hps.HPS_MIXED)
+    assert wm > w1  # refinement vectors
+    with pytest.raises(hps.HpsError):
+        hps.hps_estimate_bytes([dict(pr, q=17)])
+
+
+def test_server_without_device_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(hps.HpsError) as e:
+        hps.Server()
+    assert e.value.status == hps.HPS_EDEVICE
