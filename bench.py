@@ -236,6 +236,11 @@ def alu_peak_tflops(name, sm_mhz):
     return N_SM * per * 2 * sm_mhz * 1e6 / 1e12, per
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
+# ncu capture of this kernel's launch in the mixed step of the 64x64 workload.
+TRAFFIC_PER_LAUNCH = {"gemm_schur<f64>": 154276096 + 59662336}
+
+
 def roofline_of(stats, t_total_ms, sm_mhz):
     name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
     peak, per = alu_peak_tflops(name, sm_mhz)
@@ -243,7 +248,7 @@ def roofline_of(stats, t_total_ms, sm_mhz):
     per_launch_s = st["ms"] / 1e3 / max(st["launches"], 1)
     achieved = per_launch_flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
             "peak_source": f"{'FP64 DFMA' if per == FP64_DFMA_PER_SM_CLK else 'FP32 FFMA'}: "
                            f"{N_SM} SMs x {per}/clk x 2 flop x {sm_mhz:.0f} MHz (max SM clock; "
                            f"per-clock rate measured by an FMA probe on this pool)",

@@ -805,6 +805,7 @@ struct CallPtrs {           // per solve call: where f comes from and u goes
   // and the columns (problem, right-hand side) of the accelerated update
   double* const* fptr = nullptr;
   AaCol* cols = nullptr;
+  int* col_of = nullptr;  // per reduction chunk: its column
   int ncol = 0;
   int64_t nchunks = 0, nu = 0;
 };
@@ -964,7 +965,7 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
     leaf_out(H, cp.fptr, cp.wrs, nrhs, true);  // F_j, the correction at w_j
     const int nslots = m > 0 ? std::min(j, m) : 0;
     const int slot_new = (m > 0 && j >= 1) ? (j - 1) % m : -1;
-    aa_reduce(cp.cols, ncol, cp.nchunks, rb->F.as<double>(), rb->Fprev.as<double>(),
+    aa_reduce(cp.cols, cp.col_of, ncol, cp.nchunks, rb->F.as<double>(), rb->Fprev.as<double>(),
               rb->dWlast.as<double>(), rb->dF.as<float>(), rb->G.as<double>(), cp.nu,
               m > 0 ? j : 0, slot_new, nslots, rb->part.as<double>(), rb->colsum.as<double>(), st);
     ck(cudaGetLastError());
@@ -1019,7 +1020,7 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
     }
     ck(cudaMemcpyAsync(rb->coef.p, h_coef, (size_t)ncol * stride * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    aa_update(cp.cols, ncol, cp.nchunks, rb->F.as<double>(), rb->dWlast.as<double>(),
+    aa_update(cp.cols, cp.col_of, ncol, cp.nchunks, rb->F.as<double>(), rb->dWlast.as<double>(),
               rb->G.as<double>(), cp.nu, nslots, rb->coef.as<double>(), st);
     ck(cudaGetLastError());
   }
@@ -1042,6 +1043,14 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
   return HPS_OK;
 }
 
+// Reduction chunks of one solve's refinement columns.
+int64_t n_chunks_upper(const hps_handle_s& H, int nrhs) {
+  int64_t n = 0;
+  for (const auto& pi : H.plan.probs)
+    n += (int64_t)nrhs * (((int64_t)pi.nl * pi.s.p * pi.s.p + kAaChunk - 1) / kAaChunk);
+  return n;
+}
+
 // Upload the per-call root descriptors (with f, then with zeros), the per-leaf
 // output pointers and, in mixed mode, the refinement layout.  f[k] / u[k] are
 // device pointers.
@@ -1052,12 +1061,14 @@ CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, i
   const bool refine = H.mixed && H.opt.max_refine > 0;
   const int ncol = H.nprob * nrhs;
   H.call_st.begin(stage_bytes<RootDesc>(2 * H.nprob) + 2 * stage_bytes<double*>(nl) +
-                      stage_bytes<int64_t>(nl) + (refine ? stage_bytes<AaCol>(ncol) : 0) + 1024,
+                      stage_bytes<int64_t>(nl) + (refine ? stage_bytes<AaCol>(ncol) : 0) + 1024 +
+                      (refine ? stage_bytes<int>(n_chunks_upper(H, nrhs)) : 0),
                   H.stream);
   std::vector<RootDesc> rd(2 * H.nprob);
   std::vector<double*> wp(nl), fp;
   std::vector<int64_t> wr(nl);
   std::vector<AaCol> cols;
+  std::vector<int> col_of;
   CallPtrs cp;
   int64_t nu = 0;  // refinement vector length: every column of every problem
   for (int k = 0; k < H.nprob; ++k) nu += (int64_t)nrhs * pl.probs[k].nl * pl.probs[k].s.p * pl.probs[k].s.p;
@@ -1099,6 +1110,7 @@ CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, i
         c.len = len;
         c.ch0 = ch;
         ch += (len + kAaChunk - 1) / kAaChunk;
+        col_of.resize(ch, (int)cols.size());
         cols.push_back(c);
       }
     fo += (int64_t)nrhs * len;
@@ -1109,6 +1121,7 @@ CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, i
   if (refine) {
     cp.fptr = H.call_st.push(fp, H.stream);
     cp.cols = H.call_st.push(cols, H.stream);
+    cp.col_of = H.call_st.push(col_of, H.stream);
     cp.ncol = ncol;
     cp.nchunks = ch;
     cp.nu = nu;

@@ -86,7 +86,7 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrh
 // split of a product depends only on its own K, so its result does not depend
 // on what else the launch holds.  Needs nd * ceil(max_K / kSplitK) * max_M *
 // max_N elements (split_ws_elems); with less, the launch does not split.
-constexpr int kSplitK = 512;
+constexpr int kSplitK = 128;
 inline size_t split_ws_elems(int nd, int max_M, int max_N, int max_K) {
   return max_K > kSplitK ? (size_t)nd * ((max_K + kSplitK - 1) / kSplitK) * max_M * max_N : 0;
 }
@@ -164,12 +164,15 @@ struct AaCol {
 // Forms dF_new = F - Fprev and G_new = dWlast + dF_new in ring slot slot_new
 // (j >= 1), sets Fprev = F, and reduces per column: colsum[c*kAaQ + q] with
 // q = 0 max|F|, 1 max|w|, 2 + s <dF_s, F>, 2 + kAaMaxDepth + s <dF_s, dF_new>.
-void aa_reduce(const AaCol* cols, int ncol, int64_t nchunks, const double* F, double* Fprev,
+// col_of[b]: the column of chunk b.
+void aa_reduce(const AaCol* cols, const int* col_of, int ncol, int64_t nchunks, const double* F,
+               double* Fprev,
                const double* dWlast, float* dF, double* G, int64_t nu, int j, int slot_new,
                int nslots, double* part, double* colsum, cudaStream_t st);
 // w += F - sum_s gamma_s G_s (mode 1, also dWlast = that update), w += F
 // (mode 2) or nothing (mode 0), per column from coef[c*(kAaMaxDepth+1) ...].
-void aa_update(const AaCol* cols, int ncol, int64_t nchunks, const double* F, double* dWlast,
+void aa_update(const AaCol* cols, const int* col_of, int ncol, int64_t nchunks, const double* F,
+               double* dWlast,
                const double* G, int64_t nu, int nslots, const double* coef, cudaStream_t st);
 
 }  // namespace hps

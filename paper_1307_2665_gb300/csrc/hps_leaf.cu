@@ -19,6 +19,7 @@
 //   leaf_post     : w_full = W u_e for the solve (Section 4.3).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "hps_kernels.cuh"
@@ -361,7 +362,7 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
 //   A w = -c11 Dxx w - 2 c12 Dy (Dx w) - c22 Dyy w + c1 Dx w + c2 Dy w + c w.
 // Output rbuf[l*ni*nrhs + i + r*ni] in the element type of the correction solve.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int p,
+__global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int p, int rb,
                                                        const double2* __restrict__ hsc,
                                                        const double* __restrict__ gD,
                                                        double* const* __restrict__ wptr,
@@ -371,17 +372,13 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   const int pp = p * p, pi = p - 2, ni = pi * pi;
   double* D = sm;
   double* D2 = D + pp;
-  double* cf = D2 + pp;     // 6 x pp
-  double* W = cf + 6 * pp;  // pp
-  double* Wx = W + pp;      // pp: Dx w
+  double* W = D2 + pp;       // rb x pp: w of this block of right-hand sides
+  double* Wx = W + rb * pp;  // rb x pp: Dx w (only with the mixed term)
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
   const double* wl = wptr[l];
   const int64_t wstride = wrs[l];
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
-  for (int k = 0; k < 6; ++k)
-    for (int e = threadIdx.x; e < pp; e += blockDim.x)
-      cf[k * pp + e] = cp.c[k] ? cp.c[k][(size_t)jl * pp + e] : 0.0;
   __syncthreads();
   for (int e = threadIdx.x; e < pp; e += blockDim.x) {
     int i = e / p, jj = e % p;
@@ -392,48 +389,64 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   R* rl = rbuf + (size_t)jl * ni * nrhs;
   const bool has12 = cp.c[1] != nullptr, has1 = cp.c[3] != nullptr, has2 = cp.c[4] != nullptr,
              has0 = cp.c[5] != nullptr;
-  for (int r = 0; r < nrhs; ++r) {
+  const double* c11 = cp.c[0] ? cp.c[0] + (size_t)jl * pp : nullptr;
+  const double* c12 = has12 ? cp.c[1] + (size_t)jl * pp : nullptr;
+  const double* c22 = cp.c[2] ? cp.c[2] + (size_t)jl * pp : nullptr;
+  const double* c1 = has1 ? cp.c[3] + (size_t)jl * pp : nullptr;
+  const double* c2 = has2 ? cp.c[4] + (size_t)jl * pp : nullptr;
+  const double* c0 = has0 ? cp.c[5] + (size_t)jl * pp : nullptr;
+  // right-hand sides in blocks of rb; threads take (node, right-hand side) pairs
+  for (int r0 = 0; r0 < nrhs; r0 += rb) {
+    const int nb = min(rb, nrhs - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < pp; e += blockDim.x) W[e] = wl[(size_t)r * wstride + e];
+    for (int e = threadIdx.x; e < pp * nb; e += blockDim.x)
+      W[e] = wl[(size_t)(r0 + e / pp) * wstride + e % pp];
     __syncthreads();
     if (has12) {  // Dx w at every node: the mixed term differentiates it along y
-      for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-        int a = e / p, b = e % p;
+      for (int e = threadIdx.x; e < pp * nb; e += blockDim.x) {
+        const int node = e % pp, a = node / p, b = node % p;
+        const double* Wr = W + (e / pp) * pp;
         double s = 0.0;
-        for (int d = 0; d < p; ++d) s = fma(D[b * p + d], W[a * p + d], s);
+        for (int d = 0; d < p; ++d) s = fma(D[b * p + d], Wr[a * p + d], s);
         Wx[e] = sx * s;
       }
       __syncthreads();
     }
-    for (int ri = threadIdx.x; ri < ni; ri += blockDim.x) {
+    for (int e = threadIdx.x; e < ni * nb; e += blockDim.x) {
+      const int ri = e % ni, rr = e / ni;
       const int a = ri / pi + 1, b = ri % pi + 1, node = a * p + b;
+      const double* Wr = W + rr * pp;
       double dxx = 0.0, dyy = 0.0, dx = 0.0, dy = 0.0, dxy = 0.0;
       for (int k = 0; k < p; ++k) {
-        dxx = fma(D2[b * p + k], W[a * p + k], dxx);
-        dyy = fma(D2[a * p + k], W[k * p + b], dyy);
+        dxx = fma(D2[b * p + k], Wr[a * p + k], dxx);
+        dyy = fma(D2[a * p + k], Wr[k * p + b], dyy);
       }
       if (has1) {
         if (has12) {
-          dx = Wx[node];
+          dx = Wx[rr * pp + node];
         } else {
-          for (int k = 0; k < p; ++k) dx = fma(D[b * p + k], W[a * p + k], dx);
+          for (int k = 0; k < p; ++k) dx = fma(D[b * p + k], Wr[a * p + k], dx);
           dx *= sx;
         }
       }
       if (has2)
-        for (int k = 0; k < p; ++k) dy = fma(D[a * p + k], W[k * p + b], dy);
-      if (has12)
-        for (int k = 0; k < p; ++k) dxy = fma(D[a * p + k], Wx[k * p + b], dxy);
+        for (int k = 0; k < p; ++k) dy = fma(D[a * p + k], Wr[k * p + b], dy);
+      if (has12) {
+        const double* Wxr = Wx + rr * pp;
+        for (int k = 0; k < p; ++k) dxy = fma(D[a * p + k], Wxr[k * p + b], dxy);
+      }
       dxx *= sx * sx;
       dyy *= sy * sy;
       dy *= sy;
       dxy *= sy;
-      double Aw = -cf[node] * dxx - cf[2 * pp + node] * dyy;
-      if (has12) Aw -= 2.0 * cf[pp + node] * dxy;
-      if (has1) Aw += cf[3 * pp + node] * dx;
-      if (has2) Aw += cf[4 * pp + node] * dy;
-      if (has0) Aw += cf[5 * pp + node] * W[node];
-      rl[ri + (size_t)r * ni] = (R)(-Aw);
+      double Aw = 0.0;
+      if (c11) Aw -= c11[node] * dxx;
+      if (c22) Aw -= c22[node] * dyy;
+      if (has12) Aw -= 2.0 * c12[node] * dxy;
+      if (has1) Aw += c1[node] * dx;
+      if (has2) Aw += c2[node] * dy;
+      if (has0) Aw += c0[node] * Wr[node];
+      rl[ri + (size_t)(r0 + rr) * ni] = (R)(-Aw);
     }
   }
 }
@@ -445,19 +458,23 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
   if (nl <= 0 || nrhs <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
-  size_t smem = (size_t)(10 * p * p) * sizeof(double);
+  // right-hand sides per block: up to 4, as many as fit next to D and D^2
+  const int pp = p * p;
+  const int cap = (int)((200 * 1024 / 8 - 2 * pp) / (2 * pp));
+  const int rb = std::max(1, std::min(4, cap));
+  const size_t smem = (size_t)(2 * pp + 2 * rb * pp) * sizeof(double);
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_residual<R>), 200 * 1024))
     return;  // reported by the caller's launch check
-  const double pp = (double)p * p, ni = (double)(p - 2) * (p - 2);
+  const double ppd = (double)pp, ni = (double)(p - 2) * (p - 2);
   // FP64 flops actually issued: Dxx, Dyy at the interior nodes, plus the terms
   // of the coefficients present (Dx w everywhere only for the mixed term)
   double per = 4.0 * ni * p;
-  if (coef[1]) per += 2.0 * pp * p + 2.0 * ni * p;
+  if (coef[1]) per += 2.0 * ppd * p + 2.0 * ni * p;
   else if (coef[3]) per += 2.0 * ni * p;
   if (coef[4]) per += 2.0 * ni * p;
   prof::Scope sc("leaf_residual<f64>", st, (double)nl * nrhs * per,
-                 (double)nl * (nrhs * (pp * 8.0 + ni * sizeof(R)) + 6.0 * pp * 8.0));
-  k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, l0, p, hsc, d_D, wptr, wrs, nrhs, rbuf);
+                 (double)nl * (nrhs * (ppd * 8.0 + ni * sizeof(R)) + 6.0 * ppd * 8.0));
+  k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs, nrhs, rbuf);
 }
 
 // ------------------------------------------------- flux offsets of the leaves
@@ -468,7 +485,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ wptr,
                                                    const int64_t* __restrict__ wrs,
                                                    const R* __restrict__ z, int l0, int p, int q,
-                                                   int nrhs, const double2* __restrict__ hsc,
+                                                   int nrhs, int rb,
+                                                   const double2* __restrict__ hsc,
                                                    const double* __restrict__ gD,
                                                    const double* __restrict__ gPc2g,
                                                    const int64_t* __restrict__ leaf_off,
@@ -476,9 +494,9 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
   double* D = sm;
-  double* Pc = D + pp;   // q x p
-  double* V = Pc + q * p;
-  double* F = V + pp;    // 4p
+  double* Pc = D + pp;     // q x p
+  double* V = Pc + q * p;  // rb x pp
+  double* F = V + rb * pp; // rb x 4p
   const int l = blockIdx.x;  // group-local leaf
   const double sx = hsc[l0 + l].x, sy = hsc[l0 + l].y;
   const double* wl = wptr[l0 + l];
@@ -487,36 +505,40 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
   for (int e = threadIdx.x; e < q * p; e += blockDim.x) Pc[e] = gPc2g[e];
   const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
   const int64_t off = leaf_off[l0 + l];
-  for (int r = 0; r < nrhs; ++r) {
+  // right-hand sides in blocks of rb, so every phase keeps the CTA busy
+  for (int r0 = 0; r0 < nrhs; r0 += rb) {
+    const int nb = min(rb, nrhs - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-      const int a = e / p, b = e % p;
-      double v = wl[(size_t)r * wstride + e];
+    for (int e = threadIdx.x; e < pp * nb; e += blockDim.x) {
+      const int r = r0 + e / pp, node = e % pp, a = node / p, b = node % p;
+      double v = wl[(size_t)r * wstride + node];
       if (zl && a > 0 && a < p - 1 && b > 0 && b < p - 1)
         v += (double)zl[(a - 1) * pi + (b - 1) + (size_t)r * ni];
       V[e] = v;
     }
     __syncthreads();
-    for (int sj = threadIdx.x; sj < 4 * p; sj += blockDim.x) {
-      const int s = sj / p, j = sj % p;
+    for (int e = threadIdx.x; e < 4 * p * nb; e += blockDim.x) {
+      const int sj = e % (4 * p), s = sj / p, j = sj % p;
+      const double* Vr = V + (e / (4 * p)) * pp;
       double acc = 0.0;
       if (s == 0 || s == 2) {
         const int row = (s == 0) ? 0 : p - 1;
-        for (int a = 0; a < p; ++a) acc = fma(D[row * p + a], V[a * p + j], acc);
+        for (int a = 0; a < p; ++a) acc = fma(D[row * p + a], Vr[a * p + j], acc);
         acc *= sy;
       } else {
         const int col = (s == 1) ? p - 1 : 0;
-        for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], V[j * p + b], acc);
+        for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], Vr[j * p + b], acc);
         acc *= sx;
       }
-      F[sj] = acc;
+      F[e] = acc;
     }
     __syncthreads();
-    for (int g = threadIdx.x; g < nq; g += blockDim.x) {
-      const int s = g / q, k = g % q;
+    for (int e = threadIdx.x; e < nq * nb; e += blockDim.x) {
+      const int g = e % nq, rr = e / nq, s = g / q, k = g % q;
+      const double* Fr = F + rr * 4 * p;
       double acc = 0.0;
-      for (int j = 0; j < p; ++j) acc = fma(Pc[k * p + j], F[s * p + j], acc);
-      hp[(size_t)r * ext_total + off + g] = acc;
+      for (int j = 0; j < p; ++j) acc = fma(Pc[k * p + j], Fr[s * p + j], acc);
+      hp[(size_t)(r0 + rr) * ext_total + off + g] = acc;
     }
   }
 }
@@ -526,12 +548,17 @@ void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int 
                int nrhs, const double2* hsc, const double* d_D, const double* d_Pc2g,
                const int64_t* leaf_off, int64_t ext_total, double* hp, cudaStream_t st) {
   if (nl <= 0 || nrhs <= 0) return;
-  size_t smem = (size_t)(2 * p * p + q * p + 4 * p) * sizeof(double);
+  const int pp = p * p;
+  const int cap = (int)((200 * 1024 / 8 - pp - q * p) / (pp + 4 * p));
+  const int rb = std::max(1, std::min(8, cap));
+  const size_t smem = (size_t)(pp + q * p + rb * (pp + 4 * p)) * sizeof(double);
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_flux<R>), 200 * 1024))
+    return;  // reported by the caller's launch check
   prof::Scope sc("leaf_flux<f64>", st, (double)nl * nrhs * (8.0 * p * p + 8.0 * q * p),
                  (double)nl * nrhs * ((double)p * p * 8.0 + (p - 2.0) * (p - 2.0) * sizeof(R) +
                                       4.0 * q * 8.0));
-  k_leaf_flux<R><<<nl, 256, smem, st>>>(wptr, wrs, z, l0, p, q, nrhs, hsc, d_D, d_Pc2g, leaf_off,
-                                        ext_total, hp);
+  k_leaf_flux<R><<<nl, 256, smem, st>>>(wptr, wrs, z, l0, p, q, nrhs, rb, hsc, d_D, d_Pc2g,
+                                        leaf_off, ext_total, hp);
 }
 
 #define HPS_INST_LEAF(R)                                                                        \

@@ -48,74 +48,153 @@ struct TName<float> {
 // C[m0:m0+BM, n0:n0+BN] = beta C + alpha A[m0:, 0:K] B[0:K, n0:], computed in R.
 // A, B and C may have other element types (converted on load and store).
 // Threads: (BM/TM) x (BN/TN); thread t covers TM consecutive rows and TN
-// consecutive columns, with the column-tile index varying fastest so that one
-// warp owns a contiguous band of rows and a ragged tail of rows idles whole warps.
+// consecutive columns, the column-tile index varying fastest, so one warp owns
+// a contiguous band of rows and a ragged tail of rows idles whole warps (no
+// FMAs on padding rows: the FP64 kernels are DFMA-bound).  The epilogue moves
+// each thread's TM rows of a column as 16-byte vectors when aligned, so the
+// adjacent row groups of a warp fill whole 32-byte sectors.
+// Pipelining: the K tiles are double-buffered in shared memory; the global
+// loads of tile k+1 are issued into registers before the FMAs of tile k and
+// stored after them, so one __syncthreads per K tile and the load latency
+// overlaps the arithmetic.  Every element's FMA chain runs over k in order,
+// whatever the tile shape or the launch.
 template <typename R, int BM_, int BN_, int BK_, int TM_, int TN_>
 struct Tile {
   static constexpr int BM = BM_, BN = BN_, BK = BK_, TM = TM_, TN = TN_;
   static constexpr int NTN = BN / TN;
   static constexpr int NTM = BM / TM;
   static constexpr int NT = NTN * NTM;
-  static constexpr int SMEM = (BK * BM + BK * BN) * (int)sizeof(R);
+  static constexpr int LA = BM * BK / NT;  // A elements per thread and K tile
+  static constexpr int LB = BK * BN / NT;  // B elements per thread and K tile
+  static constexpr int BNP = BN + 1;  // padded row of the B stage: the transposed
+                                      // store of a column hits distinct banks
+  static constexpr int STAGE = BK * BM + BK * BNP;
+  static constexpr int SMEM = 2 * STAGE * (int)sizeof(R);
+  static_assert(BM * BK % NT == 0 && BK * BN % NT == 0, "tile loads must divide evenly");
 
-  // B and C may alias when one CTA owns all M rows of its columns (M <= BM).
+  template <typename TC>
+  __device__ static void store4(TC* cp, const R* v, R alpha, R beta) {
+    // TM = 4 consecutive rows of one column
+    if (sizeof(TC) == 8) {
+      double2* q = reinterpret_cast<double2*>(cp);
+      double2 lo = make_double2(0.0, 0.0), hi = lo;
+      if (beta != R(0)) {
+        lo = q[0];
+        hi = q[1];
+        lo.x = fma((double)alpha, (double)v[0], (double)beta * lo.x);
+        lo.y = fma((double)alpha, (double)v[1], (double)beta * lo.y);
+        hi.x = fma((double)alpha, (double)v[2], (double)beta * hi.x);
+        hi.y = fma((double)alpha, (double)v[3], (double)beta * hi.y);
+      } else {
+        lo = make_double2((double)(alpha * v[0]), (double)(alpha * v[1]));
+        hi = make_double2((double)(alpha * v[2]), (double)(alpha * v[3]));
+      }
+      q[0] = lo;
+      q[1] = hi;
+    } else {
+      float4* q = reinterpret_cast<float4*>(cp);
+      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (beta != R(0)) {
+        c = *q;
+        c.x = fmaf((float)alpha, (float)v[0], (float)beta * c.x);
+        c.y = fmaf((float)alpha, (float)v[1], (float)beta * c.y);
+        c.z = fmaf((float)alpha, (float)v[2], (float)beta * c.z);
+        c.w = fmaf((float)alpha, (float)v[3], (float)beta * c.w);
+      } else {
+        c = make_float4((float)(alpha * v[0]), (float)(alpha * v[1]), (float)(alpha * v[2]),
+                        (float)(alpha * v[3]));
+      }
+      *q = c;
+    }
+  }
+
   template <typename TA, typename TB, typename TC>
   __device__ static void run(int M, int N, int K, R alpha, const TA* __restrict__ A, int lda,
                              const TB* B, int ldb, R beta, TC* C, int ldc, int m0, int n0, R* sm) {
-    R* As = sm;            // [BK][BM]
-    R* Bs = sm + BK * BM;  // [BK][BN]
     const int t = threadIdx.x;
     const int tn = t % NTN, tm = t / NTN;
     const int r0 = tm * TM, c0 = tn * TN;
     // first row of this warp's band; the band is idle when it starts past M
-    const int warp_row0 = (((t / 32) * 32) / NTN) * TM;
-    const bool warp_live = (m0 + warp_row0) < M;
+    const bool warp_live = (m0 + (((t / 32) * 32) / NTN) * TM) < M;
     R acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = R(0);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-      for (int e = t; e < BM * BK; e += NT) {
-        int i = e % BM, k = e / BM;
-        int gi = m0 + i, gk = k0 + k;
-        As[k * BM + i] = (gi < M && gk < K) ? (R)A[gi + (size_t)gk * lda] : R(0);
+    R ra[LA], rb[LB];
+    auto gload = [&](int k0) {
+#pragma unroll
+      for (int l = 0; l < LA; ++l) {
+        const int e = t + l * NT, i = e % BM, k = e / BM;
+        const int gi = m0 + i, gk = k0 + k;
+        ra[l] = (gi < M && gk < K) ? (R)A[gi + (size_t)gk * lda] : R(0);
       }
-      for (int e = t; e < BK * BN; e += NT) {
-        int k = e % BK, j = e / BK;
-        int gk = k0 + k, gj = n0 + j;
-        Bs[k * BN + j] = (gk < K && gj < N) ? (R)B[gk + (size_t)gj * ldb] : R(0);
+#pragma unroll
+      for (int l = 0; l < LB; ++l) {
+        const int e = t + l * NT, k = e % BK, j = e / BK;
+        const int gk = k0 + k, gj = n0 + j;
+        rb[l] = (gk < K && gj < N) ? (R)B[gk + (size_t)gj * ldb] : R(0);
       }
-      __syncthreads();
-      if (warp_live) {
-#pragma unroll 4
-        for (int k = 0; k < BK; ++k) {
-          R a[TM], b[TN];
+    };
+    auto sstore = [&](R* st) {
 #pragma unroll
-          for (int i = 0; i < TM; ++i) a[i] = As[k * BM + r0 + i];
-#pragma unroll
-          for (int j = 0; j < TN; ++j) b[j] = Bs[k * BN + c0 + j];
-#pragma unroll
-          for (int i = 0; i < TM; ++i)
-#pragma unroll
-            for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-        }
+      for (int l = 0; l < LA; ++l) {
+        const int e = t + l * NT;
+        st[e] = ra[l];  // [k][i], i = e % BM, k = e / BM
       }
-      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < LB; ++l) {
+        const int e = t + l * NT;
+        st[BK * BM + (e % BK) * BNP + e / BK] = rb[l];
+      }
+    };
+    if (K > 0) {
+      gload(0);
+      sstore(sm);
     }
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      const bool more = k0 + BK < K;
+      if (more) gload(k0 + BK);
+      const R* As = sm + buf * STAGE;
+      const R* Bs = As + BK * BM;
+#pragma unroll 4
+      for (int k = 0; k < (warp_live ? BK : 0); ++k) {
+        R a[TM], b[TN];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      int gi = m0 + r0 + i;
-      if (gi >= M) continue;
+        for (int i = 0; i < TM; ++i) a[i] = As[k * BM + r0 + i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        int gj = n0 + c0 + j;
-        if (gj >= N) continue;
-        TC* cp = C + gi + (size_t)gj * ldc;
+        for (int j = 0; j < TN; ++j) b[j] = Bs[k * BNP + c0 + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      if (more) sstore(sm + (buf ^ 1) * STAGE);
+      __syncthreads();
+      buf ^= 1;
+    }
+    const int gi0 = m0 + r0;
+    if (gi0 >= M) return;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gj = n0 + c0 + j;
+      if (gj >= N) continue;
+      TC* cp = C + gi0 + (size_t)gj * ldc;
+      if (TM == 4 && (sizeof(TC) == 4 || sizeof(TC) == 8) && gi0 + 4 <= M &&
+          (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+        R v[4] = {acc[0][j], acc[1][j], acc[2][j], acc[3][j]};
+        store4(cp, v, alpha, beta);
+        continue;
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i) {
+        if (gi0 + i >= M) break;
         if (beta == R(0))
-          *cp = (TC)(alpha * acc[i][j]);
+          cp[i] = (TC)(alpha * acc[i][j]);
         else  // accumulate in the wider of the two types
-          *cp = (TC)fma((TC)alpha, (TC)acc[i][j], (TC)beta * *cp);
+          cp[i] = (TC)fma((TC)alpha, (TC)acc[i][j], (TC)beta * cp[i]);
       }
     }
   }

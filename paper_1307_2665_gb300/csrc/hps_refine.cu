@@ -42,18 +42,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ int find_col(const AaCol* __restrict__ cols, int ncol, int64_t chunk) {
-  int lo = 0, hi = ncol - 1;
-  while (lo < hi) {  // last column with ch0 <= chunk
-    const int mid = (lo + hi + 1) >> 1;
-    if (cols[mid].ch0 <= chunk)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 // max of two non-negative doubles (or NaN patterns with the sign bit clear,
 // which compare above every finite value and +inf) on their bit patterns
 __device__ __forceinline__ double bitmax(double a, double b) {
@@ -65,7 +53,8 @@ __device__ __forceinline__ long long absbits(double x) {
 
 // One CTA per chunk.  Partials, per chunk: [0] max|F|, [1] max|w|,
 // [2 + s] <dF_s, F>, [2 + kAaMaxDepth + s] <dF_s, dF_new> for s < nslots.
-__global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict__ cols, int ncol,
+__global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict__ cols,
+                                                        const int* __restrict__ col_of,
                                                         const double* __restrict__ F,
                                                         double* __restrict__ Fprev,
                                                         const double* __restrict__ dWlast,
@@ -74,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict_
                                                         int slot_new, int nslots,
                                                         double* __restrict__ part) {
   const int64_t b = blockIdx.x;
-  const AaCol c = cols[find_col(cols, ncol, b)];
+  const AaCol c = cols[col_of[b]];
   const int64_t e0 = (b - c.ch0) * kAaChunk;
   const int64_t e1 = min(e0 + (int64_t)kAaChunk, c.len);
   long long mf = 0, mw = 0;  // |F|, |w| maxima as bit patterns (exact, NaN-preserving)
@@ -157,13 +146,14 @@ __global__ void k_aa_colsum(const AaCol* __restrict__ cols, const double* __rest
 
 // coef[c*(kAaMaxDepth+1)]: 0 frozen, 1 accelerated update, 2 plain update
 // (w += F); then gamma_s.
-__global__ void __launch_bounds__(kThreads) k_aa_update(const AaCol* __restrict__ cols, int ncol,
+__global__ void __launch_bounds__(kThreads) k_aa_update(const AaCol* __restrict__ cols,
+                                                        const int* __restrict__ col_of,
                                                         const double* __restrict__ F,
                                                         double* __restrict__ dWlast,
                                                         const double* __restrict__ G, int64_t nu,
                                                         int nslots, const double* __restrict__ coef) {
   const int64_t b = blockIdx.x;
-  const int ci = find_col(cols, ncol, b);
+  const int ci = col_of[b];
   const AaCol c = cols[ci];
   const double* cf = coef + (int64_t)ci * (kAaMaxDepth + 1);
   const int mode = (int)cf[0];
@@ -188,7 +178,8 @@ __global__ void __launch_bounds__(kThreads) k_aa_update(const AaCol* __restrict_
 
 }  // namespace
 
-void aa_reduce(const AaCol* cols, int ncol, int64_t nchunks, const double* F, double* Fprev,
+void aa_reduce(const AaCol* cols, const int* col_of, int ncol, int64_t nchunks, const double* F,
+               double* Fprev,
                const double* dWlast, float* dF, double* G, int64_t nu, int j, int slot_new,
                int nslots, double* part, double* colsum, cudaStream_t st) {
   if (ncol <= 0 || nchunks <= 0) return;
@@ -197,17 +188,19 @@ void aa_reduce(const AaCol* cols, int ncol, int64_t nchunks, const double* F, do
   prof::Scope sc("refine_reduce", st, 4.0 * nslots * (double)nu,
                  (double)nu * (8.0 + 8.0 + 16.0 + (j >= 1 ? 8.0 + 4.0 + 8.0 : 0.0) +
                                4.0 * std::max(nslots - 1, 0)));
-  k_aa_reduce<<<(unsigned)nchunks, kThreads, 0, st>>>(cols, ncol, F, Fprev, dWlast, dF, G, nu, j,
+  k_aa_reduce<<<(unsigned)nchunks, kThreads, 0, st>>>(cols, col_of, F, Fprev, dWlast, dF, G, nu, j,
                                                      slot_new, nslots, part);
   k_aa_colsum<<<(unsigned)ncol, 32, 0, st>>>(cols, part, colsum);
 }
 
-void aa_update(const AaCol* cols, int ncol, int64_t nchunks, const double* F, double* dWlast,
+void aa_update(const AaCol* cols, const int* col_of, int ncol, int64_t nchunks, const double* F,
+               double* dWlast,
                const double* G, int64_t nu, int nslots, const double* coef, cudaStream_t st) {
   if (ncol <= 0 || nchunks <= 0) return;
   prof::Scope sc("refine_update", st, 2.0 * nslots * (double)nu,
                  (double)nu * (8.0 + 16.0 + 8.0 + 8.0 * nslots));
-  k_aa_update<<<(unsigned)nchunks, kThreads, 0, st>>>(cols, ncol, F, dWlast, G, nu, nslots, coef);
+  k_aa_update<<<(unsigned)nchunks, kThreads, 0, st>>>(cols, col_of, F, dWlast, G, nu, nslots,
+                                                     coef);
 }
 
 }  // namespace hps
