@@ -186,6 +186,18 @@ int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_
 int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* opt, int nrhs,
                        int64_t* build_peak, int64_t* resident, int64_t* solve);
 
+/* C = alpha A B + beta C for FP64 device matrices (column-major, leading
+ * dimensions lda >= M, ldb >= K, ldc >= M) through the tensor-core engine the
+ * FP64 merges use for their Schur-complement products (eq. merge): every row
+ * of A and column of B is split exactly into 8 BF16 slices of 7 bits, the 36
+ * significant slice products run as tcgen05 MMAs with exact FP32
+ * accumulation, and the integer results are combined in 64-bit fixed point;
+ * the error is of the order of an FP64 GEMM's rounding.  Synchronous on the
+ * current device.  Exposed for testing and measurement; the paper computes
+ * these products in plain double precision. */
+int hps_dgemm_tc(int M, int N, int K, double alpha, const double* A, int lda, const double* B,
+                 int ldb, double beta, double* C, int ldc);
+
 /* Release the solve workspace a handle caches between solves (exterior-value
  * pools, refinement buffers, staging); the next solve allocates it again.
  * Must not overlap a solve on the same handle. */

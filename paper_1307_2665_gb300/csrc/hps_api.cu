@@ -383,13 +383,49 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   lu_solve_batched<R>(dlu, nm, L.max_m, L.max_ne + (H.mixed ? L.max_m : 0), kLuFactor,
                       H.status.as<int>(), st, L.hm.data(), hn.data());
   ck(cudaGetLastError());
-  if (!gm.empty()) {
-    GemmDesc<R>* dg = stg.push(gm, st);
-    gemm_batched<R>(dg, (int)gm.size(), L.max_ne, L.max_ne, R(1), R(1), st,
-                    sizeof(R) == 8 ? "gemm_schur<f64>" : "gemm_schur<f32>", schur_flops,
-                    schur_bytes);
+  // FP64 products large enough go to the tensor cores (exact BF16 splitting);
+  // the choice depends on each product's own shape only
+  std::vector<GemmDesc<R>> gsimt;
+  std::vector<OzDesc> goz;
+  for (const auto& gg : gm) {
+    if (sizeof(R) == 8 && oz_eligible(gg.M, gg.N, gg.K)) {
+      OzDesc o;
+      o.A = reinterpret_cast<const double*>(gg.A);
+      o.B = reinterpret_cast<const double*>(gg.B);
+      o.C = reinterpret_cast<double*>(gg.C);
+      o.M = gg.M;
+      o.N = gg.N;
+      o.K = gg.K;
+      o.lda = gg.lda;
+      o.ldb = gg.ldb;
+      o.ldc = gg.ldc;
+      goz.push_back(o);
+    } else {
+      gsimt.push_back(gg);
+    }
+  }
+  if (!gsimt.empty()) {
+    double fl = 0, by = 0;
+    int mx = 0;
+    for (const auto& gg : gsimt) {
+      fl += 2.0 * gg.M * (double)gg.N * gg.K;
+      by += sizeof(R) * (2.0 * gg.M * (double)gg.K + 2.0 * gg.M * (double)gg.N);
+      mx = std::max(mx, std::max(gg.M, gg.N));
+    }
+    GemmDesc<R>* dg = stg.push(gsimt, st);
+    gemm_batched<R>(dg, (int)gsimt.size(), mx, mx, R(1), R(1), st,
+                    sizeof(R) == 8 ? "gemm_schur<f64>" : "gemm_schur<f32>", fl, by);
     ck(cudaGetLastError());
   }
+  if (!goz.empty()) {
+    const size_t wb = oz_plan(goz);
+    PoolBuf ow;
+    ow.alloc(wb, st);
+    OzDesc* dz = stg.push(goz, st);
+    ck(oz_gemm(dz, goz, ow.p, wb, 1.0, 1.0, H.status.as<int>(), st, "gemm_schur_tc<f64>"));
+  }
+  (void)schur_flops;
+  (void)schur_bytes;
 }
 
 void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool dev_ptrs) {
@@ -462,7 +498,8 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
   for (auto& L : H.lev)
     bytes += stage_bytes<MergeDesc<double>>(L.boxes.size()) +
              stage_bytes<LuDesc<double>>(L.boxes.size()) +
-             stage_bytes<GemmDesc<double>>(L.boxes.size());
+             stage_bytes<GemmDesc<double>>(L.boxes.size()) +
+             stage_bytes<OzDesc>(L.boxes.size());
   stg.begin(bytes, st);
   H.keep.begin(stage_bytes<SolveScatterDesc>(nb) + stage_bytes<BodyDesc>(nb) +
                    4 * 256 * (H.lev.size() + 2),
@@ -630,6 +667,10 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
   ck(e2);
   Tleaf.clear();
   Tlev.clear();
+  if (bad < 0) {
+    g_last_error = "tensor-core GEMM: a wait for an asynchronous copy or MMA gave up";
+    throw CudaError{cudaErrorLaunchTimeout};
+  }
   if (bad) throw bad;
 }
 
@@ -1350,6 +1391,51 @@ int hps_solve_batch(hps_handle h, const double* const* f, int nrhs, double* cons
     if (!f[k] || !u[k]) return HPS_EINVAL;
   g_last_error.clear();
   return solve_guarded(h, f, nrhs, u, h->opt.device_ptrs, info);
+}
+
+int hps_dgemm_tc(int M, int N, int K, double alpha, const double* A, int lda, const double* B,
+                 int ldb, double beta, double* C, int ldc) {
+  if (M < 1 || N < 1 || K < 1 || lda < M || ldb < K || ldc < M || !A || !B || !C)
+    return HPS_EINVAL;
+  g_last_error.clear();
+  try {
+    cudaStream_t st = nullptr;
+    ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    std::vector<OzDesc> h(1);
+    h[0].A = A;
+    h[0].B = B;
+    h[0].C = C;
+    h[0].M = M;
+    h[0].N = N;
+    h[0].K = K;
+    h[0].lda = lda;
+    h[0].ldb = ldb;
+    h[0].ldc = ldc;
+    const size_t wb = oz_plan(h);
+    int rc = HPS_OK;
+    {
+      PoolBuf ow, dd, stt;
+      ow.alloc(wb, st);
+      dd.alloc(sizeof(OzDesc), st);
+      stt.alloc(sizeof(int), st);
+      ck(cudaMemcpyAsync(dd.p, h.data(), sizeof(OzDesc), cudaMemcpyHostToDevice, st));
+      ck(cudaMemsetAsync(stt.p, 0, sizeof(int), st));
+      ck(oz_gemm(dd.as<OzDesc>(), h, ow.p, wb, alpha, beta, stt.as<int>(), st, "dgemm_tc<f64>"));
+      int hst = 0;
+      ck(cudaMemcpyAsync(&hst, stt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      if (hst != 0) {
+        g_last_error = "tensor-core GEMM: a wait gave up";
+        rc = HPS_EDEVICE;
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  }
 }
 
 int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* opt_in, int nrhs,

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <vector>
 
 namespace hps {
 
@@ -149,6 +150,30 @@ void solve_root_scatter(const RootDesc* d, int nprob, int max_nbnd, int nrhs, do
 void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, const double* u3,
                          int64_t u3_total, double* uext, int64_t ext_total, int nrhs,
                          cudaStream_t st);
+
+// ---- FP64 GEMM on the tensor cores by exact BF16 splitting (hps_ozaki.cu)
+// C = alpha A B + beta C, column-major, per descriptor.  oz_plan fills the
+// tiling and workspace offsets and returns the workspace bytes; oz_gemm runs
+// exponents, splitting and the tensor-core products.  A wait that gives up
+// sets *status to -1 (a device error, distinct from pivot failures > 0).
+struct OzDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  int M, N, K, lda, ldb, ldc;
+  int mt = 0, nt = 0, nkb = 0;
+  int ea_off = 0, eb_off = 0;
+  int64_t a_off = 0, b_off = 0;
+};
+size_t oz_plan(std::vector<OzDesc>& ds);
+cudaError_t oz_gemm(const OzDesc* d_desc, const std::vector<OzDesc>& h, void* work,
+                    size_t work_bytes, double alpha, double beta, int* status, cudaStream_t st,
+                    const char* name);
+// Products worth the splitting: large enough that the tensor-core path beats
+// FP64 FMAs (a property of the product alone, so batches keep solo results).
+inline bool oz_eligible(int M, int N, int K) {
+  return M >= 128 && N >= 128 && K >= 64 && (double)M * N * K >= 8.0e6;
+}
 
 // ---- accelerated refinement (hps_refine.cu)
 constexpr int kAaMaxDepth = 8;               // longest Anderson history

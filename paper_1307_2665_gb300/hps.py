@@ -32,7 +32,7 @@ EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_solve_ex", "hps_query", "hps_free", "hps_status_string", "hps_kernel_launches",
            "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error",
            "hps_solve_static", "hps_build_batch", "hps_solve_batch", "hps_batch_size",
-           "hps_estimate_bytes", "hps_release_workspace",
+           "hps_estimate_bytes", "hps_release_workspace", "hps_dgemm_tc",
            # include/hps_serve.h
            "hps_server_default_options", "hps_server_create", "hps_server_destroy",
            "hps_server_submit_build", "hps_server_submit_solve", "hps_server_wait",
@@ -146,6 +146,9 @@ def lib():
     L.hps_estimate_bytes.argtypes = [ctypes.POINTER(Problem), ctypes.c_int, ctypes.POINTER(Options),
                                      ctypes.c_int, i64p, i64p, i64p]
     L.hps_release_workspace.argtypes = [vp]
+    L.hps_dgemm_tc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp,
+                               ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int]
+    L.hps_dgemm_tc.restype = ctypes.c_int
     L.hps_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
     L.hps_server_default_options.restype = None
     L.hps_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
