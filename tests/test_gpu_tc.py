@@ -45,6 +45,7 @@ def test_tc_gemm_matches_extended_precision(M, N, K):
     B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-14, 14, (1, N)))
     A[3, :] = 0.0  # a zero row
     B[:, 5] *= 1e-300  # tiny column
+    B[:, 7] = 0.0  # a zero column
     C = rng.standard_normal((M, N))
     for alpha, beta in ((1.0, 0.0), (1.0, 1.0), (-0.5, 2.0)):
         got = run_tc(A, B, C, alpha, beta)
