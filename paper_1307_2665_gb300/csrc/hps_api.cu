@@ -324,6 +324,26 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   std::vector<int> hn(nm);
   double gather_bytes = 0.0, schur_flops = 0.0, schur_bytes = 0.0;
   int64_t ot = 0;
+  // Mixed mode, FP64 merges large enough for the tensor cores: the LU solves
+  // for W = (T33^a - T33^b)^{-1} only (identity right-hand side, 2 m^3 flops
+  // instead of 2 m^2 ne) and S = W [-T31^a | T32^b] is one tensor-core product.
+  // An explicit inverse is not backward stable (its residual can be cond times
+  // that of the substitution); the refinement absorbs that, so FP64 mode keeps
+  // the substitution.  [-T31^a | T32^b] is gathered into a temporary.  The
+  // choice depends on the merge's own shape.
+  const bool w_first = H.mixed && sizeof(R) == 8;
+  std::vector<OzDesc> sw;
+  int64_t tmp_tot = 0;
+  std::vector<int64_t> tmp_off(nm, -1);
+  for (int i = 0; i < nm && w_first; ++i) {
+    const MergeShape& sh = pl.shapes[pl.boxes[L.boxes[i]].shape];
+    if (oz_eligible(sh.m, sh.ne, sh.m)) {
+      tmp_off[i] = tmp_tot;
+      tmp_tot += (int64_t)sh.m * sh.ne;
+    }
+  }
+  PoolBuf Btmp;
+  Btmp.alloc((size_t)tmp_tot * sizeof(R), st);
   for (int i = 0; i < nm; ++i) {
     const int b = L.boxes[i];
     const Box& B = pl.boxes[b];
@@ -334,11 +354,13 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
     g.ta64 = Tref[B.child[0]].f64;
     g.Tb = Tref[B.child[1]].p;
     g.tb64 = Tref[B.child[1]].f64;
+    R* const S_final = L.S->as<R>() + L.s_off[i];
+    const bool wf = tmp_off[i] >= 0;
     g.Aw = Aw.as<R>() + aw_off[i];
-    g.S = L.S->as<R>() + L.s_off[i];
+    g.S = wf ? Btmp.as<R>() + tmp_off[i] : S_final;
     g.Cw = Cw.as<R>() + L.cw_off[i];
     g.Tp = tp ? Tout.as<R>() + ot : nullptr;
-    g.W = H.mixed ? g.S + (int64_t)sh.m * sh.ne : nullptr;
+    g.W = H.mixed ? S_final + (int64_t)sh.m * sh.ne : nullptr;
     g.src = H.maps.as<int>() + H.src_off[B.shape];
     g.na = sh.na;
     g.nb = sh.nb;
@@ -348,19 +370,32 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
     g.j3b = sh.j3b;
     lu[i].A = g.Aw;
     lu[i].ipiv = piv.as<int>() + piv_off[i];
-    lu[i].B = g.S;
+    lu[i].B = wf ? g.W : g.S;
     lu[i].m = sh.m;
     lu[i].lda = sh.m;
-    lu[i].nrhs = sh.ne + (H.mixed ? sh.m : 0);
+    lu[i].nrhs = wf ? sh.m : sh.ne + (H.mixed ? sh.m : 0);
     lu[i].ldb = sh.m;
     lu[i].box = b;
     hn[i] = lu[i].nrhs;
+    if (wf) {
+      OzDesc o;
+      o.A = reinterpret_cast<const double*>(g.W);
+      o.B = reinterpret_cast<const double*>(g.S);
+      o.C = reinterpret_cast<double*>(S_final);
+      o.M = sh.m;
+      o.N = sh.ne;
+      o.K = sh.m;
+      o.lda = sh.m;
+      o.ldb = sh.m;
+      o.ldc = sh.m;
+      sw.push_back(o);
+    }
     gather_bytes += (sizeof(R) + 8.0) *
                     ((double)sh.m * sh.m + 2.0 * sh.m * sh.ne + (tp ? (double)sh.ne * sh.ne : 0.0));
     if (tp) {
       GemmDesc<R> gg;
       gg.A = g.Cw;
-      gg.B = g.S;
+      gg.B = S_final;
       gg.C = g.Tp;
       gg.M = sh.ne;
       gg.N = sh.ne;
@@ -380,9 +415,16 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   LuDesc<R>* dlu = stg.push(lu, st);
   merge_gather<R>(dmd, nm, max_work, st, gather_bytes);
   ck(cudaGetLastError());
-  lu_solve_batched<R>(dlu, nm, L.max_m, L.max_ne + (H.mixed ? L.max_m : 0), kLuFactor,
+  lu_solve_batched<R>(dlu, nm, L.max_m, nm ? *std::max_element(hn.begin(), hn.end()) : 0, kLuFactor,
                       H.status.as<int>(), st, L.hm.data(), hn.data());
   ck(cudaGetLastError());
+  if (!sw.empty()) {  // S = W [-T31^a | T32^b] on the tensor cores
+    const size_t wb = oz_plan(sw);
+    PoolBuf ow;
+    ow.alloc(wb, st);
+    OzDesc* dz = stg.push(sw, st);
+    ck(oz_gemm(dz, sw, ow.p, wb, 1.0, 0.0, H.status.as<int>(), st, "gemm_s_tc<f64>"));
+  }
   // FP64 products large enough go to the tensor cores (exact BF16 splitting);
   // the choice depends on each product's own shape only
   std::vector<GemmDesc<R>> gsimt;
@@ -499,7 +541,7 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
     bytes += stage_bytes<MergeDesc<double>>(L.boxes.size()) +
              stage_bytes<LuDesc<double>>(L.boxes.size()) +
              stage_bytes<GemmDesc<double>>(L.boxes.size()) +
-             stage_bytes<OzDesc>(L.boxes.size());
+             2 * stage_bytes<OzDesc>(L.boxes.size());
   stg.begin(bytes, st);
   H.keep.begin(stage_bytes<SolveScatterDesc>(nb) + stage_bytes<BodyDesc>(nb) +
                    4 * 256 * (H.lev.size() + 2),
@@ -1484,6 +1526,14 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
         if (mixed) sres += (int64_t)sh.ne * sh.m * bm;
         if (B.parent >= 0 || opt.form_root_dtn) t_at[h] += (int64_t)sh.ne * sh.ne * bm;
         tmp_at[h] += (int64_t)sh.m * sh.m * bm + (mixed ? 0 : (int64_t)sh.ne * sh.m * bm);
+        if (bm == 8) {  // tensor-core products: S's temporaries, split operands
+          const int64_t m = sh.m, ne = sh.ne, kp = (m + 31) / 32 * 32;
+          if (mixed && oz_eligible(sh.m, sh.ne, sh.m))
+            tmp_at[h] += m * ne * 8 + 16 * ((m + 127) / 128 * 128) * kp +
+                         16 * ((ne + 127) / 128 * 128) * kp + 4 * (m + ne);
+          if (oz_eligible(sh.ne, sh.ne, sh.m))
+            tmp_at[h] += 32 * ((ne + 127) / 128 * 128) * kp + 8 * ne;
+        }
         u3_rows += sh.m;
         rows += sh.m;
       }
