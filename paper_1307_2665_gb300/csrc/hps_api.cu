@@ -143,18 +143,30 @@ struct Stager {
     if (dev.bytes < bytes) dev.alloc(bytes, st);
     used = 0;
   }
-  template <typename T>
-  T* push(const std::vector<T>& v, cudaStream_t st) {
+  void* push_raw(const void* src, size_t n, cudaStream_t st) {
     size_t off = (used + 255) & ~size_t(255);
-    size_t n = v.size() * sizeof(T);
     if (off + n > cap || off + n > dev.bytes) throw std::bad_alloc();
     if (n) {
-      std::memcpy(static_cast<char*>(host) + off, v.data(), n);
+      std::memcpy(static_cast<char*>(host) + off, src, n);
       ck(cudaMemcpyAsync(static_cast<char*>(dev.p) + off, static_cast<char*>(host) + off, n,
                          cudaMemcpyHostToDevice, st));
     }
     used = off + n;
-    return reinterpret_cast<T*>(static_cast<char*>(dev.p) + off);
+    return static_cast<char*>(dev.p) + off;
+  }
+  template <typename T>
+  T* push(const std::vector<T>& v, cudaStream_t st) {
+    return static_cast<T*>(push_raw(v.data(), v.size() * sizeof(T), st));
+  }
+};
+
+// Raw pushes through the stager (callback form for the two-level LU).
+struct StagerCtx {
+  Stager* stg;
+  cudaStream_t st;
+  static void* push(void* ctx, const void* src, size_t n) {
+    auto* c = static_cast<StagerCtx*>(ctx);
+    return c->stg->push_raw(src, n, c->st);
   }
 };
 
@@ -412,12 +424,43 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
     }
   }
   MergeDesc<R>* dmd = stg.push(md, st);
-  LuDesc<R>* dlu = stg.push(lu, st);
   merge_gather<R>(dmd, nm, max_work, st, gather_bytes);
   ck(cudaGetLastError());
-  lu_solve_batched<R>(dlu, nm, L.max_m, nm ? *std::max_element(hn.begin(), hn.end()) : 0, kLuFactor,
-                      H.status.as<int>(), st, L.hm.data(), hn.data());
-  ck(cudaGetLastError());
+  // FP64 systems large enough take the two-level LU (its rank-256 updates on
+  // the tensor cores), the rest the one-level LU; the choice depends on each
+  // system's own size
+  std::vector<LuDesc<R>> lu1;
+  std::vector<int> hm1, hn1;
+  std::vector<LuDesc<double>> lu2;
+  std::vector<LuDescHost> lh2;
+  for (int i = 0; i < nm; ++i) {
+    if (sizeof(R) == 8 && lu_tc_eligible(lu[i].m)) {
+      LuDesc<double> d2;
+      std::memcpy(&d2, &lu[i], sizeof(d2));
+      lu2.push_back(d2);
+      lh2.push_back({reinterpret_cast<double*>(lu[i].A), reinterpret_cast<double*>(lu[i].B),
+                     lu[i].m, lu[i].lda, lu[i].nrhs, lu[i].ldb});
+    } else {
+      lu1.push_back(lu[i]);
+      hm1.push_back(lu[i].m);
+      hn1.push_back(hn[i]);
+    }
+  }
+  if (!lu1.empty()) {
+    LuDesc<R>* dlu = stg.push(lu1, st);
+    lu_solve_batched<R>(dlu, (int)lu1.size(), *std::max_element(hm1.begin(), hm1.end()),
+                        *std::max_element(hn1.begin(), hn1.end()), kLuFactor, H.status.as<int>(),
+                        st, hm1.data(), hn1.data());
+    ck(cudaGetLastError());
+  }
+  if (!lu2.empty()) {
+    LuDesc<double>* dlu = stg.push(lu2, st);
+    const size_t wb = lu_tc_workspace(lh2);
+    PoolBuf lw;
+    lw.alloc(wb, st);
+    StagerCtx sctx{&stg, st};
+    ck(lu_solve_tc(dlu, lh2, H.status.as<int>(), st, &StagerCtx::push, &sctx, lw.p, wb));
+  }
   if (!sw.empty()) {  // S = W [-T31^a | T32^b] on the tensor cores
     const size_t wb = oz_plan(sw);
     PoolBuf ow;
@@ -537,11 +580,16 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
   const size_t nb = pl.boxes.size();
   Stager stg;
   size_t bytes = 8 * 256 + stage_bytes<LuDesc<double>>(nl_tot) + 256 * H.lg.size();
-  for (auto& L : H.lev)
+  for (auto& L : H.lev) {
     bytes += stage_bytes<MergeDesc<double>>(L.boxes.size()) +
-             stage_bytes<LuDesc<double>>(L.boxes.size()) +
+             2 * stage_bytes<LuDesc<double>>(L.boxes.size()) +
              stage_bytes<GemmDesc<double>>(L.boxes.size()) +
              2 * stage_bytes<OzDesc>(L.boxes.size());
+    // two-level LU: per outer block, at most four arrays of two products per system
+    if (L.f64 && lu_tc_eligible(L.max_m))
+      bytes += (size_t)((L.max_m + kLuOuter - 1) / kLuOuter) * 4 *
+               stage_bytes<OzDesc>(2 * L.boxes.size());
+  }
   stg.begin(bytes, st);
   H.keep.begin(stage_bytes<SolveScatterDesc>(nb) + stage_bytes<BodyDesc>(nb) +
                    4 * 256 * (H.lev.size() + 2),
@@ -1533,6 +1581,10 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
                          16 * ((ne + 127) / 128 * 128) * kp + 4 * (m + ne);
           if (oz_eligible(sh.ne, sh.ne, sh.m))
             tmp_at[h] += 32 * ((ne + 127) / 128 * 128) * kp + 8 * ne;
+          if (lu_tc_eligible(sh.m)) {  // two-level LU: split operands of one outer step
+            const int64_t nr = ne + m;
+            tmp_at[h] += 16 * (kLuOuter + 32) * (3 * (m + 128) + nr + 64) + 4 * (3 * m + nr);
+          }
         }
         u3_rows += sh.m;
         rows += sh.m;

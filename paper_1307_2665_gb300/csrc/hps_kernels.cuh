@@ -80,6 +80,27 @@ constexpr int kLuFactor = 0, kLuFactorKeep = 1, kLuSolveOnly = 2;
 template <typename R>
 void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrhs, int mode,
                       int* d_status, cudaStream_t st, const int* h_m, const int* h_nrhs);
+// Two-level blocked LU (FP64, kLuFactor semantics) for large systems: outer
+// block columns of kLuOuter are factored by the one-level steps restricted to
+// the block, then the block's interchanges and unit-lower solve reach the far
+// columns and one rank-kLuOuter product updates the trailing rows; backward
+// substitution is blocked the same way.  The rank-kLuOuter products large
+// enough run on the tensor cores (oz_gemm), the rest as FP64 tile GEMMs.
+// h: host copies of the descriptors (d_desc their device copy), every one
+// lu_tc_eligible.  push copies a host array to device memory that stays valid
+// while the stream runs this call.  ws: lu_tc_workspace(h) bytes of scratch.
+constexpr int kLuOuter = 256;
+inline bool lu_tc_eligible(int m) { return m >= 2 * kLuOuter; }
+struct LuDescHost {
+  double* A;
+  double* B;
+  int m, lda, nrhs, ldb;
+};
+size_t lu_tc_workspace(const std::vector<LuDescHost>& h);
+cudaError_t lu_solve_tc(const LuDesc<double>* d_desc, const std::vector<LuDescHost>& h,
+                        int* d_status, cudaStream_t st,
+                        void* (*push)(void* ctx, const void* src, size_t bytes), void* push_ctx,
+                        void* ws, size_t ws_bytes);
 // name / flops / bytes: launch accounting (algorithmic work of this launch).
 // ws / ws_elems (optional): scratch of element type R.  With a scratch, a
 // launch whose largest K exceeds kSplitK splits K into chunks of kSplitK across

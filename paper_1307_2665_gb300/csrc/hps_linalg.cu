@@ -396,25 +396,104 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
 }
 
 // ----------------------------------------- LU: swaps + unit-lower block solve
-// For every column outside the panel: apply the panel's row interchanges, then
-// (trailing columns of A and columns of B) solve with the unit-lower L11.
-// One warp per column.  The interchanges of a panel move at most 2*nb rows;
-// their net permutation is computed once per CTA.
+// The interchanges of one panel (rows k0.., pivots ipiv[k0..k0+nbk)) move at
+// most 2*nb rows: rows_inv lists them (relative to k0; the block rows first)
+// and slot t takes the old value of slot src_of[t].  Returns their count.
+__device__ int panel_perm(const int* ipiv, int k0, int nbk, int* rows_inv, int* src_of) {
+  int nr = nbk;
+  for (int i = 0; i < nbk; ++i) rows_inv[i] = i;
+  for (int j = 0; j < nbk; ++j) {
+    int pr = ipiv[k0 + j] - k0;
+    bool found = false;
+    for (int t = 0; t < nr; ++t) found |= (rows_inv[t] == pr);
+    if (!found) rows_inv[nr++] = pr;
+  }
+  // apply the interchanges to the slot contents
+  int content[2 * kNB];
+  for (int t = 0; t < nr; ++t) content[t] = t;
+  for (int j = 0; j < nbk; ++j) {
+    int pr = ipiv[k0 + j] - k0;
+    int tj = j, tp = 0;
+    for (int t = 0; t < nr; ++t)
+      if (rows_inv[t] == pr) tp = t;
+    int c = content[tj];
+    content[tj] = content[tp];
+    content[tp] = c;
+  }
+  for (int t = 0; t < nr; ++t) src_of[t] = content[t];
+  return nr;
+}
+
+// One warp applies a panel's interchanges to column x (rows relative to k0)
+// and returns, in lanes < nbk, the new block-row values (not yet stored).
+template <typename R>
+__device__ __forceinline__ R warp_permute(R* x, const int* rows_inv, const int* src_of, int nr,
+                                          int lane) {
+  // gather the involved rows (lane holds slots lane and lane+32)
+  R v0 = lane < nr ? x[rows_inv[lane]] : R(0);
+  R v1 = (lane + 32) < nr ? x[rows_inv[lane + 32]] : R(0);
+  // permuted values: slot t takes the old value of slot src_of[t]
+  int s0 = lane < nr ? src_of[lane] : 0;
+  int s1 = (lane + 32) < nr ? src_of[lane + 32] : 0;
+  R n0a = __shfl_sync(0xffffffffu, v0, s0 & 31);
+  R n0b = __shfl_sync(0xffffffffu, v1, s0 & 31);
+  R n1a = __shfl_sync(0xffffffffu, v0, s1 & 31);
+  R n1b = __shfl_sync(0xffffffffu, v1, s1 & 31);
+  R w0 = s0 < 32 ? n0a : n0b;
+  R w1 = s1 < 32 ? n1a : n1b;
+  if ((lane + 32) < nr) x[rows_inv[lane + 32]] = w1;
+  return w0;
+}
+
+// Columns a panel's interchanges and block solve act on.  part < 0 (one-level
+// LU): the trailing columns of A and the columns of B, plus the columns left of
+// the panel when swap_left.  Two-level LU (outer block column [K0, oe), oe =
+// min(K0 + kLuOuter, m)): part 0 is the outer block itself, its columns left of
+// the panel (interchanges only) and right of it; part 1 is the far columns,
+// A's [oe, m) and B, solved only (their interchanges were applied before).
+struct SwapCols {
+  int nleft, left0, a_lo, a_hi, nb;
+};
+__device__ __forceinline__ SwapCols swap_cols(int part, int K0, int k0, int nbk, int m, int nrhs,
+                                              int swap_left, int b_only) {
+  SwapCols c;
+  if (part < 0) {
+    c.nleft = (swap_left && !b_only) ? k0 : 0;
+    c.left0 = 0;
+    c.a_lo = k0 + nbk;
+    c.a_hi = b_only ? c.a_lo : m;
+    c.nb = nrhs;
+  } else {
+    const int oe = min(K0 + kLuOuter, m);
+    c.nleft = part == 0 ? k0 - K0 : 0;
+    c.left0 = K0;
+    c.a_lo = part == 0 ? k0 + nbk : oe;
+    c.a_hi = part == 0 ? oe : m;
+    c.nb = part == 0 ? 0 : nrhs;
+  }
+  return c;
+}
+
+// For every column of the region: apply the panel's row interchanges (unless
+// part 1), then (all but the left columns) solve with the unit-lower L11.
+// One warp per column.
 template <typename R>
 __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restrict__ d, int k0,
                                                       int chunks, int cols_per_cta,
-                                                      int swap_left, int b_only) {
+                                                      int swap_left, int b_only, int part,
+                                                      int K0) {
   const LuDesc<R> D = d[blockIdx.x / chunks];
   const int chunk = blockIdx.x % chunks;
   const int m = D.m;
   if (k0 >= m) return;
   const int nbk = min(kNB, m - k0);
-  const int nleft = (swap_left && !b_only) ? k0 : 0;
-  const int ntr = b_only ? 0 : m - k0 - nbk;
-  const int total = nleft + ntr + D.nrhs;
+  const SwapCols sc = swap_cols(part, K0, k0, nbk, m, D.nrhs, swap_left, b_only);
+  const int nleft = sc.nleft, ntr = sc.a_hi - sc.a_lo;
+  const int total = nleft + ntr + sc.nb;
   const int cbeg = chunk * cols_per_cta;
   if (cbeg >= total) return;
   const int cend = min(total, cbeg + cols_per_cta);
+  const bool do_swap = part != 1;
   __shared__ R L11[kNB * kNB];
   __shared__ int rows_inv[2 * kNB];  // involved rows (relative to k0)
   __shared__ int src_of[2 * kNB];    // new value of rows_inv[t] comes from rows_inv[src_of[t]]
@@ -423,31 +502,7 @@ __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restric
     int i = e % nbk, j = e / nbk;
     L11[i + j * kNB] = D.A[(k0 + i) + (size_t)(k0 + j) * D.lda];
   }
-  if (threadIdx.x == 0) {
-    // rows 0..nbk-1 plus every pivot row beyond the block
-    int nr = nbk;
-    for (int i = 0; i < nbk; ++i) rows_inv[i] = i;
-    for (int j = 0; j < nbk; ++j) {
-      int pr = D.ipiv[k0 + j] - k0;
-      bool found = false;
-      for (int t = 0; t < nr; ++t) found |= (rows_inv[t] == pr);
-      if (!found) rows_inv[nr++] = pr;
-    }
-    // apply the interchanges to the slot contents
-    int content[2 * kNB];
-    for (int t = 0; t < nr; ++t) content[t] = t;
-    for (int j = 0; j < nbk; ++j) {
-      int pr = D.ipiv[k0 + j] - k0;
-      int tj = j, tp = 0;
-      for (int t = 0; t < nr; ++t)
-        if (rows_inv[t] == pr) tp = t;
-      int c = content[tj];
-      content[tj] = content[tp];
-      content[tp] = c;
-    }
-    for (int t = 0; t < nr; ++t) src_of[t] = content[t];
-    s_nr = nr;
-  }
+  if (threadIdx.x == 0) s_nr = do_swap ? panel_perm(D.ipiv, k0, nbk, rows_inv, src_of) : nbk;
   __syncthreads();
   const int nr = s_nr;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -455,28 +510,20 @@ __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restric
     R* x;
     bool solve;
     if (col < nleft) {
-      x = D.A + k0 + (size_t)col * D.lda;
+      x = D.A + k0 + (size_t)(sc.left0 + col) * D.lda;
       solve = false;
     } else if (col < nleft + ntr) {
-      x = D.A + k0 + (size_t)(k0 + nbk + (col - nleft)) * D.lda;
+      x = D.A + k0 + (size_t)(sc.a_lo + (col - nleft)) * D.lda;
       solve = true;
     } else {
       x = D.B + k0 + (size_t)(col - nleft - ntr) * D.ldb;
       solve = true;
     }
-    // gather the involved rows (lane holds slots lane and lane+32)
-    R v0 = lane < nr ? x[rows_inv[lane]] : R(0);
-    R v1 = (lane + 32) < nr ? x[rows_inv[lane + 32]] : R(0);
-    // permuted values: slot t takes the old value of slot src_of[t]
-    int s0 = lane < nr ? src_of[lane] : 0;
-    int s1 = (lane + 32) < nr ? src_of[lane + 32] : 0;
-    R n0a = __shfl_sync(0xffffffffu, v0, s0 & 31);
-    R n0b = __shfl_sync(0xffffffffu, v1, s0 & 31);
-    R n1a = __shfl_sync(0xffffffffu, v0, s1 & 31);
-    R n1b = __shfl_sync(0xffffffffu, v1, s1 & 31);
-    R w0 = s0 < 32 ? n0a : n0b;
-    R w1 = s1 < 32 ? n1a : n1b;
-    if ((lane + 32) < nr) x[rows_inv[lane + 32]] = w1;
+    R w0;
+    if (do_swap)
+      w0 = warp_permute(x, rows_inv, src_of, nr, lane);
+    else
+      w0 = lane < nbk ? x[lane] : R(0);
     // w0 of lanes < nbk is the block row; solve with unit-lower L11
     if (solve) {
       for (int j = 0; j < nbk - 1; ++j) {
@@ -484,15 +531,60 @@ __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restric
         if (lane > j && lane < nbk) w0 = fma(-L11[lane + j * kNB], xj, w0);
       }
     }
-    if (lane < nr) x[rows_inv[lane]] = w0;
+    if (lane < nr) x[do_swap ? rows_inv[lane] : lane] = w0;
+  }
+}
+
+// Two-level LU: the interchanges of every panel of the outer block column
+// [K0, oe), in panel order, applied to the far columns (A's [oe, m) and B).
+// One warp per column; the panels' permutations are computed in parallel.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lu_swap_far(const LuDesc<R>* __restrict__ d, int K0,
+                                                     int chunks, int cols_per_cta) {
+  constexpr int kP = kLuOuter / kNB;
+  const LuDesc<R> D = d[blockIdx.x / chunks];
+  const int chunk = blockIdx.x % chunks;
+  const int m = D.m;
+  if (K0 >= m) return;
+  const int oe = min(K0 + kLuOuter, m);
+  const int nfa = m - oe, total = nfa + D.nrhs;
+  const int cbeg = chunk * cols_per_cta;
+  if (cbeg >= total) return;
+  const int cend = min(total, cbeg + cols_per_cta);
+  const int np = (oe - K0 + kNB - 1) / kNB;
+  __shared__ int rows_inv[kP][2 * kNB];
+  __shared__ int src_of[kP][2 * kNB];
+  __shared__ int s_nr[kP];
+  if (threadIdx.x < np) {
+    const int k0 = K0 + threadIdx.x * kNB;
+    s_nr[threadIdx.x] =
+        panel_perm(D.ipiv, k0, min(kNB, m - k0), rows_inv[threadIdx.x], src_of[threadIdx.x]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int col = cbeg + wid; col < cend; col += nw) {
+    R* x0 = col < nfa ? D.A + (size_t)(oe + col) * D.lda : D.B + (size_t)(col - nfa) * D.ldb;
+    for (int p = 0; p < np; ++p) {
+      R* x = x0 + K0 + p * kNB;
+      const int nr = s_nr[p];
+      const R w0 = warp_permute(x, rows_inv[p], src_of[p], nr, lane);
+      if (lane < nr) x[rows_inv[p][lane]] = w0;
+      __syncwarp();  // the next panel's gather reads rows other lanes wrote
+    }
   }
 }
 
 // ------------------------------------------------------ LU: trailing update
-// Rows k0+nbk..m-1 of (trailing columns of A, columns of B) -= L21 * U12.
+// (rows, columns of A, columns of B) -= L21 * U12 over the panel's nbk columns:
+//   part < 0: rows k0+nbk..m-1, A columns k0+nbk..m-1 and B (one-level LU);
+//   part 0:   rows k0+nbk..m-1, A columns k0+nbk..oe-1 (two-level: inside the
+//             outer block column [K0, oe));
+//   part 1:   rows k0+nbk..oe-1, A columns oe..m-1 and B (the far columns'
+//             block-row solve).
 template <typename R, class TL>
 __global__ void __launch_bounds__(TL::NT) k_lu_update(const LuDesc<R>* __restrict__ d, int k0,
-                                                      int tpm, int tpnA, int tpnB) {
+                                                      int tpm, int tpnA, int tpnB, int part,
+                                                      int K0) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int per = tpm * (tpnA + tpnB);
   const LuDesc<R> D = d[blockIdx.x / per];
@@ -501,17 +593,22 @@ __global__ void __launch_bounds__(TL::NT) k_lu_update(const LuDesc<R>* __restric
   if (k0 >= m) return;
   const int nbk = min(kNB, m - k0);
   const int r0 = k0 + nbk;
-  const int M = m - r0;
+  const int oe = part < 0 ? m : min(K0 + kLuOuter, m);
+  const int r_hi = part == 1 ? oe : m;
+  const int c_lo = part == 1 ? oe : r0, c_hi = part == 0 ? oe : m;
+  const bool with_b = part != 0;
+  const int M = r_hi - r0;
   if (M <= 0) return;
   const int tmi = tile % tpm, tni = tile / tpm;
   const R* L21 = D.A + r0 + (size_t)k0 * D.lda;
   if (tni < tpnA) {
-    const int N = m - r0;
+    const int N = c_hi - c_lo;
     const int m0 = tmi * TL::BM, n0 = tni * TL::BN;
     if (m0 >= M || n0 >= N) return;
-    TL::run(M, N, nbk, R(-1), L21, D.lda, D.A + k0 + (size_t)r0 * D.lda, D.lda, R(1),
-            D.A + r0 + (size_t)r0 * D.lda, D.lda, m0, n0, reinterpret_cast<R*>(smraw));
+    TL::run(M, N, nbk, R(-1), L21, D.lda, D.A + k0 + (size_t)c_lo * D.lda, D.lda, R(1),
+            D.A + r0 + (size_t)c_lo * D.lda, D.lda, m0, n0, reinterpret_cast<R*>(smraw));
   } else {
+    if (!with_b) return;
     const int N = D.nrhs;
     const int m0 = tmi * TL::BM, n0 = (tni - tpnA) * TL::BN;
     if (m0 >= M || n0 >= N) return;
@@ -564,20 +661,22 @@ __global__ void __launch_bounds__(256) k_trsm_upper(const LuDesc<R>* __restrict_
 }
 
 // ---------------------------------------------- back substitution: update
-// Rows 0..kb0-1 of B -= U[0:kb0, kb0:kb0+nbk] * B[kb0:kb0+nbk, :].
+// Rows rlo..kb0-1 of B -= U[rlo:kb0, kb0:kb0+nbk] * B[kb0:kb0+nbk, :]
+// (rlo = 0 in the one-level LU, the outer block's first row in the two-level).
 template <typename R, class TL>
 __global__ void __launch_bounds__(TL::NT) k_backsub_update(const LuDesc<R>* __restrict__ d,
-                                                           int kb0, int tpm, int tpn) {
+                                                           int kb0, int tpm, int tpn, int rlo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int per = tpm * tpn;
   const LuDesc<R> D = d[blockIdx.x / per];
   const int tile = blockIdx.x % per;
-  if (kb0 >= D.m || kb0 == 0) return;
+  if (kb0 >= D.m || kb0 <= rlo) return;
   const int nbk = min(kNB, D.m - kb0);
+  const int M = kb0 - rlo;
   const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
-  if (m0 >= kb0 || n0 >= D.nrhs) return;
-  TL::run(kb0, D.nrhs, nbk, R(-1), D.A + (size_t)kb0 * D.lda, D.lda, D.B + kb0, D.ldb, R(1), D.B,
-          D.ldb, m0, n0, reinterpret_cast<R*>(smraw));
+  if (m0 >= M || n0 >= D.nrhs) return;
+  TL::run(M, D.nrhs, nbk, R(-1), D.A + rlo + (size_t)kb0 * D.lda, D.lda, D.B + kb0, D.ldb, R(1),
+          D.B + rlo, D.ldb, m0, n0, reinterpret_cast<R*>(smraw));
 }
 
 // ------------------------------------------------------------------ driver
@@ -638,7 +737,7 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
       });
       prof::Scope sc(TName<R>::swap(), st, fl, by);
       k_lu_swap_trsm<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(
-          d_desc, k0, chunks, cols_per_cta, swap_left ? 1 : 0, factor ? 0 : 1);
+          d_desc, k0, chunks, cols_per_cta, swap_left ? 1 : 0, factor ? 0 : 1, -1, 0);
     }
     int rem = max_m - k0 - kNB;
     if (rem > 0) {
@@ -659,7 +758,8 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
         return (M * nbk + nbk * N + 2.0 * M * N) * es;
       });
       prof::Scope sc(TName<R>::update(), st, fl, by);
-      k_lu_update<R, TL><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d_desc, k0, tpm, tpnA, tpnB);
+      k_lu_update<R, TL><<<(unsigned)blocks, TL::NT, TL::SMEM, st>>>(d_desc, k0, tpm, tpnA, tpnB,
+                                                                    -1, 0);
     }
   }
   const int last = ((max_m - 1) / kNB) * kNB;
@@ -693,14 +793,271 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
       if (max_nrhs <= 16) {
         int tpm = (kb0 + TN::BM - 1) / TN::BM, tpn = (max_nrhs + TN::BN - 1) / TN::BN;
         k_backsub_update<R, TN><<<(unsigned)((long long)nd * tpm * tpn), TN::NT, TN::SMEM, st>>>(
-            d_desc, kb0, tpm, tpn);
+            d_desc, kb0, tpm, tpn, 0);
       } else {
         int tpm = (kb0 + TL::BM - 1) / TL::BM, tpn = (max_nrhs + TL::BN - 1) / TL::BN;
         k_backsub_update<R, TL><<<(unsigned)((long long)nd * tpm * tpn), TL::NT, TL::SMEM, st>>>(
-            d_desc, kb0, tpm, tpn);
+            d_desc, kb0, tpm, tpn, 0);
       }
     }
   }
+}
+
+// ------------------------------------------------------- two-level blocked LU
+namespace {
+
+// The rank-kLuOuter products of one outer step: those worth the splitting on
+// the tensor cores, the rest as FP64 tile GEMMs.  C -= A B for each.
+struct TcStep {
+  std::vector<OzDesc> oz;
+  std::vector<GemmDesc<double>> simt;
+  int maxM = 0, maxN = 0, maxK = 0;
+  double simt_flops = 0.0, simt_bytes = 0.0;
+  void add(const double* A, int lda, const double* B, int ldb, double* C, int ldc, int M, int N,
+           int K) {
+    if (M <= 0 || N <= 0 || K <= 0) return;
+    if (oz_eligible(M, N, K)) {
+      OzDesc o;
+      o.A = A;
+      o.B = B;
+      o.C = C;
+      o.M = M;
+      o.N = N;
+      o.K = K;
+      o.lda = lda;
+      o.ldb = ldb;
+      o.ldc = ldc;
+      oz.push_back(o);
+      return;
+    }
+    GemmDesc<double> g;
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.lda = lda;
+    g.ldb = ldb;
+    g.ldc = ldc;
+    simt.push_back(g);
+    maxM = std::max(maxM, M);
+    maxN = std::max(maxN, N);
+    maxK = std::max(maxK, K);
+    simt_flops += 2.0 * M * (double)N * K;
+    simt_bytes += 8.0 * ((double)M * K + (double)K * N + 2.0 * M * N);
+  }
+};
+
+// Forward, after the outer block column [K0, oe) is factored and its block row
+// solved: rows oe..m-1 of A's columns oe..m-1 and of B -= L21 U12, with
+// L21 = A[oe:m, K0:oe] and U12 the block row of those columns.
+TcStep fwd_step(const std::vector<LuDescHost>& h, int K0) {
+  TcStep s;
+  for (const auto& d : h) {
+    if (K0 >= d.m) continue;
+    const int oe = std::min(K0 + kLuOuter, d.m), M = d.m - oe, K = oe - K0;
+    const double* L21 = d.A + oe + (size_t)K0 * d.lda;
+    s.add(L21, d.lda, d.A + K0 + (size_t)oe * d.lda, d.lda, d.A + oe + (size_t)oe * d.lda, d.lda,
+          M, d.m - oe, K);
+    s.add(L21, d.lda, d.B + K0, d.ldb, d.B + oe, d.ldb, M, d.nrhs, K);
+  }
+  return s;
+}
+
+// Backward, once rows K0..oe-1 of B hold the solution: rows 0..K0-1 of B -=
+// U[0:K0, K0:oe] B[K0:oe, :].
+TcStep bwd_step(const std::vector<LuDescHost>& h, int K0) {
+  TcStep s;
+  for (const auto& d : h) {
+    if (K0 >= d.m || K0 == 0) continue;
+    const int oe = std::min(K0 + kLuOuter, d.m);
+    s.add(d.A + (size_t)K0 * d.lda, d.lda, d.B + K0, d.ldb, d.B, d.ldb, K0, d.nrhs, oe - K0);
+  }
+  return s;
+}
+
+}  // namespace
+
+size_t lu_tc_workspace(const std::vector<LuDescHost>& h) {
+  int max_m = 0;
+  for (const auto& d : h) max_m = std::max(max_m, d.m);
+  size_t w = 0;
+  for (int K0 = 0; K0 < max_m; K0 += kLuOuter) {
+    TcStep f = fwd_step(h, K0), b = bwd_step(h, K0);
+    w = std::max(w, oz_plan(f.oz));
+    w = std::max(w, oz_plan(b.oz));
+  }
+  return w;
+}
+
+cudaError_t lu_solve_tc(const LuDesc<double>* d_desc, const std::vector<LuDescHost>& h,
+                        int* d_status, cudaStream_t st,
+                        void* (*push)(void* ctx, const void* src, size_t bytes), void* push_ctx,
+                        void* ws, size_t ws_bytes) {
+  using R = double;
+  using TL = TileSq<R>;
+  const int nd = (int)h.size();
+  if (nd == 0) return cudaSuccess;
+  int max_m = 0, max_nrhs = 0;
+  for (const auto& d : h) {
+    max_m = std::max(max_m, d.m);
+    max_nrhs = std::max(max_nrhs, d.nrhs);
+  }
+  const int smem_max = 224 * 1024;
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel<R>), smem_max))
+    return cudaErrorInvalidValue;
+  const int cpc = 64;  // columns per CTA of the interchange kernels
+  const double es = 8.0;
+  // per-descriptor maxima and sums over the descriptors that reach panel k0
+  auto over = [&](int k0, auto fn) {
+    for (const auto& d : h)
+      if (k0 < d.m) fn(d.m, d.nrhs, std::min(kNB, d.m - k0));
+  };
+  auto run_step = [&](TcStep& s, const char* tc_name, const char* simt_name) -> cudaError_t {
+    if (!s.oz.empty()) {
+      if (oz_plan(s.oz) > ws_bytes) return cudaErrorInvalidValue;
+      auto* dz = static_cast<const OzDesc*>(push(push_ctx, s.oz.data(), s.oz.size() * sizeof(OzDesc)));
+      const cudaError_t e = oz_gemm(dz, s.oz, ws, ws_bytes, -1.0, 1.0, d_status, st, tc_name);
+      if (e != cudaSuccess) return e;
+    }
+    if (!s.simt.empty()) {
+      auto* dg = static_cast<const GemmDesc<double>*>(
+          push(push_ctx, s.simt.data(), s.simt.size() * sizeof(GemmDesc<double>)));
+      gemm_batched<R>(dg, (int)s.simt.size(), s.maxM, s.maxN, R(-1), R(1), st, simt_name,
+                      s.simt_flops, s.simt_bytes, s.maxK);
+    }
+    return cudaGetLastError();
+  };
+  for (int K0 = 0; K0 < max_m; K0 += kLuOuter) {
+    const int kend = std::min(K0 + kLuOuter, max_m);
+    // 1. the outer block column: one-level steps restricted to it
+    for (int k0 = K0; k0 < kend; k0 += kNB) {
+      {
+        double fl = 0.0, by = 0.0;
+        over(k0, [&](int m, int, int nbk) {
+          const int rows = m - k0;
+          for (int jj = 0; jj < nbk; ++jj) fl += (double)(rows - jj - 1) * (2.0 * (nbk - jj - 1) + 1.0);
+          by += 2.0 * rows * nbk * es;
+        });
+        const int rows = max_m - k0;
+        const long long need = (long long)rows * std::min(kNB, rows) * (long long)sizeof(R);
+        const int smem_bytes = (int)std::min<long long>(need, smem_max);
+        prof::Scope sc(TName<R>::panel(), st, fl, by);
+        k_lu_panel<R><<<nd, rows > 512 ? 512 : 256, smem_bytes, st>>>(
+            d_desc, k0, smem_bytes / (int)sizeof(R), d_status);
+      }
+      int cols = 0, Mx = 0, Nx = 0;
+      double fl = 0.0, by = 0.0, flu = 0.0, byu = 0.0;
+      over(k0, [&](int m, int, int nbk) {
+        const int oe = std::min(K0 + kLuOuter, m), right = oe - k0 - nbk, M = m - k0 - nbk;
+        cols = std::max(cols, (k0 - K0) + right);
+        Mx = std::max(Mx, M);
+        Nx = std::max(Nx, right);
+        fl += (double)nbk * (nbk - 1) * right;
+        by += 2.0 * nbk * ((k0 - K0) + right) * es;
+        flu += 2.0 * M * (double)right * nbk;
+        byu += ((double)M * nbk + (double)nbk * right + 2.0 * M * right) * es;
+      });
+      if (cols > 0) {
+        const int chunks = (cols + cpc - 1) / cpc;
+        prof::Scope sc(TName<R>::swap(), st, fl, by);
+        k_lu_swap_trsm<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, k0, chunks,
+                                                                            cpc, 0, 0, 0, K0);
+      }
+      if (Mx > 0 && Nx > 0) {
+        const int tpm = (Mx + TL::BM - 1) / TL::BM, tpn = (Nx + TL::BN - 1) / TL::BN;
+        prof::Scope sc(TName<R>::update(), st, flu, byu);
+        k_lu_update<R, TL><<<(unsigned)((long long)nd * tpm * tpn), TL::NT, TL::SMEM, st>>>(
+            d_desc, k0, tpm, tpn, 0, 0, K0);
+      }
+    }
+    // 2. the far columns: the block's interchanges, then its unit-lower solve
+    {
+      int cols = 0;
+      double by = 0.0;
+      over(K0, [&](int m, int nrhs, int) {
+        const int oe = std::min(K0 + kLuOuter, m);
+        cols = std::max(cols, m - oe + nrhs);
+        by += 2.0 * 2.0 * (oe - K0) * (double)(m - oe + nrhs) * es;
+      });
+      if (cols > 0) {
+        const int chunks = (cols + cpc - 1) / cpc;
+        prof::Scope sc(TName<R>::swap(), st, 0.0, by);
+        k_lu_swap_far<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, K0, chunks,
+                                                                           cpc);
+      }
+    }
+    for (int k0 = K0; k0 < kend; k0 += kNB) {
+      int cols = 0, Mx = 0, NA = 0, NB = 0;
+      double fl = 0.0, by = 0.0, flu = 0.0, byu = 0.0;
+      over(k0, [&](int m, int nrhs, int nbk) {
+        const int oe = std::min(K0 + kLuOuter, m), far = m - oe + nrhs, M = oe - k0 - nbk;
+        cols = std::max(cols, far);
+        fl += (double)nbk * (nbk - 1) * far;
+        by += 2.0 * nbk * far * es;
+        if (M > 0) {
+          Mx = std::max(Mx, M);
+          NA = std::max(NA, m - oe);
+          NB = std::max(NB, nrhs);
+          flu += 2.0 * M * (double)far * nbk;
+          byu += ((double)M * nbk + (double)nbk * far + 2.0 * M * far) * es;
+        }
+      });
+      if (cols > 0) {
+        const int chunks = (cols + cpc - 1) / cpc;
+        prof::Scope sc(TName<R>::swap(), st, fl, by);
+        k_lu_swap_trsm<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, k0, chunks,
+                                                                            cpc, 0, 0, 1, K0);
+      }
+      if (Mx > 0 && NA + NB > 0) {
+        const int tpm = (Mx + TL::BM - 1) / TL::BM;
+        const int tpnA = (NA + TL::BN - 1) / TL::BN, tpnB = (NB + TL::BN - 1) / TL::BN;
+        prof::Scope sc(TName<R>::update(), st, flu, byu);
+        k_lu_update<R, TL><<<(unsigned)((long long)nd * tpm * (tpnA + tpnB)), TL::NT, TL::SMEM,
+                             st>>>(d_desc, k0, tpm, tpnA, tpnB, 1, K0);
+      }
+    }
+    // 3. the trailing rows: one rank-kLuOuter product
+    TcStep f = fwd_step(h, K0);
+    const cudaError_t e = run_step(f, "lu_update_tc<f64>", TName<R>::update());
+    if (e != cudaSuccess) return e;
+  }
+  // backward substitution, blocked the same way
+  const int lastK0 = ((max_m - 1) / kLuOuter) * kLuOuter;
+  for (int K0 = lastK0; K0 >= 0; K0 -= kLuOuter) {
+    const int kend = std::min(K0 + kLuOuter, max_m);
+    for (int kb0 = K0 + ((kend - 1 - K0) / kNB) * kNB; kb0 >= K0; kb0 -= kNB) {
+      {
+        double fl = 0.0, by = 0.0;
+        over(kb0, [&](int, int nrhs, int nbk) {
+          fl += (double)nbk * nbk * nrhs;
+          by += (2.0 * nbk * nrhs + 0.5 * nbk * nbk) * es;
+        });
+        const int chunks = (max_nrhs + 255) / 256;
+        prof::Scope sc(TName<R>::trsm(), st, fl, by);
+        k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, kb0, chunks);
+      }
+      if (kb0 > K0) {
+        double fl = 0.0, by = 0.0;
+        const int M = kb0 - K0;
+        over(kb0, [&](int, int nrhs, int nbk) {
+          fl += 2.0 * M * (double)nrhs * nbk;
+          by += ((double)M * nbk + (double)nbk * nrhs + 2.0 * M * nrhs) * es;
+        });
+        const int tpm = (M + TL::BM - 1) / TL::BM, tpn = (max_nrhs + TL::BN - 1) / TL::BN;
+        prof::Scope sc(TName<R>::backsub(), st, fl, by);
+        k_backsub_update<R, TL><<<(unsigned)((long long)nd * tpm * tpn), TL::NT, TL::SMEM, st>>>(
+            d_desc, kb0, tpm, tpn, K0);
+      }
+    }
+    if (K0 > 0) {
+      TcStep b = bwd_step(h, K0);
+      const cudaError_t e = run_step(b, "backsub_tc<f64>", TName<R>::backsub());
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaGetLastError();
 }
 
 template void lu_solve_batched<double>(const LuDesc<double>*, int, int, int, int, int*,

@@ -108,6 +108,24 @@ def test_config_64x64_convection_diffusion_16rhs():
     assert err < TOL, err
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_level_lu_ragged_blocks(precision):
+    """40 x 40 leaves with q = 13: the top merge's interface system has
+    m = 520 = 2 * 256 + 8 unknowns, so the two-level LU runs two full outer
+    blocks (the first trailing update on the tensor cores) and a ragged one of
+    8 rows whose updates fall back to FP64 FMAs; the levels below keep the
+    one-level LU."""
+    n, p, q = 40, 15, 13
+    f = boundary_data(UNIT, n, n, q, seeds=(3, 4), with_exp=True)
+    prec = hps.HPS_MIXED if precision == "mixed" else hps.HPS_FP64
+    h = hps.hps_build(UNIT, n, n, p, q, gpu_coeffs(UNIT, n, n, p, varcoef), precision=prec)
+    u = hps.hps_solve(h, f)
+    h.close()
+    sol = O.solve_condensed(O.make_problem(UNIT, n, n, p, q, varcoef), f.T)
+    err = np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w))
+    assert err < TOL, err
+
+
 def test_device_pointers_match_host_pointers():
     torch = pytest.importorskip("torch")
     dom, nx, ny, p, q = SKEW, 3, 4, 12, 10
