@@ -14,7 +14,7 @@
  * collocation nodes) and q Gauss-Legendre points on each edge (the nodes of
  * the global unknowns).  hps_build runs Algorithm 1 (leaf DtN maps, Section 3;
  * Schur-complement merges, Section 4, eqs. U_parent and merge); hps_solve runs
- * Algorithm 2 (downward pass) and the leaf post-processing of Section 4.3, and
+ * Algorithm 2 (downward pass) and the leaf post-processing of Section 5.3, and
  * returns u at every leaf's p x p Chebyshev grid.
  *
  * Conventions shared by every entry point:
@@ -102,7 +102,7 @@ int hps_boundary_nodes_grid(hps_domain d, int nx, int ny, int q, double* xy);
 /* Build stage (Algorithm 1): leaf DtN maps T = L4 L3 L2 L1 (Section 3.2) for
  * every leaf, then the merges of Section 4 up the binary tree, storing each
  * merge's solution operator S (eq. U_parent) and each leaf's interior solution
- * operator Y = -A_ii^{-1} A_ie L1 (eq. leaf_solve, Section 4.3) on the device.
+ * operator Y = -A_ii^{-1} A_ie L1 (eq. leaf_solve, Section 5.3) on the device.
  * The tree splits a box's longer side at floor(n/2) (ties: x), so any nx, ny
  * >= 1 is accepted.  q must be below p when nx > 1 and ny > 1: with q == p the
  * side interpolants of Step 1 are bijective and averaging the two values at a
@@ -146,7 +146,7 @@ int hps_solve_batch(hps_handle h, const double* const* f, int nrhs, double* cons
  * 2*nbnd doubles); for a batch handle, of its first problem. */
 int hps_boundary_nodes(hps_handle h, double* xy);
 
-/* Solve stage (Algorithm 2 and Section 4.3): given nrhs Dirichlet data sets f,
+/* Solve stage (Algorithm 2 and Section 5.3): given nrhs Dirichlet data sets f,
  * compute u at every leaf's Chebyshev grid.  In HPS_MIXED mode this runs
  * iterative refinement against the FP64 residual of the global collocation
  * system: each step solves the correction equation (interior residual as a

@@ -22,7 +22,7 @@ oracle writes that system out and solves it by sparse LU:
             beta (right / above): flux^alpha - flux^beta = G, flux being
             L4 L3 w_full: d/dx on vertical sides, d/dy on horizontal sides, in the
             global direction (Section 2, definition of v; Section 3.2, Steps 3-4).
-            G = 0 for eq. (1.1): this is v_3^alpha = v_3^beta, the equation that
+            G = 0 for eq. basic: this is v_3^alpha = v_3^beta, the equation that
             eq. (U_parent) of Section 4 solves.
 
 Non-zero F and G (a body load and a flux jump) are not in the paper; they are
@@ -532,7 +532,7 @@ def solve_condensed(prob: Problem, f, F=None, G=None):
 def leaf_dtn(prob: Problem, l=0):
     """The leaf map T = L4 L3 L2 L1 of Section 3.2 (4q x 4q, sides S, E, N, W,
     each in increasing coordinate, fluxes in the global direction), and the
-    leaf solution operator Y = -A_ii^{-1} A_ie L1 ((p-2)^2 x 4q, Section 4.3)."""
+    leaf solution operator Y = -A_ii^{-1} A_ie L1 ((p-2)^2 x 4q, Section 5.3)."""
     ops = LeafOps(prob.p, prob.q, prob.hx, prob.hy)
     A = ops.operator(_leaf_coef(prob, l))
     Ai = A[ops.Ji]
@@ -672,7 +672,7 @@ def flux_at_cheb(prob: Problem, w, l, side):
 
 # ================================================================ counting
 def gauss_count(n, q):
-    """N = 2 n (n+1) q Gauss nodes on an n x n leaf grid (Section 4.2)."""
+    """N = 2 n (n+1) q Gauss nodes on an n x n leaf grid (Section 5.2)."""
     return 2 * n * (n + 1) * q
 
 

@@ -1,5 +1,5 @@
 // C ABI of libhps: the build stage (Algorithm 1) and the solve stage
-// (Algorithm 2 + Section 4.3) orchestrated over the batched kernels.
+// (Algorithm 2 + Section 5.3) orchestrated over the batched kernels.
 //
 // A handle holds one problem or a batch of independent problems (a forest).
 // Leaves are processed per group of equal (p, q); merges per tree height

@@ -7,7 +7,7 @@
 // interpolant is evaluated at the side's end points (Step 1 extrapolates the
 // Gauss interpolant to the Chebyshev corners).
 //
-// Plan (Section 2 and Section 4.1): the binary tree over the leaves, each box's
+// Plan (Section 2 and Section 5.1): the binary tree over the leaves, each box's
 // exterior ordering, and, per merge geometry, the maps that split the children's
 // exterior nodes into J1, J2, J3 (Algorithm 1, line 6; Figure 3).
 #include <algorithm>

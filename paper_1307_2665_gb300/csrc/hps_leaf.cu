@@ -1,6 +1,6 @@
-// Leaf kernels (Section 3 and Section 4.3).
+// Leaf kernels (Section 3 and Section 5.3).
 //
-// On the p x p Chebyshev grid of a leaf the operator of eq. (1.2) is the
+// On the p x p Chebyshev grid of a leaf the operator of eq. defA is the
 // collocation matrix of Section 3.1,
 //   A = -C11 Dx^2 - 2 C12 Dx Dy - C22 Dy^2 + C1 Dx + C2 Dy + C,
 // with Dx = (2/hx) I (x) D acting along x and Dy = (2/hy) D (x) I along y.  The
@@ -16,7 +16,7 @@
 //                   unit Gauss datum (Steps 3-4: d/dy on horizontal sides, d/dx
 //                   on vertical sides, then evaluation of the side interpolant
 //                   at the q Gauss points).
-//   leaf_post     : w_full = W u_e for the solve (Section 4.3).
+//   leaf_post     : w_full = W u_e for the solve (Section 5.3).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -239,7 +239,7 @@ void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const d
 }
 
 // ------------------------------------------------------------ post-process
-// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 4.3), right-hand sides in
+// w_full = W u_e + [0 ; z] with W = [L1 ; Y] (Section 5.3), right-hand sides in
 // chunks of RC.  The interior rows Y u_e (+ z) run in the element type R of Y.
 // The boundary rows L1 u_e run in FP64: they are the values that neighbouring
 // leaves share and must stay consistent between them.  They are formed first,

@@ -1,7 +1,7 @@
 """Seeded synthetic inputs for the composite spectral solver.
 
 Every function here maps sample coordinates (x, y) to values: coefficient
-fields of the operator of eq. (1.2) and Dirichlet data f on the boundary.
+fields of the operator of eq. defA and Dirichlet data f on the boundary.
 The coordinates come from the caller (the solver's own node helpers, or the
 test oracle's), so this module holds none of the discretisation: no nodes,
 no differentiation, no interpolation.  Both sides of a parity test sample
@@ -9,9 +9,9 @@ the same functions here and nothing else is shared between them.
 
 Sign convention: the operator is
     A u = -c11 u_xx - 2 c12 u_xy - c22 u_yy + c1 u_x + c2 u_y + c u
-(eq. 1.2).  The numerical examples of Section 8 write their PDE as
--Lap u - c1 u_x - c2 u_y - c u = 0 (eq. 8.1); the helpers for those
-examples return coefficients already converted to the eq. (1.2) signs.
+(eq. defA).  The numerical examples of Section 9 write their PDE as
+-Lap u - c1 u_x - c2 u_y - c u = 0 (eq. example); the helpers for those
+examples return coefficients already converted to the eq. defA signs.
 """
 from __future__ import annotations
 
@@ -36,7 +36,7 @@ def laplace(x, y):
 
 
 def convection_diffusion(x, y, amp=100.0):
-    """c11 = c22 = 1, c1 = -amp cos(4 pi y), c2 = amp sin(4 pi x), c = 0 (eq. 1.2 signs)."""
+    """c11 = c22 = 1, c1 = -amp cos(4 pi y), c2 = amp sin(4 pi x), c = 0 (eq. defA signs)."""
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
     return {"c11": _ones_like(x), "c12": None, "c22": _ones_like(x),
@@ -45,7 +45,7 @@ def convection_diffusion(x, y, amp=100.0):
 
 
 def gaussian_bump_helmholtz(x, y, kappa=80.0):
-    """-Lap u - kappa^2 (1 - 0.5 exp(-((x-.5)^2 + (y-.5)^2)/0.02)) u = 0, as eq. (1.2) coefficients."""
+    """-Lap u - kappa^2 (1 - 0.5 exp(-((x-.5)^2 + (y-.5)^2)/0.02)) u = 0, as eq. defA coefficients."""
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
     bump = 1.0 - 0.5 * np.exp(-((x - 0.5) ** 2 + (y - 0.5) ** 2) / 0.02)
@@ -54,14 +54,14 @@ def gaussian_bump_helmholtz(x, y, kappa=80.0):
 
 
 def constant_helmholtz(x, y, kappa):
-    """-Lap u - kappa^2 u = 0 (Section 8.1, Helmholtz I/II), eq. (1.2) signs."""
+    """-Lap u - kappa^2 u = 0 (Section 9.1, Helmholtz I/II), eq. defA signs."""
     x = np.asarray(x, np.float64)
     return {"c11": _ones_like(x), "c12": None, "c22": _ones_like(x),
             "c1": None, "c2": None, "c": -(kappa ** 2) * _ones_like(x)}
 
 
 def paper_variable_helmholtz(x, y, kappa=640.0):
-    """Section 8.2 'variable Helmholtz': eq. (8.1) c = kappa^2 (1 - (sin 4pi x sin 4pi y)^2)."""
+    """Section 9.2 'variable Helmholtz': eq. example c = kappa^2 (1 - (sin 4pi x sin 4pi y)^2)."""
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
     c81 = kappa ** 2 * (1.0 - (np.sin(4 * np.pi * x) * np.sin(4 * np.pi * y)) ** 2)
@@ -70,7 +70,7 @@ def paper_variable_helmholtz(x, y, kappa=640.0):
 
 
 def paper_diffusion_convection(x, y):
-    """Section 8.2 'diffusion-convection': eq. (8.1) c1 = -1e4 cos(4pi y), c2 = -1e4 cos(4pi x)."""
+    """Section 9.2 'diffusion-convection': eq. example c1 = -1e4 cos(4pi y), c2 = -1e4 cos(4pi x)."""
     x = np.asarray(x, np.float64)
     y = np.asarray(y, np.float64)
     c1_81 = -1.0e4 * np.cos(4 * np.pi * y)
@@ -80,7 +80,7 @@ def paper_diffusion_convection(x, y):
 
 
 def paper_constant_convection(x, y):
-    """Section 8.2 'constant convection': eq. (8.1) c2 = -1e5."""
+    """Section 9.2 'constant convection': eq. example c2 = -1e5."""
     x = np.asarray(x, np.float64)
     return {"c11": _ones_like(x), "c12": None, "c22": _ones_like(x),
             "c1": None, "c2": 1.0e5 * _ones_like(x), "c": None}
@@ -132,12 +132,12 @@ def harmonic_poly(k, part, x, y):
 
 
 def log_source(x, y, xs=-2.0, ys=0.0):
-    """log |x_hat - x| with x_hat = (-2, 0) (Section 8.1, Laplace)."""
+    """log |x_hat - x| with x_hat = (-2, 0) (Section 9.1, Laplace)."""
     return np.log(np.hypot(np.asarray(x, np.float64) - xs, np.asarray(y, np.float64) - ys))
 
 
 def paper_table3_data(x, y):
-    """f = cos(2 x1) (1 - 2 x2), the Dirichlet data of Section 8.2."""
+    """f = cos(2 x1) (1 - 2 x2), the Dirichlet data of Section 9.2."""
     return np.cos(2 * np.asarray(x, np.float64)) * (1.0 - 2 * np.asarray(y, np.float64))
 
 

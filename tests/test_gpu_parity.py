@@ -71,7 +71,7 @@ def test_laplace_ladder(nx, ny):
                                        (1, 6, 10, 8), (5, 3, 9, 8), (2, 3, 6, 3), (7, 1, 8, 8),
                                        (1, 5, 9, 9)])
 def test_variable_coefficients_uneven_trees(nx, ny, p, q):
-    """All six coefficients of eq. (1.2) on a skewed domain, trees from
+    """All six coefficients of eq. defA on a skewed domain, trees from
     non-power-of-two grids (splits at floor(n/2)), q < p, and q = p on strips
     (no interior vertex, so the system stays nonsingular)."""
     f = boundary_data(SKEW, nx, ny, q)

@@ -127,7 +127,7 @@ def _varcoef(x, y):
 
 
 def _apply_A(cf, ux, uy, uxx, uxy, uyy, u):
-    """eq. (1.2) applied to analytic derivatives (written independently of the
+    """eq. defA applied to analytic derivatives (written independently of the
     oracle's matrices: pointwise products of exact derivatives)."""
     return (-cf["c11"] * uxx - 2 * cf["c12"] * uxy - cf["c22"] * uyy
             + cf["c1"] * ux + cf["c2"] * uy + cf["c"] * u)
@@ -136,7 +136,7 @@ def _apply_A(cf, ux, uy, uxx, uxy, uyy, u):
 @pytest.mark.parametrize("nx,ny", [(1, 1), (2, 2), (3, 2)])
 @pytest.mark.parametrize("solver", ["global", "condensed"])
 def test_polynomial_solution_with_body_load(nx, ny, solver):
-    """Every coefficient term and sign of eq. (1.2) (the factor -2 on c12, +c1,
+    """Every coefficient term and sign of eq. defA (the factor -2 on c12, +c1,
     +c2, +c), the 2/hx and 2/hy scalings (hx != hy): a polynomial u of degree
     <= q-1 with body load F = A u evaluated analytically is reproduced exactly."""
     p, q = 12, 10
@@ -287,7 +287,7 @@ def test_spectral_convergence_exp_sin():
 
 
 def test_spectral_convergence_log_source():
-    """P4: u = log|x - (-2, 0)| (Section 8.1, Laplace)."""
+    """P4: u = log|x - (-2, 0)| (Section 9.1, Laplace)."""
     e = _conv_errors(I.log_source, I.laplace, [6, 8, 10, 12, 16])
     _geometric(e, 0.5)
     assert e[-1] < 1e-10
