@@ -14,6 +14,12 @@ refinement against the FP64 residual).  Workloads (--workload):
                 [8, 128]) and order (p in {12, 16, 20}, q = p - 2) with random
                 smooth coefficient fields, 16 right-hand sides each, one batched
                 build and solve
+  post          post-processing on the helmholtz256 problem built in FP64 with
+                its root DtN map T^1 (nbnd = 14336): T^1 applied to 1, 8 and 64
+                data sets (Section 9.1's T_apply) and the solution evaluated at
+                4 M random points (Section 5.3); one step = one T^1 apply to one
+                data set
+  serve         the request loop (include/hps_serve.h) on a Poisson stream
 
 Both precisions are timed; the mixed one is the headline and the FP64 one is
 reported beside it.  Inputs (coefficients and boundary data) are resident in
@@ -577,6 +583,116 @@ def run_serve(args):
     return 0
 
 
+def run_post(args):
+    """T^1 apply and point evaluation on the 256 x 256 Helmholtz problem."""
+    import torch
+    from paper_1307_2665_gb300 import hps
+    from paper_1307_2665_gb300.build import build
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank != 0:  # replicas: one GPU is measured
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    W = make_workload("helmholtz256", args.leaves, 0)
+    pr = W.probs[0]
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    co_d = {k: (None if v is None else torch.from_numpy(v).to(dev)) for k, v in pr["coeffs"].items()}
+    h = hps.hps_build(pr["domain"], pr["nx"], pr["ny"], pr["p"], pr["q"], co_d, device_ptrs=True,
+                      stream=sp, form_root_dtn=True)
+    n = hps.hps_boundary_count(pr["nx"], pr["ny"], pr["q"])
+    f_all = torch.from_numpy(np.ascontiguousarray(pr["f"])).to(dev)
+    K, Wm = max(args.steps, 1), max(args.warmup, 3)
+    clk = ClockSampler(local)
+
+    def timed(fn, reps):
+        for _ in range(Wm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    clk.start()
+    hps.hps_profile_reset()
+    hps.hps_profile_enable(True)
+    launches0 = hps.hps_kernel_launches()
+    g1 = torch.empty((1, n), dtype=torch.float64, device=dev)
+    f1 = f_all[:1].contiguous()
+    t1 = timed(lambda: hps.hps_apply_dtn(h, f1, g1, device_ptrs=True), K)
+    launches = (hps.hps_kernel_launches() - launches0) // (K + Wm)
+    stats = hps.hps_profile_read()
+    hps.hps_profile_enable(False)
+    for k in (8, 64):
+        fk = f_all[:k].contiguous()
+        gk = torch.empty((k, n), dtype=torch.float64, device=dev)
+        out[k] = timed(lambda: hps.hps_apply_dtn(h, fk, gk, device_ptrs=True), K)
+    # point evaluation of one solution at 4 M random points
+    u = torch.empty((1, pr["nx"] * pr["ny"], pr["p"], pr["p"]), dtype=torch.float64, device=dev)
+    hps.hps_solve(h, f1, u, device_ptrs=True)
+    npts = 4 * 1024 * 1024
+    rng = np.random.default_rng(3)
+    xy = torch.from_numpy(rng.random((npts, 2))).to(dev)
+    vals = torch.empty((1, npts), dtype=torch.float64, device=dev)
+    t_interp = timed(lambda: hps.hps_interpolate(h, u, xy, vals, device_ptrs=True), K)
+    clocks = clk.stop()
+    # end to end: host arrays, copies inside the call
+    f1h = np.ascontiguousarray(pr["f"][:1])
+    g1h = np.empty_like(f1h)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        hps.hps_apply_dtn(h, f1h, g1h, device_ptrs=False)
+    t_e2e = (time.perf_counter() - t0) / K * 1e3
+    h.close()
+    mv = stats.get("dtn_matvec", {"ms": 0.0, "bytes": 0.0, "launches": 1})
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    per_launch_bytes = mv["bytes"] / max(mv["launches"], 1)
+    per_launch_s = mv["ms"] / 1e3 / max(mv["launches"], 1)
+    achieved = per_launch_bytes / per_launch_s / 1e9 if per_launch_s > 0 else 0.0
+    line = {"metric": "T_apply: applications of the root DtN map T^1 per second (1 data set)",
+            "value": 1e3 / t1, "unit": "applies/s", "n_gpus": 1, "steps": K, "warmup": Wm,
+            "ms_per_step": t1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"T^1 of the helmholtz256 problem (nbnd = {n}, "
+                                   f"{8.0 * n * n / 1e9:.2f} GB in FP64) applied to 20-mode Fourier "
+                                   f"data; point evaluation at {npts} uniform random points",
+                       "l2": "inputs larger than L2 (T^1 is read from HBM every apply)"},
+            "apply_ms": {"1": t1, "8": out[8], "64": out[64]},
+            "interp_points_per_s": npts / (t_interp / 1e3), "interp_ms": t_interp,
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "dtn_matvec", "bound": "hbm", "achieved": achieved,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+            "e2e": {"value": 1e3 / t_e2e, "unit": "applies/s", "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "clocks": clocks, "kernels": stats}
+    if not args.no_cpu_baseline:  # the oracle's T^1 f: global sparse solve + boundary fluxes
+        from oracle import hps_oracle as O
+        from paper_1307_2665_gb300 import inputs as I
+        ns = 16
+        prob = O.make_problem(UNIT_SQ, ns, ns, 16, 14, I.gaussian_bump_helmholtz)
+        xyb = O.boundary_points(prob)
+        fs = I.fourier_boundary(0, xyb[:, 0], xyb[:, 1], UNIT_SQ)[None, :]
+        t0 = time.perf_counter()
+        O.dtn_apply(prob, fs)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "applies/s", "cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"one T^1 f by the FP64 oracle (sparse LU of the global "
+                                          f"system + boundary fluxes) on {ns}x{ns} leaves, p=16, "
+                                          f"q=14, not the full 256x256 problem"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,7 +700,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="convdiff64",
-                    choices=["convdiff64", "helmholtz256", "batch64", "serve"])
+                    choices=["convdiff64", "helmholtz256", "batch64", "serve", "post"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")
     ap.add_argument("--workers", type=int, default=4, help="serve: concurrent device jobs")
@@ -602,6 +718,8 @@ def main():
         return run_reference(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "post":
+        return run_post(args)
     return run_native(args)
 
 

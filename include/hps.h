@@ -5,7 +5,7 @@
  * complexity for variable coefficient elliptic PDEs discretized via a
  * high-order composite spectral collocation method" (arXiv:1307.2665).
  *
- * Problem (Section 1.1, eq. 1.1-1.2): on Omega = [x0,x1] x [y0,y1],
+ * Problem (Section 1.1, eqs. basic and defA): on Omega = [x0,x1] x [y0,y1],
  *     A u = 0 in Omega,  u = f on the boundary Gamma, with
  *     A u = -c11 u_xx - 2 c12 u_xy - c22 u_yy + c1 u_x + c2 u_y + c u.
  *
@@ -185,6 +185,33 @@ int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_
  * output pointer may be NULL.  The serving loop admits work by these. */
 int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* opt, int nrhs,
                        int64_t* build_peak, int64_t* resident, int64_t* solve);
+
+/* Apply the DtN map of the whole domain (the root map T^1 of Algorithm 1;
+ * Section 9.1 times this as T_apply, Table 1): g = T^1 f for nrhs Dirichlet
+ * data sets f (nrhs * nbnd, the layout and Gamma order of hps_solve).  g has
+ * the same layout: at each Gamma node, the derivative of the solution in the
+ * global direction (d/dx on the west and east sides, d/dy on the south and
+ * north sides; the fluxes v of Section 2), not the outward normal derivative.
+ * Needs a single-problem handle built with form_root_dtn = 1, which keeps T^1
+ * (nbnd^2 doubles) on the device; T^1 is applied as the build formed it
+ * (mixed mode: from the FP32 maps of the lower levels, without refinement).
+ * f and g: host arrays (device_ptrs 0, copied inside the call) or device
+ * arrays (1).  HPS_EINVAL: NULL pointer, nrhs < 1, a batch handle or a handle
+ * without T^1. */
+int hps_apply_dtn(hps_handle h, const double* f, int nrhs, double* g, int device_ptrs);
+
+/* Evaluate solutions at arbitrary points (Section 5.3): inside a leaf the
+ * solution is the tensor-product polynomial interpolant of its p x p
+ * Chebyshev values.  u: nrhs solutions in the layout of hps_solve's output;
+ * xy: npts (x, y) pairs; out[r * npts + i] = u_r(x_i, y_i).  A point on an
+ * edge shared by two leaves takes the leaf to its east (north); a point on the
+ * domain's east (north) side takes the last leaf.  Points must lie in the
+ * closed domain: with host arrays (device_ptrs 0) any other point makes the
+ * call return HPS_EINVAL before device work; with device arrays (1) its outputs
+ * are NaN and the call returns HPS_EINVAL.  npts = 0 is a no-op.  Needs a
+ * single-problem handle (its grid is all that is used). */
+int hps_interpolate(hps_handle h, const double* u, int nrhs, const double* xy, int64_t npts,
+                    double* out, int device_ptrs);
 
 /* C = alpha A B + beta C for FP64 device matrices (column-major, leading
  * dimensions lda >= M, ldb >= K, ldc >= M) through the tensor-core engine the

@@ -14,7 +14,7 @@ oracle writes that system out and solves it by sparse LU:
   unknowns  u at the Gauss nodes of every interior leaf edge (Section 2) and
             w at the (p-2)^2 interior Chebyshev nodes of every leaf (Section 3.1);
   (E1)      per leaf and per interior Chebyshev node, the collocation equation
-            (A w_full)_i = F_i  (Section 3.1, eq. A_interior; F = 0 for eq. 1.1),
+            (A w_full)_i = F_i  (Section 3.1, eq. A_interior; F = 0 for eq. basic),
             where the boundary nodes of w_full carry L1 u_e: the per-side
             degree (q-1) Gauss interpolant evaluated at the side's Chebyshev
             points, corners averaged (Section 3.2, Step 1);
@@ -106,7 +106,7 @@ def interp_matrix(src, dst):
 # ================================================================= geometry
 @dataclass
 class Problem:
-    """A Dirichlet problem (eq. 1.1) on the rectangle domain = (x0, x1, y0, y1),
+    """A Dirichlet problem (eq. basic) on the rectangle domain = (x0, x1, y0, y1),
     split into nx-by-ny leaves, p Chebyshev points per leaf side, q Gauss points
     per leaf edge.  coeffs[name] is None (absent, i.e. zero) or an array of shape
     (ny*nx, p, p) sampled at cheb_grid(); leaf l = iy*nx + ix, local [a, b] with a
@@ -668,6 +668,82 @@ def flux_at_cheb(prob: Problem, w, l, side):
             1: [a * p + p - 1 for a in range(p)], 3: [a * p for a in range(p)]}[side]
     M = ops.Dy if side in (0, 2) else ops.Dx
     return M[rows] @ full
+
+
+# ============================================================ post-processing
+def boundary_flux(prob: Problem, w):
+    """The DtN map of the whole domain applied to the Dirichlet data of the
+    solutions w (nrhs, n_leaves, p, p): at every Gamma Gauss node, in the order
+    of f, the flux of Section 2 (d/dx on vertical sides, d/dy on horizontal
+    sides, global direction), computed from the boundary leaf as L4 L3 w_full
+    (Section 3.2, Steps 3-4; the map F of LeafOps).  This is T^1 f for the data
+    f of the solve (Algorithm 1's root map), without forming T^1.
+    Returns (nrhs, nbnd)."""
+    w = np.asarray(w, np.float64)
+    if w.ndim == 3:
+        w = w[None]
+    en = EdgeNumbering(prob)
+    ops = LeafOps(prob.p, prob.q, prob.hx, prob.hy)
+    q, nx, ny = prob.q, prob.nx, prob.ny
+    G = np.zeros((en.N, w.shape[0]))
+    for iy in range(ny):
+        for ix in range(nx):
+            if 0 < ix < nx - 1 and 0 < iy < ny - 1:
+                continue
+            fl = ops.F @ w[:, iy * nx + ix].reshape(w.shape[0], -1).T  # (4q, nrhs): S, E, N, W
+            if iy == 0:
+                G[en.h(0, ix)] = fl[0:q]
+            if ix == nx - 1:
+                G[en.v(nx, iy)] = fl[q:2 * q]
+            if iy == ny - 1:
+                G[en.h(ny, ix)] = fl[2 * q:3 * q]
+            if ix == 0:
+                G[en.v(0, iy)] = fl[3 * q:4 * q]
+    return G[en.gamma_order()].T
+
+
+def dtn_apply(prob: Problem, f):
+    """T^1 f for Dirichlet data f (nrhs, nbnd): the boundary fluxes of the
+    global system's solution (sparse LU, solve_global)."""
+    f = np.atleast_2d(np.asarray(f, np.float64))
+    sol, _, _ = solve_global(prob, f.T)
+    return boundary_flux(prob, sol.w)
+
+
+def lagrange_basis(nodes, t):
+    """Values at t of the Lagrange polynomials of the nodes, in product form:
+    l_j(t) = prod_{k != j} (t - t_k) / (t_j - t_k)."""
+    nodes = np.asarray(nodes, np.float64)
+    out = np.ones(len(nodes))
+    for j in range(len(nodes)):
+        for k in range(len(nodes)):
+            if k != j:
+                out[j] *= (t - nodes[k]) / (nodes[j] - nodes[k])
+    return out
+
+
+def evaluate_points(prob: Problem, w, xy):
+    """Section 5.3: the solutions w (nrhs, n_leaves, p, p) at points xy (npts, 2)
+    by the tensor-product interpolant of the containing leaf's Chebyshev values.
+    A point on an edge shared by two leaves takes the leaf to its east (north);
+    one on the domain's east (north) side the last leaf.  Returns (nrhs, npts)."""
+    w = np.asarray(w, np.float64)
+    if w.ndim == 3:
+        w = w[None]
+    x0, x1, y0, y1 = prob.domain
+    t = cheb_points(prob.p)
+    out = np.empty((w.shape[0], len(xy)))
+    for i, (x, y) in enumerate(np.asarray(xy, np.float64)):
+        if not (x0 <= x <= x1 and y0 <= y <= y1):
+            raise ValueError("point outside the domain")
+        sx = (x - x0) / (x1 - x0) * prob.nx
+        sy = (y - y0) / (y1 - y0) * prob.ny
+        ix = min(int(np.floor(sx)), prob.nx - 1)
+        iy = min(int(np.floor(sy)), prob.ny - 1)
+        bx = lagrange_basis(t, 2.0 * (sx - ix) - 1.0)
+        by = lagrange_basis(t, 2.0 * (sy - iy) - 1.0)
+        out[:, i] = np.einsum("a,rab,b->r", by, w[:, iy * prob.nx + ix], bx)
+    return out
 
 
 # ================================================================ counting

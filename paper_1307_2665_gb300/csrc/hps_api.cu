@@ -217,6 +217,8 @@ struct hps_handle_s {
   std::vector<LeafGroup> lg;
   std::vector<LevelGroup> lev;      // in increasing height
   PoolBuf maps, root_from_f, leaf_off, hsc, status, coef;
+  PoolBuf root_dtn;                 // form_root_dtn: each problem's T^1 in FP64
+  std::vector<int64_t> root_dtn_off;
   std::vector<int64_t> src_off, cma_off, cmb_off, u3_off;
   int64_t u3_total = 0;
   Stager keep;                      // descriptors that live as long as the handle
@@ -744,6 +746,27 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
     }
     L.scatter = H.keep.push(sd, st);
     L.body = H.keep.push(bd, st);
+  }
+  // form_root_dtn, single-problem handles (the only ones hps_apply_dtn takes;
+  // in a batch a one-leaf problem's T may share a buffer released above): keep
+  // the root DtN, in FP64
+  if (H.opt.form_root_dtn && H.nprob == 1) {
+    int64_t tot = 0;
+    H.root_dtn_off.assign(H.nprob, 0);
+    for (int k = 0; k < H.nprob; ++k) {
+      H.root_dtn_off[k] = tot;
+      tot += (int64_t)pl.probs[k].nbnd * pl.probs[k].nbnd;
+    }
+    H.root_dtn.alloc((size_t)tot * sizeof(double), st);
+    for (int k = 0; k < H.nprob; ++k) {
+      const TRef& t = Tref[pl.probs[k].root];
+      const int64_t n2 = (int64_t)pl.probs[k].nbnd * pl.probs[k].nbnd;
+      double* dst = H.root_dtn.as<double>() + H.root_dtn_off[k];
+      if (t.f64)
+        ck(cudaMemcpyAsync(dst, t.p, (size_t)n2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      else
+        f32_to_f64(static_cast<const float*>(t.p), dst, n2, st);
+    }
   }
   if (!H.mixed) H.coef.release();  // only the residual of mixed mode reads it later
   int* bad_h = nullptr;
@@ -1483,6 +1506,104 @@ int hps_solve_batch(hps_handle h, const double* const* f, int nrhs, double* cons
   return solve_guarded(h, f, nrhs, u, h->opt.device_ptrs, info);
 }
 
+int hps_apply_dtn(hps_handle h, const double* f, int nrhs, double* g, int device_ptrs) {
+  if (!h || !f || !g || nrhs < 1 || h->nprob != 1 || !h->opt.form_root_dtn || !h->root_dtn.p)
+    return HPS_EINVAL;
+  g_last_error.clear();
+  try {
+    hps_handle_s& H = *h;
+    cudaStream_t st = H.stream;
+    const int n = H.plan.probs[0].nbnd;
+    const size_t nb = (size_t)n * nrhs * sizeof(double);
+    const size_t wb = dtn_apply_ws_bytes(n, nrhs);
+    PoolBuf ws, io, stt;
+    ws.alloc(wb, st);
+    stt.alloc(sizeof(int), st);
+    ck(cudaMemsetAsync(stt.p, 0, sizeof(int), st));
+    const double* fd = f;
+    double* gd = g;
+    if (!device_ptrs) {
+      io.alloc(2 * nb, st);
+      fd = io.as<double>();
+      gd = io.as<double>() + (size_t)n * nrhs;
+      ck(cudaMemcpyAsync(const_cast<double*>(fd), f, nb, cudaMemcpyHostToDevice, st));
+    }
+    ck(dtn_apply(H.root_dtn.as<double>(), n, H.root_from_f.as<int>() + H.plan.probs[0].rff_off,
+                 fd, nrhs, gd, ws.p, wb, stt.as<int>(), st));
+    if (!device_ptrs) ck(cudaMemcpyAsync(g, gd, nb, cudaMemcpyDeviceToHost, st));
+    int hst = 0;
+    ck(cudaMemcpyAsync(&hst, stt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    if (hst != 0) {
+      g_last_error = "tensor-core GEMM: a wait gave up";
+      return HPS_EDEVICE;
+    }
+    return HPS_OK;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  } catch (std::bad_alloc&) {
+    return HPS_ENOMEM;
+  } catch (...) {
+    return HPS_EDEVICE;
+  }
+}
+
+int hps_interpolate(hps_handle h, const double* u, int nrhs, const double* xy, int64_t npts,
+                    double* out, int device_ptrs) {
+  if (!h || nrhs < 1 || npts < 0 || h->nprob != 1) return HPS_EINVAL;
+  if (npts == 0) return HPS_OK;
+  if (!u || !xy || !out) return HPS_EINVAL;
+  const ProblemSpec& ps = h->plan.probs[0].s;
+  if (!device_ptrs)
+    for (int64_t i = 0; i < npts; ++i) {
+      const double x = xy[2 * i], y = xy[2 * i + 1];
+      if (!(x >= ps.x0 && x <= ps.x1 && y >= ps.y0 && y <= ps.y1)) return HPS_EINVAL;
+    }
+  g_last_error.clear();
+  try {
+    cudaStream_t st = h->stream;
+    InterpGrid gr;
+    gr.x0 = ps.x0;
+    gr.x1 = ps.x1;
+    gr.y0 = ps.y0;
+    gr.y1 = ps.y1;
+    gr.nx = ps.nx;
+    gr.ny = ps.ny;
+    gr.p = ps.p;
+    const size_t ub = (size_t)nrhs * ps.nx * ps.ny * ps.p * ps.p * sizeof(double);
+    const size_t xb = (size_t)npts * 2 * sizeof(double), ob = (size_t)npts * nrhs * sizeof(double);
+    PoolBuf io, stt;
+    stt.alloc(sizeof(int), st);
+    ck(cudaMemsetAsync(stt.p, 0, sizeof(int), st));
+    const double *ud = u, *xd = xy;
+    double* od = out;
+    if (!device_ptrs) {
+      io.alloc(ub + xb + ob, st);
+      char* b = static_cast<char*>(io.p);
+      ud = reinterpret_cast<const double*>(b);
+      xd = reinterpret_cast<const double*>(b + ub);
+      od = reinterpret_cast<double*>(b + ub + xb);
+      ck(cudaMemcpyAsync(const_cast<double*>(ud), u, ub, cudaMemcpyHostToDevice, st));
+      ck(cudaMemcpyAsync(const_cast<double*>(xd), xy, xb, cudaMemcpyHostToDevice, st));
+    }
+    interp_points(ud, nrhs, gr, xd, npts, od, stt.as<int>(), st);
+    ck(cudaGetLastError());
+    if (!device_ptrs) ck(cudaMemcpyAsync(out, od, ob, cudaMemcpyDeviceToHost, st));
+    int hst = 0;
+    ck(cudaMemcpyAsync(&hst, stt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    return hst ? HPS_EINVAL : HPS_OK;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  } catch (std::bad_alloc&) {
+    return HPS_ENOMEM;
+  } catch (...) {
+    return HPS_EDEVICE;
+  }
+}
+
 int hps_dgemm_tc(int M, int N, int K, double alpha, const double* A, int lda, const double* B,
                  int ldb, double beta, double* C, int ldc) {
   if (M < 1 || N < 1 || K < 1 || lda < M || ldb < K || ldc < M || !A || !B || !C)
@@ -1591,10 +1712,12 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
       }
       max_level_rows = std::max(max_level_rows, rows);
     }
-    const int64_t res = y + sres + (mixed ? coef_bytes : 0);
+    int64_t root_dtn = 0;  // form_root_dtn: the kept T^1 of every problem
+    if (opt.form_root_dtn && nprob == 1) root_dtn = (int64_t)pl.probs[0].nbnd * pl.probs[0].nbnd * 8;
+    const int64_t res = y + sres + (mixed ? coef_bytes : 0) + root_dtn;
     int64_t peak = leaf_tmp;
     for (int h = 1; h <= pl.height; ++h) peak = std::max(peak, t_at[h - 1] + t_at[h] + tmp_at[h]);
-    peak += y + sres + coef_bytes;
+    peak += y + sres + coef_bytes + root_dtn;
     int64_t work = (int64_t)nrhs * (pl.ext_total + u3_rows) * 8 + 2 * (int64_t)nrhs * max_level_rows * 8;
     if (mixed && opt.max_refine > 0) {
       const int64_t m = std::max(0, opt.refine_depth);
@@ -1640,7 +1763,8 @@ int hps_query(hps_handle h, int* n_leaves, int* p, int* q, int64_t* nbnd, int64_
   if (device_bytes) {
     int64_t b = 0;
     for (const PoolBuf* x : {&h->coef, &h->maps, &h->uext, &h->u3, &h->hpool, &h->fstage,
-                             &h->ustage, &h->split_ws, &h->keep.dev, &h->solve_st.dev})
+                             &h->ustage, &h->split_ws, &h->keep.dev, &h->solve_st.dev,
+                             &h->root_dtn})
       b += (int64_t)x->bytes;
     for (const auto& G : h->lg) b += (int64_t)(G.Y->bytes + G.rleaf->bytes + G.zleaf->bytes);
     for (const auto& L : h->lev)

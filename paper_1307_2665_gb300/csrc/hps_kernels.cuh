@@ -196,6 +196,25 @@ inline bool oz_eligible(int M, int N, int K) {
   return M >= 128 && N >= 128 && K >= 64 && (double)M * N * K >= 8.0e6;
 }
 
+// ---- post-processing (hps_post.cu)
+// g = T f for a root DtN T (n x n, column-major, FP64) with f and g in Gamma
+// order (nrhs columns of n) and rff[k] the Gamma index of root exterior
+// position k; ws holds dtn_apply_ws_bytes(n, nrhs) bytes.  A wait of the
+// tensor-core path that gives up sets *status to -1.
+size_t dtn_apply_ws_bytes(int n, int nrhs);
+cudaError_t dtn_apply(const double* T, int n, const int* rff, const double* f, int nrhs,
+                      double* g, void* ws, size_t ws_bytes, int* status, cudaStream_t st);
+void f32_to_f64(const float* s, double* d, int64_t n, cudaStream_t st);
+// The leaf grid of one problem, for point evaluation.
+struct InterpGrid {
+  double x0, x1, y0, y1;
+  int nx, ny, p;
+};
+// out[r * npts + i] = u_r(xy_i) from the leaf Chebyshev values u (nrhs blocks
+// of nx*ny*p*p); points outside the closed domain give NaN and set *status to 1.
+void interp_points(const double* u, int nrhs, const InterpGrid& s, const double* xy,
+                   int64_t npts, double* out, int* status, cudaStream_t st);
+
 // ---- accelerated refinement (hps_refine.cu)
 constexpr int kAaMaxDepth = 8;               // longest Anderson history
 constexpr int kAaChunk = 8192;               // elements per reduction chunk

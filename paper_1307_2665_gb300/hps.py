@@ -32,7 +32,8 @@ EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_solve_ex", "hps_query", "hps_free", "hps_status_string", "hps_kernel_launches",
            "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error",
            "hps_solve_static", "hps_build_batch", "hps_solve_batch", "hps_batch_size",
-           "hps_estimate_bytes", "hps_release_workspace", "hps_dgemm_tc",
+           "hps_estimate_bytes", "hps_release_workspace", "hps_dgemm_tc", "hps_apply_dtn",
+           "hps_interpolate",
            # include/hps_serve.h
            "hps_server_default_options", "hps_server_create", "hps_server_destroy",
            "hps_server_submit_build", "hps_server_submit_solve", "hps_server_wait",
@@ -149,6 +150,10 @@ def lib():
     L.hps_dgemm_tc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp,
                                ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int]
     L.hps_dgemm_tc.restype = ctypes.c_int
+    L.hps_apply_dtn.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int]
+    L.hps_apply_dtn.restype = ctypes.c_int
+    L.hps_interpolate.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int64, vp, ctypes.c_int]
+    L.hps_interpolate.restype = ctypes.c_int
     L.hps_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
     L.hps_server_default_options.restype = None
     L.hps_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
@@ -355,6 +360,38 @@ def hps_solve(h: Handle, f, u=None, device_ptrs=None, info=None, check=True):
     if st != HPS_OK and check:
         raise HpsError(st, "hps_solve")
     return u
+
+
+def hps_apply_dtn(h: Handle, f, g=None, device_ptrs=None, check=True):
+    """g = T^1 f (the root DtN of a handle built with form_root_dtn=True).
+    f: (nrhs, nbnd) or (nbnd,) float64; g: same shape (allocated on the host
+    when omitted and f is on the host)."""
+    dev = h.device_ptrs if device_ptrs is None else bool(device_ptrs)
+    nrhs = 1 if f.ndim == 1 else f.shape[0]
+    if g is None:
+        if dev:
+            raise ValueError("device applies need a preallocated g")
+        g = np.empty(f.shape)
+    st = lib().hps_apply_dtn(h.ptr, _ptr(f), nrhs, _ptr(g), 1 if dev else 0)
+    if st != HPS_OK and check:
+        raise HpsError(st, "hps_apply_dtn")
+    return g if check else (g, st)
+
+
+def hps_interpolate(h: Handle, u, xy, out=None, device_ptrs=None, check=True):
+    """Solutions u (nrhs, nx*ny, p, p) evaluated at points xy (npts, 2):
+    returns out (nrhs, npts)."""
+    dev = h.device_ptrs if device_ptrs is None else bool(device_ptrs)
+    nrhs = u.shape[0]
+    npts = xy.shape[0]
+    if out is None:
+        if dev:
+            raise ValueError("device evaluations need a preallocated out")
+        out = np.empty((nrhs, npts))
+    st = lib().hps_interpolate(h.ptr, _ptr(u), nrhs, _ptr(xy), npts, _ptr(out), 1 if dev else 0)
+    if st != HPS_OK and check:
+        raise HpsError(st, "hps_interpolate")
+    return out if check else (out, st)
 
 
 def hps_solve_static(h: Handle, f, u, check=True):

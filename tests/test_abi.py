@@ -82,6 +82,8 @@ def test_null_pointer_arguments():
     assert L.hps_free(None) == hps.HPS_OK
     assert L.hps_solve(None, None, 1, None, None) == hps.HPS_EINVAL
     assert L.hps_cheb_nodes(hps.Domain(0, 1, 0, 1), 2, 2, 8, None) == hps.HPS_EINVAL
+    assert L.hps_apply_dtn(None, None, 1, None, 0) == hps.HPS_EINVAL
+    assert L.hps_interpolate(None, None, 1, None, 5, None, 0) == hps.HPS_EINVAL
 
 
 def test_estimate_bytes_host_only():

@@ -437,3 +437,100 @@ def test_sampled_residual_zero_at_solution_and_matches_residual():
     bad[0, 0, 4, 9] += 1e-3  # east side of leaf 0, non-corner point
     assert O.sampled_residual(prob, bad, f, [0])["cont"] > 1e-5
     assert O.sampled_residual(prob, sol.w, f + 1e-3, [0])["gamma"] > 1e-5
+
+
+# ---------------------------------------------------------------- post-processing
+def _gamma_sides(prob):
+    """Side of every Gamma node in the order of f: 0 S, 1 E, 2 N, 3 W."""
+    q = prob.q
+    return np.concatenate([np.full(prob.nx * q, 0), np.full(prob.ny * q, 1),
+                           np.full(prob.nx * q, 2), np.full(prob.ny * q, 3)])
+
+
+def _exact_flux(prob, ux, uy):
+    """The fluxes of Section 2 from the exact gradient: d/dy on S and N, d/dx on E and W."""
+    xy = O.boundary_points(prob)
+    side = _gamma_sides(prob)
+    gx, gy = ux(xy[:, 0], xy[:, 1]), uy(xy[:, 0], xy[:, 1])
+    return np.where((side == 0) | (side == 2), gy, gx)
+
+
+def test_boundary_flux_of_a_linear_solution_is_exact():
+    """u = 2x - 3y + 1 solves Laplace's equation and lies in the discrete space:
+    T^1 f is (2 on vertical sides, -3 on horizontal sides) up to rounding."""
+    prob = O.make_problem(SKEW, 3, 2, 10, 8, I.laplace)
+    xy = O.boundary_points(prob)
+    f = 2 * xy[:, 0] - 3 * xy[:, 1] + 1
+    g = O.dtn_apply(prob, f[None, :])[0]
+    want = _exact_flux(prob, lambda x, y: np.full_like(x, 2.0), lambda x, y: np.full_like(x, -3.0))
+    assert np.max(np.abs(g - want)) < 1e-11
+
+
+def test_dtn_annihilates_constants():
+    """Constant Dirichlet data: the Laplace solution is that constant and every flux vanishes."""
+    prob = O.make_problem(UNIT, 2, 2, 12, 10, I.laplace)
+    g = O.dtn_apply(prob, np.full((1, 4 * 2 * 10), 3.5))
+    assert np.max(np.abs(g)) < 1e-11
+
+
+@pytest.mark.parametrize("case", ["exp_sin", "plane_wave"])
+def test_boundary_flux_matches_exact_gradient(case):
+    """Smooth exact solutions: T^1 f converges spectrally to the exact fluxes.
+    exp(x) sin(y) solves Laplace; cos(3x + 4y) solves -Lap u - 25 u = 0 (c = -25)."""
+    if case == "exp_sin":
+        coef = I.laplace
+        u = lambda x, y: np.exp(x) * np.sin(y)
+        ux = lambda x, y: np.exp(x) * np.sin(y)
+        uy = lambda x, y: np.exp(x) * np.cos(y)
+        dom, tol = SKEW, 1e-10
+    else:
+        def coef(x, y):
+            return {"c11": np.ones_like(x), "c22": np.ones_like(x), "c": np.full_like(x, -25.0)}
+        u = lambda x, y: np.cos(3 * x + 4 * y)
+        ux = lambda x, y: -3 * np.sin(3 * x + 4 * y)
+        uy = lambda x, y: -4 * np.sin(3 * x + 4 * y)
+        dom, tol = UNIT, 1e-9
+    prob = O.make_problem(dom, 2, 3, 16, 14, coef)
+    xy = O.boundary_points(prob)
+    g = O.dtn_apply(prob, u(xy[:, 0], xy[:, 1])[None, :])[0]
+    want = _exact_flux(prob, ux, uy)
+    assert np.max(np.abs(g - want)) / np.max(np.abs(want)) < tol
+
+
+def _poly(x, y):
+    return x ** 5 * y ** 3 - 2 * x ** 2 * y + 0.5 * y ** 7 + 1.25
+
+
+def test_point_evaluation_reproduces_polynomials():
+    """A polynomial of degree < p in each variable is its own interpolant: its
+    Chebyshev samples evaluate to it anywhere, including leaf edges, leaf
+    corners and the domain's corners (Section 5.3)."""
+    prob = O.make_problem(SKEW, 3, 2, 9, 7, I.laplace)
+    grid = O.cheb_grid(prob.domain, prob.nx, prob.ny, prob.p)
+    w = _poly(grid[..., 0], grid[..., 1])[None]
+    x0, x1, y0, y1 = prob.domain
+    rng = np.random.default_rng(5)
+    pts = np.column_stack([rng.uniform(x0, x1, 40), rng.uniform(y0, y1, 40)])
+    hx, hy = prob.hx, prob.hy
+    special = np.array([[x0, y0], [x1, y1], [x0, y1], [x1, y0], [x0 + hx, y0 + hy],
+                        [x0 + 2 * hx, 0.5 * (y0 + y1)], [0.5 * (x0 + x1), y0 + hy]])
+    pts = np.vstack([pts, special])
+    out = O.evaluate_points(prob, w, pts)[0]
+    want = _poly(pts[:, 0], pts[:, 1])
+    assert np.max(np.abs(out - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_lagrange_basis_is_cardinal_and_sums_to_one():
+    t = O.cheb_points(11)
+    for j, tj in enumerate(t):
+        b = O.lagrange_basis(t, tj)
+        assert b[j] == 1.0 and np.count_nonzero(b) == 1
+    b = O.lagrange_basis(t, 0.3141)
+    assert abs(b.sum() - 1.0) < 1e-14
+
+
+def test_point_evaluation_rejects_outside_points():
+    prob = O.make_problem(UNIT, 2, 2, 6, 4, I.laplace)
+    w = np.zeros((1, 4, 6, 6))
+    with pytest.raises(ValueError):
+        O.evaluate_points(prob, w, np.array([[1.0 + 1e-9, 0.5]]))
