@@ -245,17 +245,21 @@ def alu_peak_tflops(name, sm_mhz):
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the same kernel's launch in the same workload step; a kernel
 # changed since its capture has no entry.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # first refinement launch of the 64x64 convection-diffusion step, 16 RHS
+    # (profiles/leaf_residual_convdiff64.md): 163.7 MB read + 32.3 MB written
+    ("convdiff64", "leaf_residual<f64>"): 196012032,
+}
 
 
-def roofline_of(stats, t_total_ms, sm_mhz):
+def roofline_of(stats, t_total_ms, sm_mhz, workload=None):
     name, st = max(stats.items(), key=lambda kv: kv[1]["ms"])
     peak, per = alu_peak_tflops(name, sm_mhz)
     per_launch_flops = st["flops"] / max(st["launches"], 1)
     per_launch_s = st["ms"] / 1e3 / max(st["launches"], 1)
     achieved = per_launch_flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(name),
+            "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get((workload, name)),
             "peak_source": f"{'FP64 DFMA' if per == FP64_DFMA_PER_SM_CLK else 'FP32 FFMA'}: "
                            f"{N_SM} SMs x {per}/clk x 2 flop x {sm_mhz:.0f} MHz (max SM clock; "
                            f"per-clock rate measured by an FMA probe on this pool)",
@@ -433,7 +437,7 @@ def run_native(args):
                 "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                                 "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] > 0 else 0.0}
                             for k, v in sorted(r["stats"].items(), key=lambda kv: -kv[1]["ms"])},
-                "roofline": roofline_of(r["stats"], tt, sm_max)}
+                "roofline": roofline_of(r["stats"], tt, sm_max, None if args.leaves else args.workload)}
 
     summ = {k: summary(v) for k, v in results.items()}
     H = summ[head]
@@ -642,6 +646,12 @@ def run_post(args):
     xy = torch.from_numpy(rng.random((npts, 2))).to(dev)
     vals = torch.empty((1, npts), dtype=torch.float64, device=dev)
     t_interp = timed(lambda: hps.hps_interpolate(h, u, xy, vals, device_ptrs=True), K)
+    # the same number of points on a regular 2048 x 2048 grid (neighbouring
+    # threads share leaves)
+    g1d = (np.arange(2048) + 0.5) / 2048
+    gx, gy = np.meshgrid(g1d, g1d)
+    xyg = torch.from_numpy(np.ascontiguousarray(np.column_stack([gx.ravel(), gy.ravel()]))).to(dev)
+    t_interp_grid = timed(lambda: hps.hps_interpolate(h, u, xyg, vals, device_ptrs=True), K)
     clocks = clk.stop()
     # end to end: host arrays, copies inside the call
     f1h = np.ascontiguousarray(pr["f"][:1])
@@ -662,10 +672,12 @@ def run_post(args):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"T^1 of the helmholtz256 problem (nbnd = {n}, "
                                    f"{8.0 * n * n / 1e9:.2f} GB in FP64) applied to 20-mode Fourier "
-                                   f"data; point evaluation at {npts} uniform random points",
+                                   f"data; point evaluation at {npts} uniform random points "
+                                   f"and at a regular 2048x2048 grid",
                        "l2": "inputs larger than L2 (T^1 is read from HBM every apply)"},
             "apply_ms": {"1": t1, "8": out[8], "64": out[64]},
             "interp_points_per_s": npts / (t_interp / 1e3), "interp_ms": t_interp,
+            "interp_grid_points_per_s": npts / (t_interp_grid / 1e3),
             "gpu_launches": int(launches),
             "roofline": {"kernel": "dtn_matvec", "bound": "hbm", "achieved": achieved,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",

@@ -7,7 +7,7 @@ shares no code with the CUDA path: its constants, node orderings, assembly and
 solvers are written independently, with NumPy/SciPy as plain library primitives.
 
 What it computes.  The merges of Section 4 are exact in exact arithmetic (the
-remark after Algorithm 2): the hierarchical solver reaches, up to rounding, the
+Remark 5.1): the hierarchical solver reaches, up to rounding, the
 solution of ONE linear system, the global composite collocation system.  The
 oracle writes that system out and solves it by sparse LU:
 

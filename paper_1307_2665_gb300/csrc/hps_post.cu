@@ -7,12 +7,14 @@
 // on vertical sides, d/dy on horizontal sides, in the global direction); it is
 // kept column-major in the root's exterior order, and rff[k] names the Gamma
 // index of exterior position k.  g = T f is therefore a gather of f into the
-// exterior order, a dense product, and a scatter back.  For few right-hand
-// sides the product is HBM-bound (T is read once per group of 8 right-hand
-// sides): one thread per row, the columns split into fixed chunks of
-// kDtnChunk whose partial sums are added in chunk order, so the result of a
-// right-hand side does not depend on the others.  Many right-hand sides take
-// the tensor-core FP64 GEMM.
+// exterior order, a dense product, and a scatter back.  One right-hand side
+// is HBM-bound (T read once, one FMA per element); from two on the FP64 FMAs
+// bound the product, so 16 or more right-hand sides take the tensor-core FP64
+// GEMM.  Fewer run as matvec passes of NR = 8, 4, 2, 1 right-hand sides
+// (NR a template parameter: predicated-off FMAs would still occupy the FP64
+// pipe): one thread per row, the columns split into fixed chunks of kDtnChunk
+// whose partial sums are added in chunk order, so the result of a right-hand
+// side does not depend on the others.
 //
 // Point evaluation.  Inside a leaf the solution is the tensor-product
 // polynomial interpolant of its p x p Chebyshev values; it is evaluated with
@@ -31,9 +33,11 @@ namespace hps {
 
 namespace {
 
-constexpr int kDtnChunk = 512;  // columns per partial sum
+constexpr int kDtnChunk = 128;  // columns per partial sum
 constexpr int kDtnRows = 256;   // rows (threads) per CTA
-constexpr int kDtnGroup = 8;    // right-hand sides per pass over T
+constexpr int kDtnTcMin = 16;   // right-hand sides from which the tensor cores take the product
+
+bool dtn_use_tc(int n, int nrhs) { return n >= 128 && nrhs >= kDtnTcMin; }
 
 __global__ void k_dtn_gather(const double* __restrict__ f, const int* __restrict__ rff, int n,
                              int nrhs, double* __restrict__ fr) {
@@ -45,35 +49,44 @@ __global__ void k_dtn_gather(const double* __restrict__ f, const int* __restrict
 }
 
 // part[(kc * nrhs + r) * n + i] = sum over the chunk's columns l of T[i, l] fr[r, l],
-// for the right-hand sides r0 .. r0 + nr - 1 of this pass
+// for the right-hand sides r0 .. r0 + NR - 1 of this pass.  Eight column loads
+// of a thread are issued before their FMAs.
+template <int NR>
 __global__ void __launch_bounds__(kDtnRows) k_dtn_matvec(const double* __restrict__ T, int n,
                                                          const double* __restrict__ fr, int nrhs,
-                                                         int r0, int nr,
-                                                         double* __restrict__ part) {
-  __shared__ double xs[kDtnGroup][kDtnChunk];
+                                                         int r0, double* __restrict__ part) {
+  __shared__ double xs[NR][kDtnChunk];
   const int kc = blockIdx.y;
   const int c0 = kc * kDtnChunk, c1 = min(n, c0 + kDtnChunk);
-  for (int e = threadIdx.x; e < kDtnGroup * kDtnChunk; e += blockDim.x) {
+  for (int e = threadIdx.x; e < NR * kDtnChunk; e += blockDim.x) {
     const int r = e / kDtnChunk, l = e % kDtnChunk;
-    xs[r][l] = (r < nr && c0 + l < c1) ? fr[(int64_t)(r0 + r) * n + c0 + l] : 0.0;
+    xs[r][l] = (c0 + l < c1) ? fr[(int64_t)(r0 + r) * n + c0 + l] : 0.0;
   }
   __syncthreads();
   const int i = blockIdx.x * kDtnRows + threadIdx.x;
   if (i >= n) return;
-  double acc[kDtnGroup];
+  double acc[NR];
 #pragma unroll
-  for (int r = 0; r < kDtnGroup; ++r) acc[r] = 0.0;
+  for (int r = 0; r < NR; ++r) acc[r] = 0.0;
   const double* col = T + i + (size_t)c0 * n;
-#pragma unroll 4
-  for (int l = 0; l < c1 - c0; ++l) {
+  const int len = c1 - c0;
+  int l = 0;
+  for (; l + 8 <= len; l += 8) {
+    double t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t[u] = col[(size_t)(l + u) * n];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] = fma(t[u], xs[r][l + u], acc[r]);
+  }
+  for (; l < len; ++l) {
     const double t = col[(size_t)l * n];
 #pragma unroll
-    for (int r = 0; r < kDtnGroup; ++r)
-      if (r < nr) acc[r] = fma(t, xs[r][l], acc[r]);
+    for (int r = 0; r < NR; ++r) acc[r] = fma(t, xs[r][l], acc[r]);
   }
 #pragma unroll
-  for (int r = 0; r < kDtnGroup; ++r)
-    if (r < nr) part[((int64_t)kc * nrhs + r0 + r) * n + i] = acc[r];
+  for (int r = 0; r < NR; ++r) part[((int64_t)kc * nrhs + r0 + r) * n + i] = acc[r];
 }
 
 // g[r * n + rff[i]] = sum over chunks kc (in order) of part[(kc * nrhs + r) * n + i]
@@ -102,14 +115,13 @@ __global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, int64
   if (e < n) d[e] = (double)s[e];
 }
 
-// Barycentric Lagrange basis of the p Chebyshev points of the second kind,
-// increasing (t_j = -cos(pi j / (p - 1))), at t; exact at the nodes.
-__device__ void cheb_basis(double t, int p, double* ell) {
+// Barycentric Lagrange basis of the p Chebyshev points of the second kind
+// ts (increasing), at t; exactly 1 / 0 when t is a node.
+__device__ void cheb_basis(double t, int p, const double* ts, double* ell) {
   double den = 0.0;
   int hit = -1;
   for (int j = 0; j < p; ++j) {
-    const double tj = -cospi((double)j / (double)(p - 1));
-    const double d = t - tj;
+    const double d = t - ts[j];
     if (d == 0.0) hit = j;
     double wj = (j & 1) ? -1.0 : 1.0;
     if (j == 0 || j == p - 1) wj *= 0.5;
@@ -124,38 +136,44 @@ __device__ void cheb_basis(double t, int p, double* ell) {
   for (int j = 0; j < p; ++j) ell[j] *= inv;
 }
 
-// One thread per (point, right-hand side).  out[r * npts + i] = u_r(x_i, y_i).
-__global__ void k_interp(const double* __restrict__ u, int nrhs, int64_t per_rhs,
-                         InterpGrid s, const double* __restrict__ xy, int64_t npts,
-                         double* __restrict__ out, int* __restrict__ status) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= npts * nrhs) return;
-  const int64_t i = e % npts;
-  const int64_t r = e / npts;
+// One thread per point (all right-hand sides); the nodes are computed once per
+// CTA.  out[r * npts + i] = u_r(x_i, y_i).
+__global__ void __launch_bounds__(128) k_interp(const double* __restrict__ u, int nrhs,
+                                                int64_t per_rhs, InterpGrid s,
+                                                const double* __restrict__ xy, int64_t npts,
+                                                double* __restrict__ out,
+                                                int* __restrict__ status) {
+  __shared__ double ts[64];
+  const int p = s.p;
+  if (threadIdx.x < p) ts[threadIdx.x] = -cospi((double)threadIdx.x / (double)(p - 1));
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npts) return;
   const double x = xy[2 * i], y = xy[2 * i + 1];
   if (!(x >= s.x0 && x <= s.x1 && y >= s.y0 && y <= s.y1)) {
-    out[r * npts + i] = __longlong_as_double(0x7ff8000000000000LL);  // NaN
+    for (int r = 0; r < nrhs; ++r) out[r * npts + i] = __longlong_as_double(0x7ff8000000000000LL);
     if (status) atomicCAS(status, 0, 1);
     return;
   }
-  // leaf: the one to the right (above) of a shared edge, the last one on the
+  // leaf: the one to the east (north) of a shared edge, the last one on the
   // domain's east (north) side
   const double sx = (x - s.x0) / (s.x1 - s.x0) * s.nx;
   const double sy = (y - s.y0) / (s.y1 - s.y0) * s.ny;
   const int ix = min((int)floor(sx), s.nx - 1), iy = min((int)floor(sy), s.ny - 1);
-  const double tx = 2.0 * (sx - ix) - 1.0, ty = 2.0 * (sy - iy) - 1.0;
-  const int p = s.p;
   double lx[64], ly[64];
-  cheb_basis(tx, p, lx);
-  cheb_basis(ty, p, ly);
-  const double* w = u + r * per_rhs + ((int64_t)iy * s.nx + ix) * p * p;
-  double acc = 0.0;
-  for (int a = 0; a < p; ++a) {
-    double row = 0.0;
-    for (int b = 0; b < p; ++b) row = fma(lx[b], w[a * p + b], row);
-    acc = fma(ly[a], row, acc);
+  cheb_basis(2.0 * (sx - ix) - 1.0, p, ts, lx);
+  cheb_basis(2.0 * (sy - iy) - 1.0, p, ts, ly);
+  const int64_t leaf = ((int64_t)iy * s.nx + ix) * p * p;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* w = u + r * per_rhs + leaf;
+    double acc = 0.0;
+    for (int a = 0; a < p; ++a) {
+      double row = 0.0;
+      for (int b = 0; b < p; ++b) row = fma(lx[b], w[a * p + b], row);
+      acc = fma(ly[a], row, acc);
+    }
+    out[r * npts + i] = acc;
   }
-  out[r * npts + i] = acc;
 }
 
 }  // namespace
@@ -163,7 +181,7 @@ __global__ void k_interp(const double* __restrict__ u, int nrhs, int64_t per_rhs
 size_t dtn_apply_ws_bytes(int n, int nrhs) {
   const size_t fr = (size_t)n * nrhs * sizeof(double);
   const int nchunks = (n + kDtnChunk - 1) / kDtnChunk;
-  if (oz_eligible(n, nrhs, n)) {
+  if (dtn_use_tc(n, nrhs)) {
     std::vector<OzDesc> h(1);
     h[0].M = n;
     h[0].N = nrhs;
@@ -187,7 +205,7 @@ cudaError_t dtn_apply(const double* T, int n, const int* rff, const double* f, i
     prof::Scope sc("dtn_gather", st, 0.0, 16.0 * tot);
     k_dtn_gather<<<eb, 256, 0, st>>>(f, rff, n, nrhs, fr);
   }
-  if (oz_eligible(n, nrhs, n)) {
+  if (dtn_use_tc(n, nrhs)) {
     double* gr = reinterpret_cast<double*>(w);
     w += ((size_t)n * nrhs * sizeof(double) + 255) & ~size_t(255);
     std::vector<OzDesc> h(1);
@@ -214,12 +232,18 @@ cudaError_t dtn_apply(const double* T, int n, const int* rff, const double* f, i
   double* part = reinterpret_cast<double*>(w);
   const int nchunks = (n + kDtnChunk - 1) / kDtnChunk;
   const dim3 grid((unsigned)((n + kDtnRows - 1) / kDtnRows), (unsigned)nchunks);
-  for (int r0 = 0; r0 < nrhs; r0 += kDtnGroup) {
-    const int nr = std::min(kDtnGroup, nrhs - r0);
+  for (int r0 = 0; r0 < nrhs;) {
+    const int nr = nrhs - r0 >= 8 ? 8 : nrhs - r0 >= 4 ? 4 : nrhs - r0 >= 2 ? 2 : 1;
     // bytes: T once per pass, the data and the partial sums
     prof::Scope sc("dtn_matvec", st, 2.0 * n * (double)n * nr,
                    8.0 * ((double)n * n + (double)n * nr * (1 + nchunks)));
-    k_dtn_matvec<<<grid, kDtnRows, 0, st>>>(T, n, fr, nrhs, r0, nr, part);
+    switch (nr) {
+      case 8: k_dtn_matvec<8><<<grid, kDtnRows, 0, st>>>(T, n, fr, nrhs, r0, part); break;
+      case 4: k_dtn_matvec<4><<<grid, kDtnRows, 0, st>>>(T, n, fr, nrhs, r0, part); break;
+      case 2: k_dtn_matvec<2><<<grid, kDtnRows, 0, st>>>(T, n, fr, nrhs, r0, part); break;
+      default: k_dtn_matvec<1><<<grid, kDtnRows, 0, st>>>(T, n, fr, nrhs, r0, part); break;
+    }
+    r0 += nr;
   }
   prof::Scope sc("dtn_reduce", st, (double)tot * nchunks, 8.0 * tot * (nchunks + 1));
   k_dtn_reduce<<<eb, 256, 0, st>>>(part, n, nrhs, nchunks, rff, g);
@@ -239,7 +263,7 @@ void interp_points(const double* u, int nrhs, const InterpGrid& s, const double*
   const int64_t pp = (int64_t)s.p * s.p;
   prof::Scope sc("interp_points", st, (double)tot * (2.0 * pp + 8.0 * s.p),
                  (double)tot * (8.0 * pp + 8.0) + 16.0 * npts);
-  k_interp<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(u, nrhs, (int64_t)s.nx * s.ny * pp, s,
+  k_interp<<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(u, nrhs, (int64_t)s.nx * s.ny * pp, s,
                                                           xy, npts, out, status);
 }
 

@@ -2,7 +2,7 @@
 
 Tolerance: relative max error <= 1e-10 over all output nodes (the FP64 bar);
 the Laplace ladder is also held to 1e-11, since the merges are exact in exact
-arithmetic (remark after Algorithm 2) and only rounding, amplified by the
+arithmetic (Remark 5.1) and only rounding, amplified by the
 conditioning of the DtN maps for oscillatory boundary data, separates the two
 eliminations.
 """
