@@ -397,30 +397,39 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
 
 // ----------------------------------------- LU: swaps + unit-lower block solve
 // The interchanges of one panel (rows k0.., pivots ipiv[k0..k0+nbk)) move at
-// most 2*nb rows: rows_inv lists them (relative to k0; the block rows first)
-// and slot t takes the old value of slot src_of[t].  Returns their count.
-__device__ int panel_perm(const int* ipiv, int k0, int nbk, int* rows_inv, int* src_of) {
-  int nr = nbk;
-  for (int i = 0; i < nbk; ++i) rows_inv[i] = i;
+// most 2*nb rows: rows_inv lists them (relative to k0; the block rows first,
+// then the other pivot rows in order of first use) and slot t takes the old
+// value of slot src_of[t].  Built by one warp in parallel: lane j holds
+// interchange j; the external pivot rows are deduplicated with
+// __match_any_sync and numbered by a ballot; the interchanges are then
+// replayed on the slot contents (lane t holds slots t and t + 32) with
+// shuffles.  Returns the number of rows involved.
+__device__ int panel_perm_warp(const int* ipiv, int k0, int nbk, int* rows_inv, int* src_of,
+                               int lane) {
+  const int pr = lane < nbk ? ipiv[k0 + lane] - k0 : -1;
+  const bool ext = lane < nbk && pr >= nbk;
+  const unsigned same = __match_any_sync(0xffffffffu, ext ? pr : -1 - lane);
+  const int lead = __ffs(same) - 1;  // first lane with this pivot row
+  const bool first = ext && lead == lane;
+  const unsigned firsts = __ballot_sync(0xffffffffu, first);
+  const int nr = nbk + __popc(firsts);
+  const int slot = !ext ? (lane < nbk ? pr : 0) : nbk + __popc(firsts & ((1u << lead) - 1u));
+  if (lane < nbk) rows_inv[lane] = lane;
+  if (first) rows_inv[slot] = pr;
+  int c0 = lane, c1 = lane + 32;
   for (int j = 0; j < nbk; ++j) {
-    int pr = ipiv[k0 + j] - k0;
-    bool found = false;
-    for (int t = 0; t < nr; ++t) found |= (rows_inv[t] == pr);
-    if (!found) rows_inv[nr++] = pr;
+    const int tp = __shfl_sync(0xffffffffu, slot, j);
+    const int vj = __shfl_sync(0xffffffffu, c0, j);
+    const int vt = __shfl_sync(0xffffffffu, tp < 32 ? c0 : c1, tp & 31);
+    if (lane == j) c0 = vt;
+    if (tp < 32) {
+      if (lane == tp) c0 = vj;
+    } else if (lane == (tp & 31)) {
+      c1 = vj;
+    }
   }
-  // apply the interchanges to the slot contents
-  int content[2 * kNB];
-  for (int t = 0; t < nr; ++t) content[t] = t;
-  for (int j = 0; j < nbk; ++j) {
-    int pr = ipiv[k0 + j] - k0;
-    int tj = j, tp = 0;
-    for (int t = 0; t < nr; ++t)
-      if (rows_inv[t] == pr) tp = t;
-    int c = content[tj];
-    content[tj] = content[tp];
-    content[tp] = c;
-  }
-  for (int t = 0; t < nr; ++t) src_of[t] = content[t];
+  if (lane < nr) src_of[lane] = c0;
+  if (lane + 32 < nr) src_of[lane + 32] = c1;
   return nr;
 }
 
@@ -502,10 +511,13 @@ __global__ void __launch_bounds__(256) k_lu_swap_trsm(const LuDesc<R>* __restric
     int i = e % nbk, j = e / nbk;
     L11[i + j * kNB] = D.A[(k0 + i) + (size_t)(k0 + j) * D.lda];
   }
-  if (threadIdx.x == 0) s_nr = do_swap ? panel_perm(D.ipiv, k0, nbk, rows_inv, src_of) : nbk;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (wid == 0) {
+    const int n = do_swap ? panel_perm_warp(D.ipiv, k0, nbk, rows_inv, src_of, lane) : nbk;
+    if (lane == 0) s_nr = n;
+  }
   __syncthreads();
   const int nr = s_nr;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int col = cbeg + wid; col < cend; col += nw) {
     R* x;
     bool solve;
@@ -555,13 +567,13 @@ __global__ void __launch_bounds__(256) k_lu_swap_far(const LuDesc<R>* __restrict
   __shared__ int rows_inv[kP][2 * kNB];
   __shared__ int src_of[kP][2 * kNB];
   __shared__ int s_nr[kP];
-  if (threadIdx.x < np) {
-    const int k0 = K0 + threadIdx.x * kNB;
-    s_nr[threadIdx.x] =
-        panel_perm(D.ipiv, k0, min(kNB, m - k0), rows_inv[threadIdx.x], src_of[threadIdx.x]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = wid; b < np; b += nw) {  // one warp per panel
+    const int k0 = K0 + b * kNB;
+    const int n = panel_perm_warp(D.ipiv, k0, min(kNB, m - k0), rows_inv[b], src_of[b], lane);
+    if (lane == 0) s_nr[b] = n;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int col = cbeg + wid; col < cend; col += nw) {
     R* x0 = col < nfa ? D.A + (size_t)(oe + col) * D.lda : D.B + (size_t)(col - nfa) * D.ldb;
     for (int p = 0; p < np; ++p) {
