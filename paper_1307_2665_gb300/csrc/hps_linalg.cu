@@ -12,6 +12,7 @@
 // argmax, and the scale + rank-1 update of each column is fused.  Row swaps and
 // the unit-lower triangular solve of the block row run one warp per column with
 // the block row held in registers (lane = row).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -395,6 +396,164 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
   }
 }
 
+// Tall panels: one thread-block cluster of kPanelCl CTAs per matrix, the
+// panel's rows split into kPanelCl slices, each staged in its CTA's shared
+// memory, so the rank-1 updates of a column run on kPanelCl SMs (FP64 FMAs are
+// 2 per clock per SM: one SM bounds a tall panel).  Per column: every CTA
+// offers its best row (largest |value|, ties to the smaller row), all read the
+// kPanelCl offers over distributed shared memory and take the same pivot; a
+// swap reads both rows before a cluster barrier and writes them after it; the
+// pivot row is read by every CTA and each updates its own rows.  Same pivots,
+// same FMAs in the same order per element: the factors equal k_lu_panel's bit
+// for bit.  Cluster barriers: one per column, three when rows are swapped, and
+// one before exit (no CTA leaves while others may still read its memory).
+constexpr int kPanelCl = 8;
+
+template <typename R>
+__global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
+    k_lu_panel_cl(const LuDesc<R>* __restrict__ d, int k0, int chunk_max, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const LuDesc<R> D = d[blockIdx.x / kPanelCl];
+  const int m = D.m;
+  if (k0 >= m) return;  // the whole cluster
+  const int nbk = min(kNB, m - k0);
+  const int rows = m - k0;
+  const int chunk = (rows + kPanelCl - 1) / kPanelCl;  // <= chunk_max
+  const int r0 = min(rows, rank * chunk), r1 = min(rows, r0 + chunk);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  R* P = reinterpret_cast<R*>(smraw);  // own rows r0..r1-1 (relative to k0), column-major, ld chunk
+  __shared__ R cand_v[2];  // this CTA's offer per column parity
+  __shared__ int cand_i[2];
+  __shared__ R red_v[8];
+  __shared__ int red_i[8];
+  __shared__ int s_piv;
+  __shared__ R prow[kNB];
+  R* A0 = D.A + k0 + (size_t)k0 * D.lda;
+  const int nown = r1 - r0;
+  for (int e = threadIdx.x; e < nown * nbk; e += blockDim.x) {
+    const int i = e % nown, c = e / nown;
+    P[i + c * chunk] = A0[(r0 + i) + (size_t)c * D.lda];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int jj = 0; jj < nbk; ++jj) {
+    const int par = jj & 1;
+    R best = R(-1);
+    int bi = jj;
+    for (int i = max(jj, r0) + threadIdx.x; i < r1; i += blockDim.x) {
+      const R v = fabs(P[(i - r0) + jj * chunk]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[wid] = best;
+      red_i[wid] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      R bv = red_v[0];
+      int bx = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) {
+          bv = red_v[w];
+          bx = red_i[w];
+        }
+      cand_v[par] = bv;
+      cand_i[par] = bx;
+    }
+    cl.sync();  // offers visible
+    if (threadIdx.x == 0) {
+      R bv = R(-1);
+      int bx = jj;
+      for (int r = 0; r < kPanelCl; ++r) {
+        const R v = *cl.map_shared_rank(&cand_v[par], r);
+        const int x = *cl.map_shared_rank(&cand_i[par], r);
+        if (v > bv || (v == bv && x < bx)) {
+          bv = v;
+          bx = x;
+        }
+      }
+      s_piv = bx;
+      if (rank == 0) D.ipiv[k0 + jj] = k0 + bx;
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    const int og = jj / chunk;  // owner of row jj
+    if (piv != jj) {  // the same decision in every CTA
+      const int op = piv / chunk;
+      R vg = R(0), vp = R(0);
+      if (threadIdx.x < nbk) {
+        const int c = threadIdx.x;
+        if (rank == og) vp = cl.map_shared_rank(P, op)[(piv - op * chunk) + c * chunk];
+        if (rank == op) vg = cl.map_shared_rank(P, og)[(jj - og * chunk) + c * chunk];
+      }
+      cl.sync();  // both rows read before either is written
+      if (threadIdx.x < nbk) {
+        const int c = threadIdx.x;
+        if (rank == og) P[(jj - r0) + c * chunk] = vp;
+        if (rank == op) P[(piv - r0) + c * chunk] = vg;
+      }
+      cl.sync();  // swapped rows visible
+    }
+    if (threadIdx.x < nbk)
+      prow[threadIdx.x] = cl.map_shared_rank(P, og)[(jj - og * chunk) + threadIdx.x * chunk];
+    __syncthreads();
+    const R pv = prow[jj];
+    const bool bad = !(pv != R(0)) || !isfinite(pv);
+    if (bad && rank == 0 && threadIdx.x == 0 && status) atomicCAS(status, 0, D.box + 1);
+    const R inv = bad ? R(0) : R(1) / pv;
+    for (int i = max(jj + 1, r0) + threadIdx.x; i < r1; i += blockDim.x) {
+      const int li = i - r0;
+      R l = P[li + jj * chunk] * inv;
+      P[li + jj * chunk] = l;
+      for (int c = jj + 1; c < nbk; ++c) P[li + c * chunk] = fma(-l, prow[c], P[li + c * chunk]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nown * nbk; e += blockDim.x) {
+    const int i = e % nown, c = e / nown;
+    A0[(r0 + i) + (size_t)c * D.lda] = P[i + c * chunk];
+  }
+  cl.sync();  // no CTA exits while another may still read its shared memory
+}
+
+// One panel launch: a cluster per matrix for tall panels of few matrices (the
+// top merges), else one CTA per matrix.  Both give the same factors.
+template <typename R>
+bool launch_panel(const LuDesc<R>* d_desc, int nd, int max_m, int k0, int* d_status,
+                  cudaStream_t st, double fl, double by) {
+  const int rows = max_m - k0;
+  const int smem_max = 224 * 1024;
+  const int chunk = (rows + kPanelCl - 1) / kPanelCl;
+  const long long cl_bytes = (long long)chunk * std::min(kNB, rows) * (long long)sizeof(R);
+  prof::Scope sc(TName<R>::panel(), st, fl, by);
+  // the opt-in is cached per kernel: always ask for the same (largest) size
+  if (rows >= 512 && nd <= 32 && cl_bytes <= smem_max &&
+      opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel_cl<R>), smem_max)) {
+    k_lu_panel_cl<R><<<(unsigned)(nd * kPanelCl), 256, (size_t)cl_bytes, st>>>(d_desc, k0, chunk,
+                                                                             d_status);
+    return true;
+  }
+  const long long need = (long long)rows * std::min(kNB, rows) * (long long)sizeof(R);
+  const int smem_bytes = (int)std::min<long long>(need, smem_max);
+  const int threads = rows > 512 ? 512 : 256;
+  k_lu_panel<R><<<nd, threads, smem_bytes, st>>>(d_desc, k0, smem_bytes / (int)sizeof(R), d_status);
+  return true;
+}
+
 // ----------------------------------------- LU: swaps + unit-lower block solve
 // The interchanges of one panel (rows k0.., pivots ipiv[k0..k0+nbk)) move at
 // most 2*nb rows: rows_inv lists them (relative to k0; the block rows first,
@@ -726,13 +885,7 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
       double by = sum([&](int m, int nr) {
         return k0 < m ? 2.0 * (m - k0) * std::min(kNB, m - k0) * es : 0.0;
       });
-      const int rows = max_m - k0;
-      const long long need = (long long)rows * std::min(kNB, rows) * (long long)sizeof(R);
-      const int smem_bytes = (int)std::min<long long>(need, smem_max);
-      const int smem_elems = smem_bytes / (int)sizeof(R);
-      const int threads = rows > 512 ? 512 : 256;
-      prof::Scope sc(TName<R>::panel(), st, fl, by);
-      k_lu_panel<R><<<nd, threads, smem_bytes, st>>>(d_desc, k0, smem_elems, d_status);
+      launch_panel<R>(d_desc, nd, max_m, k0, d_status, st, fl, by);
     }
     int total_cols = (factor ? (swap_left ? k0 : 0) + max_m : 0) + max_nrhs;
     int chunks = (total_cols + cols_per_cta - 1) / cols_per_cta;
@@ -952,12 +1105,7 @@ cudaError_t lu_solve_tc(const LuDesc<double>* d_desc, const std::vector<LuDescHo
           for (int jj = 0; jj < nbk; ++jj) fl += (double)(rows - jj - 1) * (2.0 * (nbk - jj - 1) + 1.0);
           by += 2.0 * rows * nbk * es;
         });
-        const int rows = max_m - k0;
-        const long long need = (long long)rows * std::min(kNB, rows) * (long long)sizeof(R);
-        const int smem_bytes = (int)std::min<long long>(need, smem_max);
-        prof::Scope sc(TName<R>::panel(), st, fl, by);
-        k_lu_panel<R><<<nd, rows > 512 ? 512 : 256, smem_bytes, st>>>(
-            d_desc, k0, smem_bytes / (int)sizeof(R), d_status);
+        launch_panel<R>(d_desc, nd, max_m, k0, d_status, st, fl, by);
       }
       int cols = 0, Mx = 0, Nx = 0;
       double fl = 0.0, by = 0.0, flu = 0.0, byu = 0.0;

@@ -45,7 +45,8 @@ int read(Stat* out, int max_out);
 
 // Raise a kernel's dynamic shared-memory limit to `bytes` once per (kernel,
 // device), thread-safe; false if the device refused (the launch then fails and
-// the caller's launch check reports it).
+// the caller's launch check reports it).  Only the first call per (kernel,
+// device) sets the limit: every caller passes the kernel's largest size.
 bool opt_in_smem(const void* kernel, int bytes);
 
 }  // namespace hps

@@ -81,3 +81,26 @@ def test_batch_rejects_single_solve_entry():
     st = hps.lib().hps_solve_ex(bh.ptr, probs[0]["f"].ctypes.data, 3, u.ctypes.data, 0, None)
     assert st == hps.HPS_EINVAL
     bh.close()
+
+
+def test_tall_panels_agree_alone_and_batched():
+    """A 40 x 40 problem with q = 13 has a 520-unknown top merge: solved alone,
+    its tall panels are factored by a thread-block cluster; in a batch of 33
+    copies (too many matrices for the cluster path) by one CTA each.  Same
+    pivots and FMAs: the solutions agree bit for bit."""
+    dom, n, p, q = (0.0, 1.0, 0.0, 1.0), 40, 15, 13
+    xy = hps.hps_cheb_nodes(dom, n, n, p)
+    co = {k: (None if v is None else np.ascontiguousarray(v, dtype=np.float64))
+          for k, v in I.random_smooth_operator(3, xy[..., 0], xy[..., 1]).items()}
+    bxy = hps.hps_boundary_nodes_grid(dom, n, n, q)
+    f = np.ascontiguousarray(np.stack([I.fourier_boundary(s, bxy[:, 0], bxy[:, 1], dom)
+                                       for s in range(2)]))
+    h = hps.hps_build(dom, n, n, p, q, co)
+    u1 = hps.hps_solve(h, f)
+    h.close()
+    pr = {"domain": dom, "nx": n, "ny": n, "p": p, "q": q, "coeffs": co}
+    bh = hps.hps_build_batch([pr] * 33)
+    us = [np.empty((2, n * n, p, p)) for _ in range(33)]
+    hps.hps_solve_batch(bh, [f] * 33, us)
+    bh.close()
+    assert np.array_equal(u1, us[0]) and np.array_equal(u1, us[32])
