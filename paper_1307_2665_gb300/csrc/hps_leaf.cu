@@ -79,49 +79,74 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int l0, int 
     G[e] = s;
   }
   __syncthreads();
-  const double* c11 = cf;
-  const double* c12 = cf + pp;
-  const double* c22 = cf + 2 * pp;
-  const double* c1 = cf + 3 * pp;
-  const double* c2 = cf + 4 * pp;
-  const double* c0 = cf + 5 * pp;
+  // per interior row r = (a, b): the coefficient products every entry of the
+  // row uses, once (FP64; the FP64 pipe is scarce)
   const bool has12 = cp.c[1] != nullptr;
+  double* rf = cf + 6 * pp;  // 5 x ni: -c11 sx^2, c1 sx, -c22 sy^2, c2 sy, -2 c12 sx sy
+  for (int ri = threadIdx.x; ri < ni; ri += blockDim.x) {
+    const int r = (ri / pi + 1) * p + ri % pi + 1;
+    rf[ri] = -cf[r] * sx * sx;
+    rf[ni + ri] = cf[3 * pp + r] * sx;
+    rf[2 * ni + ri] = -cf[2 * pp + r] * sy * sy;
+    rf[3 * ni + ri] = cf[4 * pp + r] * sy;
+    rf[4 * ni + ri] = has12 ? -2.0 * cf[pp + r] * sx * sy : 0.0;
+  }
+  __syncthreads();
+  const double* c0 = cf + 5 * pp;
   R* Al = Aii + (size_t)j * ni * ni;
-  // A_ii(ri, ci), ri = (a-1)*(p-2) + (b-1), ci = (c-1)*(p-2) + (d-1)
-  for (int e = threadIdx.x; e < ni * ni; e += blockDim.x) {
-    const int ri = e % ni, ci = e / ni;
-    const int a = ri / pi + 1, b = ri % pi + 1, c = ci / pi + 1, d = ci % pi + 1;
-    const int r = a * p + b;
-    double v = 0.0;
-    if (a == c) v += -c11[r] * sx * sx * D2[b * p + d] + c1[r] * sx * D[b * p + d];
-    if (b == d) v += -c22[r] * sy * sy * D2[a * p + c] + c2[r] * sy * D[a * p + c];
-    if (has12) v += -2.0 * c12[r] * sx * sy * D[a * p + c] * D[b * p + d];
-    if (a == c && b == d) v += c0[r];
-    Al[e] = (R)v;
+  R* Yl = Y + (size_t)j * ys;
+  // A_ii(ri, ci), ri = (a-1)*(p-2) + (b-1), ci = (c-1)*(p-2) + (d-1): thread
+  // rows, columns uniform per iteration (no index divisions per entry)
+  for (int ri0 = 0; ri0 < ni; ri0 += blockDim.x) {
+    const int ri = ri0 + threadIdx.x;
+    if (ri >= ni) break;
+    const int a = ri / pi + 1, b = ri % pi + 1, r = a * p + b;
+    const double fxx = rf[ri], fx = rf[ni + ri], fyy = rf[2 * ni + ri], fy = rf[3 * ni + ri],
+                 fxy = rf[4 * ni + ri];
+    int c = 1, d = 1;
+    for (int ci = 0; ci < ni; ++ci) {
+      double v = 0.0;
+      if (a == c) v += fxx * D2[b * p + d] + fx * D[b * p + d];
+      if (b == d) v += fyy * D2[a * p + c] + fy * D[a * p + c];
+      if (has12) v += fxy * D[a * p + c] * D[b * p + d];
+      if (a == c && b == d) v += c0[r];
+      Al[ri + (size_t)ci * ni] = (R)v;
+      if (with_identity)  // columns nq .. nq+ni-1: the identity, so the solve also returns A_ii^{-1}
+        Yl[(size_t)ni * nq + ri + (size_t)ci * ni] = (ri == ci) ? R(1) : R(0);
+      if (++d == p - 1) {
+        d = 1;
+        ++c;
+      }
+    }
   }
   // B = -A_ie L1 (ni x 4q).  For an interior row (a, b) only the boundary nodes
   // of row a / column b are reached by the pure x / pure y terms; the mixed term
   // reaches every node of a side, collapsed through G.
-  R* Yl = Y + (size_t)j * ys;
-  if (with_identity)  // columns nq .. nq+ni-1: the identity, so the solve also returns A_ii^{-1}
-    for (int e = threadIdx.x; e < ni * ni; e += blockDim.x)
-      Yl[(size_t)ni * nq + e] = (e % ni == e / ni) ? R(1) : R(0);
-  for (int e = threadIdx.x; e < ni * nq; e += blockDim.x) {
-    const int ri = e % ni, gcol = e / ni;
-    const int s = gcol / q, k = gcol % q;
+  for (int ri0 = 0; ri0 < ni; ri0 += blockDim.x) {
+    const int ri = ri0 + threadIdx.x;
+    if (ri >= ni) break;
     const int a = ri / pi + 1, b = ri % pi + 1;
-    const int r = a * p + b;
-    double v;
-    if (s == 0 || s == 2) {  // horizontal side: node (c, b) with c = 0 or p-1
-      const int c = (s == 0) ? 0 : p - 1;
-      v = (c22[r] * sy * sy * D2[a * p + c] - c2[r] * sy * D[a * p + c]) * Pg[b * q + k];
-      if (has12) v += 2.0 * c12[r] * sx * sy * D[a * p + c] * G[b * q + k];
-    } else {  // vertical side: node (a, d) with d = p-1 (east) or 0 (west)
-      const int d = (s == 1) ? p - 1 : 0;
-      v = (c11[r] * sx * sx * D2[b * p + d] - c1[r] * sx * D[b * p + d]) * Pg[a * q + k];
-      if (has12) v += 2.0 * c12[r] * sx * sy * D[b * p + d] * G[a * q + k];
+    const double fxx = rf[ri], fx = rf[ni + ri], fyy = rf[2 * ni + ri], fy = rf[3 * ni + ri],
+                 fxy = rf[4 * ni + ri];
+    // the four sides' row factors, then the q Gauss columns of each side
+    const double hS = -(fyy * D2[a * p] + fy * D[a * p]);
+    const double hN = -(fyy * D2[a * p + p - 1] + fy * D[a * p + p - 1]);
+    const double hE = -(fxx * D2[b * p + p - 1] + fx * D[b * p + p - 1]);
+    const double hW = -(fxx * D2[b * p] + fx * D[b * p]);
+    for (int k = 0; k < q; ++k) {
+      double vS = hS * Pg[b * q + k], vN = hN * Pg[b * q + k];
+      double vE = hE * Pg[a * q + k], vW = hW * Pg[a * q + k];
+      if (has12) {
+        vS -= fxy * D[a * p] * G[b * q + k];
+        vN -= fxy * D[a * p + p - 1] * G[b * q + k];
+        vE -= fxy * D[b * p + p - 1] * G[a * q + k];
+        vW -= fxy * D[b * p] * G[a * q + k];
+      }
+      Yl[ri + (size_t)(0 * q + k) * ni] = (R)vS;
+      Yl[ri + (size_t)(1 * q + k) * ni] = (R)vE;
+      Yl[ri + (size_t)(2 * q + k) * ni] = (R)vN;
+      Yl[ri + (size_t)(3 * q + k) * ni] = (R)vW;
     }
-    Yl[e] = (R)v;
   }
 }
 
@@ -132,7 +157,8 @@ void leaf_assemble(const double* const* coef, int l0, int nleaves, int p, int q,
   if (nleaves <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
-  size_t smem = (size_t)(2 * p * p + 2 * p * q + 6 * p * p) * sizeof(double);
+  size_t smem = (size_t)(2 * p * p + 2 * p * q + 6 * p * p + 5 * (p - 2) * (p - 2)) *
+                sizeof(double);
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_assemble<R>), 200 * 1024))
     return;  // reported by the caller's launch check
   const double ni = (double)(p - 2) * (p - 2);

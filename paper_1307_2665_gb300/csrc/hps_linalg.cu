@@ -25,6 +25,7 @@
 namespace hps {
 
 constexpr int kNB = 32;  // panel width == warp width (lane = row of the block row)
+constexpr int kTrsmCols = 64;  // columns (threads) per CTA of the diagonal-block solve
 
 template <typename R>
 struct TName;
@@ -531,7 +532,8 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
 }
 
 // One panel launch: a cluster per matrix for tall panels of few matrices (the
-// top merges), else one CTA per matrix.  Both give the same factors.
+// top merges; below 512 rows the cluster barriers cost what the spread saves),
+// else one CTA per matrix.  Both give the same factors.
 template <typename R>
 bool launch_panel(const LuDesc<R>* d_desc, int nd, int max_m, int k0, int* d_status,
                   cudaStream_t st, double fl, double by) {
@@ -541,11 +543,13 @@ bool launch_panel(const LuDesc<R>* d_desc, int nd, int max_m, int k0, int* d_sta
   const long long cl_bytes = (long long)chunk * std::min(kNB, rows) * (long long)sizeof(R);
   prof::Scope sc(TName<R>::panel(), st, fl, by);
   // the opt-in is cached per kernel: always ask for the same (largest) size
-  if (rows >= 512 && nd <= 32 && cl_bytes <= smem_max &&
+  if (rows >= 512 && nd <= 32) {
+    if (cl_bytes <= smem_max &&
       opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel_cl<R>), smem_max)) {
-    k_lu_panel_cl<R><<<(unsigned)(nd * kPanelCl), 256, (size_t)cl_bytes, st>>>(d_desc, k0, chunk,
-                                                                             d_status);
-    return true;
+      k_lu_panel_cl<R><<<(unsigned)(nd * kPanelCl), 256, (size_t)cl_bytes, st>>>(d_desc, k0,
+                                                                               chunk, d_status);
+      return true;
+    }
   }
   const long long need = (long long)rows * std::min(kNB, rows) * (long long)sizeof(R);
   const int smem_bytes = (int)std::min<long long>(need, smem_max);
@@ -872,7 +876,9 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
   const int smem_max = 224 * 1024;
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel<R>), smem_max))
     return;  // reported by the caller's launch check
-  const int cols_per_cta = 64;
+  // few matrices: narrower column chunks, so the FP64 interchange and solve
+  // work spreads over more SMs
+  const int cols_per_cta = nd >= 64 ? 64 : 16;
   for (int k0 = 0; k0 < max_m; k0 += kNB) {
     if (factor) {
       double fl = sum([&](int m, int nr) {
@@ -941,8 +947,8 @@ void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, 
         return (2.0 * nbk * nr + 0.5 * nbk * nbk) * es;
       });
       prof::Scope sc(TName<R>::trsm(), st, fl, by);
-      int chunks = (max_nrhs + 255) / 256;
-      k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, kb0, chunks);
+      int chunks = (max_nrhs + kTrsmCols - 1) / kTrsmCols;
+      k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), kTrsmCols, 0, st>>>(d_desc, kb0, chunks);
     }
     if (kb0 > 0) {
       double fl = sum([&](int m, int nr) {
@@ -1072,7 +1078,7 @@ cudaError_t lu_solve_tc(const LuDesc<double>* d_desc, const std::vector<LuDescHo
   const int smem_max = 224 * 1024;
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel<R>), smem_max))
     return cudaErrorInvalidValue;
-  const int cpc = 64;  // columns per CTA of the interchange kernels
+  const int cpc = nd >= 64 ? 64 : 16;  // columns per CTA of the interchange kernels
   const double es = 8.0;
   // per-descriptor maxima and sums over the descriptors that reach panel k0
   auto over = [&](int k0, auto fn) {
@@ -1194,9 +1200,10 @@ cudaError_t lu_solve_tc(const LuDesc<double>* d_desc, const std::vector<LuDescHo
           fl += (double)nbk * nbk * nrhs;
           by += (2.0 * nbk * nrhs + 0.5 * nbk * nbk) * es;
         });
-        const int chunks = (max_nrhs + 255) / 256;
+        const int chunks = (max_nrhs + kTrsmCols - 1) / kTrsmCols;
         prof::Scope sc(TName<R>::trsm(), st, fl, by);
-        k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(d_desc, kb0, chunks);
+        k_trsm_upper<R><<<(unsigned)((long long)nd * chunks), kTrsmCols, 0, st>>>(d_desc, kb0,
+                                                                                chunks);
       }
       if (kb0 > K0) {
         double fl = 0.0, by = 0.0;
