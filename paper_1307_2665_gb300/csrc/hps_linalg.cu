@@ -300,6 +300,17 @@ void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int 
 }
 
 // ------------------------------------------------------------ LU: the panel
+// Pivot keys: |x| as its bit pattern, which orders non-negative values as the
+// values do, so the argmax runs on integer compares (FP64 compares share the
+// FP64 pipe, 2 per clock per SM).  A NaN pattern sorts above every number: a
+// NaN in the column becomes the pivot and is reported as a bad pivot.
+__device__ __forceinline__ long long pivot_key(double x) {
+  return __double_as_longlong(x) & 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ int pivot_key(float x) { return __float_as_int(x) & 0x7fffffff; }
+template <typename R>
+using PivotKey = decltype(pivot_key(R(0)));
+
 // Factor columns k0..k0+nbk-1 (rows k0..m-1) of one matrix per CTA.
 template <typename R>
 __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ d, int k0,
@@ -311,9 +322,11 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
   const int rows = m - k0;
   extern __shared__ __align__(16) unsigned char smraw[];
   R* sm = reinterpret_cast<R*>(smraw);
-  __shared__ R red_v[32];
+  using Key = PivotKey<R>;
+  __shared__ Key red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_piv;
+  __shared__ R s_inv;
   const bool staged = rows * nbk <= smem_elems;
   R* A0 = D.A + k0 + (size_t)k0 * D.lda;
   R* P = staged ? sm : A0;
@@ -328,10 +341,10 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int jj = 0; jj < nbk; ++jj) {
     // pivot search: largest |P(i, jj)| over i >= jj, ties to the smaller row
-    R best = R(-1);
+    Key best = -1;
     int bi = jj;
     for (int i = jj + threadIdx.x; i < rows; i += blockDim.x) {
-      R v = fabs(P[i + jj * ldp]);
+      const Key v = pivot_key(P[i + jj * ldp]);
       if (v > best) {
         best = v;
         bi = i;
@@ -339,8 +352,8 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      R ov = __shfl_xor_sync(0xffffffffu, best, o);
-      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const Key ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) {
         best = ov;
         bi = oi;
@@ -352,12 +365,12 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
     }
     __syncthreads();
     if (wid == 0) {
-      best = lane < nw ? red_v[lane] : R(-1);
+      best = lane < nw ? red_v[lane] : -1;
       bi = lane < nw ? red_i[lane] : jj;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        R ov = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const Key ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) {
           best = ov;
           bi = oi;
@@ -366,6 +379,11 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
       if (lane == 0) {
         s_piv = bi;
         D.ipiv[k0 + jj] = k0 + bi;
+        // the pivot value (row bi before the swap) and its reciprocal, once
+        const R pv = P[bi + jj * ldp];
+        const bool bad = !(pv != R(0)) || !isfinite(pv);
+        if (bad && status) atomicCAS(status, 0, D.box + 1);
+        s_inv = bad ? R(0) : R(1) / pv;
       }
     }
     __syncthreads();
@@ -378,10 +396,7 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
       }
       __syncthreads();
     }
-    const R pv = P[jj + jj * ldp];
-    const bool bad = !(pv != R(0)) || !isfinite(pv);
-    if (bad && threadIdx.x == 0 && status) atomicCAS(status, 0, D.box + 1);
-    const R inv = bad ? R(0) : R(1) / pv;
+    const R inv = s_inv;
     for (int i = jj + 1 + threadIdx.x; i < rows; i += blockDim.x) {
       R l = P[i + jj * ldp] * inv;
       P[i + jj * ldp] = l;
@@ -425,11 +440,13 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
   const int r0 = min(rows, rank * chunk), r1 = min(rows, r0 + chunk);
   extern __shared__ __align__(16) unsigned char smraw[];
   R* P = reinterpret_cast<R*>(smraw);  // own rows r0..r1-1 (relative to k0), column-major, ld chunk
-  __shared__ R cand_v[2];  // this CTA's offer per column parity
+  using Key = PivotKey<R>;
+  __shared__ Key cand_v[2];  // this CTA's offer per column parity (pivot key)
   __shared__ int cand_i[2];
-  __shared__ R red_v[8];
+  __shared__ Key red_v[8];
   __shared__ int red_i[8];
   __shared__ int s_piv;
+  __shared__ R s_inv;
   __shared__ R prow[kNB];
   R* A0 = D.A + k0 + (size_t)k0 * D.lda;
   const int nown = r1 - r0;
@@ -441,10 +458,10 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int jj = 0; jj < nbk; ++jj) {
     const int par = jj & 1;
-    R best = R(-1);
+    Key best = -1;
     int bi = jj;
     for (int i = max(jj, r0) + threadIdx.x; i < r1; i += blockDim.x) {
-      const R v = fabs(P[(i - r0) + jj * chunk]);
+      const Key v = pivot_key(P[(i - r0) + jj * chunk]);
       if (v > best) {
         best = v;
         bi = i;
@@ -452,7 +469,7 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const Key ov = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) {
         best = ov;
@@ -465,7 +482,7 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      R bv = red_v[0];
+      Key bv = red_v[0];
       int bx = red_i[0];
       for (int w = 1; w < nw; ++w)
         if (red_v[w] > bv || (red_v[w] == bv && red_i[w] < bx)) {
@@ -477,10 +494,10 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
     }
     cl.sync();  // offers visible
     if (threadIdx.x == 0) {
-      R bv = R(-1);
+      Key bv = -1;
       int bx = jj;
       for (int r = 0; r < kPanelCl; ++r) {
-        const R v = *cl.map_shared_rank(&cand_v[par], r);
+        const Key v = *cl.map_shared_rank(&cand_v[par], r);
         const int x = *cl.map_shared_rank(&cand_i[par], r);
         if (v > bv || (v == bv && x < bx)) {
           bv = v;
@@ -512,10 +529,14 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
     if (threadIdx.x < nbk)
       prow[threadIdx.x] = cl.map_shared_rank(P, og)[(jj - og * chunk) + threadIdx.x * chunk];
     __syncthreads();
-    const R pv = prow[jj];
-    const bool bad = !(pv != R(0)) || !isfinite(pv);
-    if (bad && rank == 0 && threadIdx.x == 0 && status) atomicCAS(status, 0, D.box + 1);
-    const R inv = bad ? R(0) : R(1) / pv;
+    if (threadIdx.x == 0) {  // the reciprocal once per CTA
+      const R pv = prow[jj];
+      const bool bad = !(pv != R(0)) || !isfinite(pv);
+      if (bad && rank == 0 && status) atomicCAS(status, 0, D.box + 1);
+      s_inv = bad ? R(0) : R(1) / pv;
+    }
+    __syncthreads();
+    const R inv = s_inv;
     for (int i = max(jj + 1, r0) + threadIdx.x; i < r1; i += blockDim.x) {
       const int li = i - r0;
       R l = P[li + jj * chunk] * inv;
