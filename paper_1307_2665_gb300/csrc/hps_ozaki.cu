@@ -157,9 +157,11 @@ __global__ void __launch_bounds__(kThreads) k_oz_split(const OzDesc* __restrict_
     ex[r] = in ? exp_at(ework, (side == 0 ? g.ea_off : g.eb_off) + gi) : 0;
   }
   __syncthreads();
+  // block-major: the 8 slices of one (tile, K block) are contiguous, so the
+  // GEMM fetches a block's operand with one bulk copy
   const int blk = side == 0 ? kABlock : kBBlock;
-  const int64_t base = (side == 0 ? g.a_off : g.b_off) + ((int64_t)tile * g.nkb + kb) * blk;
-  const int64_t sstride = (int64_t)ntiles * g.nkb * blk;
+  const int64_t base =
+      (side == 0 ? g.a_off : g.b_off) + ((int64_t)tile * g.nkb + kb) * kS * (int64_t)blk;
   for (int o = threadIdx.x; o < blk; o += kThreads) {
     // operand layout: core (r / 8, k / 8) of 64 elements, rows of 8 k
     const int core = o >> 6, w = o & 63;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_oz_split(const OzDesc* __restrict_
     int q[kS];
     slice8(X[k * ld + r], ex[r], q);
 #pragma unroll
-    for (int s = 0; s < kS; ++s) work[base + s * sstride + o] = __float2bfloat16_rn((float)q[s]);
+    for (int s = 0; s < kS; ++s) work[base + s * blk + o] = __float2bfloat16_rn((float)q[s]);
   }
 }
 
@@ -226,7 +228,8 @@ __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
 
 // grid: (nt, mt, descriptor); 256 threads.  Two stages of shared memory each
 // hold all 8 A slices (8 x 8 KB) and all 8 B slices (8 x 4 KB) of one K block
-// of 32, filled by bulk copies on the stage's barrier; the copies of block
+// of 32, filled by two bulk copies (the slices of a block are contiguous in
+// the workspace) on the stage's barrier; the copies of block
 // kb + 1 run while block kb multiplies.  Thread 0 issues the 36 pair products
 // of a block into 8 TMEM accumulators, one per diagonal d = s + t (8 x 64
 // columns: all of tensor memory), accumulating over groups of 4 blocks (a
@@ -270,8 +273,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const int64_t a_sstride = (int64_t)g.mt * g.nkb * kABlock;
-  const int64_t b_sstride = (int64_t)g.nt * g.nkb * kBBlock;
   const int r = 32 * (warp & 3) + lane;
   const int c0 = 32 * (warp >> 2);
   long long uhi[32], ulo[32];
@@ -285,14 +286,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
     __nv_bfloat16* As = stage[b];
     __nv_bfloat16* Bs = stage[b] + kS * kABlock;
     expect_tx(&bar_ld[b], (uint32_t)(kStage * 2));
-    for (int s = 0; s < kS; ++s) {
-      bulk_load(As + s * kABlock,
-                work + g.a_off + s * a_sstride + ((int64_t)tm * g.nkb + kb) * kABlock,
-                (uint32_t)(kABlock * 2), &bar_ld[b]);
-      bulk_load(Bs + s * kBBlock,
-                work + g.b_off + s * b_sstride + ((int64_t)tn * g.nkb + kb) * kBBlock,
-                (uint32_t)(kBBlock * 2), &bar_ld[b]);
-    }
+    bulk_load(As, work + g.a_off + ((int64_t)tm * g.nkb + kb) * kS * kABlock,
+              (uint32_t)(kS * kABlock * 2), &bar_ld[b]);
+    bulk_load(Bs, work + g.b_off + ((int64_t)tn * g.nkb + kb) * kS * kBBlock,
+              (uint32_t)(kS * kBBlock * 2), &bar_ld[b]);
   };
   if (tid == 0) {
     load_block(0);
