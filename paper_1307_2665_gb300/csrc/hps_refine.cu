@@ -23,6 +23,11 @@
 // weights are FP32, and the dot products run in FP32 (weights need few digits;
 // the FP64 pipe is the scarce one).
 //
+// The number of live history slots is a template parameter of both kernels:
+// FP64 instructions of lanes predicated off still occupy the FP64 pipe (2 per
+// clock per SM), so a loop unrolled to the maximum depth with a runtime guard
+// cost the update 8 FP64 FMAs per element for 3 live slots.
+//
 // Reductions are deterministic: every column is cut into fixed chunks of
 // kChunk elements (independent of the other columns), each chunk reduces in a
 // fixed order into its own partial, and the partials of a column are summed
@@ -41,6 +46,7 @@ namespace hps {
 namespace {
 
 constexpr int kThreads = 256;
+static_assert(kAaMaxDepth == 8, "the launch switches below cover depths 0..8");
 
 // max of two non-negative doubles (or NaN patterns with the sign bit clear,
 // which compare above every finite value and +inf) on their bit patterns
@@ -52,7 +58,8 @@ __device__ __forceinline__ long long absbits(double x) {
 }
 
 // One CTA per chunk.  Partials, per chunk: [0] max|F|, [1] max|w|,
-// [2 + s] <dF_s, F>, [2 + kAaMaxDepth + s] <dF_s, dF_new> for s < nslots.
+// [2 + s] <dF_s, F>, [2 + kAaMaxDepth + s] <dF_s, dF_new> for s < nslots (NS).
+template <int NS>
 __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict__ cols,
                                                         const int* __restrict__ col_of,
                                                         const double* __restrict__ F,
@@ -60,16 +67,17 @@ __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict_
                                                         const double* __restrict__ dWlast,
                                                         float* __restrict__ dF,
                                                         double* __restrict__ G, int64_t nu, int j,
-                                                        int slot_new, int nslots,
+                                                        int slot_new,
                                                         double* __restrict__ part) {
+  constexpr int nslots = NS;
   const int64_t b = blockIdx.x;
   const AaCol c = cols[col_of[b]];
   const int64_t e0 = (b - c.ch0) * kAaChunk;
   const int64_t e1 = min(e0 + (int64_t)kAaChunk, c.len);
   long long mf = 0, mw = 0;  // |F|, |w| maxima as bit patterns (exact, NaN-preserving)
-  float accF[kAaMaxDepth], accD[kAaMaxDepth];
+  float accF[NS > 0 ? NS : 1], accD[NS > 0 ? NS : 1];
 #pragma unroll
-  for (int s = 0; s < kAaMaxDepth; ++s) accF[s] = accD[s] = 0.0f;
+  for (int s = 0; s < NS; ++s) accF[s] = accD[s] = 0.0f;
   for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
     const int64_t i = c.off + e;
     const double fv = F[i];
@@ -85,12 +93,10 @@ __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict_
     }
     Fprev[i] = fv;
 #pragma unroll
-    for (int s = 0; s < kAaMaxDepth; ++s) {
-      if (s < nslots) {
-        const float d = (s == slot_new) ? dfn : dF[(int64_t)s * nu + i];
-        accF[s] = fmaf(d, f32, accF[s]);
-        accD[s] = fmaf(d, dfn, accD[s]);
-      }
+    for (int s = 0; s < NS; ++s) {
+      const float d = (s == slot_new) ? dfn : dF[(int64_t)s * nu + i];
+      accF[s] = fmaf(d, f32, accF[s]);
+      accD[s] = fmaf(d, dfn, accD[s]);
     }
   }
   // fixed-order block reduction
@@ -113,8 +119,8 @@ __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict_
   }
 #pragma unroll
   for (int s = 0; s < kAaMaxDepth; ++s) {
-    const double a = warp_sum(accF[s]);
-    const double d = warp_sum(accD[s]);
+    const double a = s < NS ? warp_sum(accF[s < NS ? s : 0]) : 0.0;
+    const double d = s < NS ? warp_sum(accD[s < NS ? s : 0]) : 0.0;
     if (lane == 0) {
       red[wid][2 + s] = a;
       red[wid][2 + kAaMaxDepth + s] = d;
@@ -145,22 +151,23 @@ __global__ void k_aa_colsum(const AaCol* __restrict__ cols, const double* __rest
 }
 
 // coef[c*(kAaMaxDepth+1)]: 0 frozen, 1 accelerated update, 2 plain update
-// (w += F); then gamma_s.
+// (w += F); then gamma_s for the NS live slots.
+template <int NS>
 __global__ void __launch_bounds__(kThreads) k_aa_update(const AaCol* __restrict__ cols,
                                                         const int* __restrict__ col_of,
                                                         const double* __restrict__ F,
                                                         double* __restrict__ dWlast,
                                                         const double* __restrict__ G, int64_t nu,
-                                                        int nslots, const double* __restrict__ coef) {
+                                                        const double* __restrict__ coef) {
   const int64_t b = blockIdx.x;
   const int ci = col_of[b];
   const AaCol c = cols[ci];
   const double* cf = coef + (int64_t)ci * (kAaMaxDepth + 1);
   const int mode = (int)cf[0];
   if (mode == 0) return;
-  double g[kAaMaxDepth];
+  double g[NS > 0 ? NS : 1];
 #pragma unroll
-  for (int s = 0; s < kAaMaxDepth; ++s) g[s] = (mode == 1 && s < nslots) ? cf[1 + s] : 0.0;
+  for (int s = 0; s < NS; ++s) g[s] = mode == 1 ? cf[1 + s] : 0.0;
   const int64_t e0 = (b - c.ch0) * kAaChunk;
   const int64_t e1 = min(e0 + (int64_t)kAaChunk, c.len);
   for (int64_t e = e0 + threadIdx.x; e < e1; e += kThreads) {
@@ -168,8 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_aa_update(const AaCol* __restrict_
     double d = F[i];
     if (mode == 1) {
 #pragma unroll
-      for (int s = 0; s < kAaMaxDepth; ++s)
-        if (s < nslots) d = fma(-g[s], G[(int64_t)s * nu + i], d);
+      for (int s = 0; s < NS; ++s) d = fma(-g[s], G[(int64_t)s * nu + i], d);
       dWlast[i] = d;
     }
     c.w[e] += d;
@@ -188,8 +194,17 @@ void aa_reduce(const AaCol* cols, const int* col_of, int ncol, int64_t nchunks, 
   prof::Scope sc("refine_reduce", st, 4.0 * nslots * (double)nu,
                  (double)nu * (8.0 + 8.0 + 16.0 + (j >= 1 ? 8.0 + 4.0 + 8.0 : 0.0) +
                                4.0 * std::max(nslots - 1, 0)));
-  k_aa_reduce<<<(unsigned)nchunks, kThreads, 0, st>>>(cols, col_of, F, Fprev, dWlast, dF, G, nu, j,
-                                                     slot_new, nslots, part);
+  switch (nslots) {
+#define HPS_AA_REDUCE(NS)                                                                        \
+  case NS:                                                                                       \
+    k_aa_reduce<NS><<<(unsigned)nchunks, kThreads, 0, st>>>(cols, col_of, F, Fprev, dWlast, dF, G, \
+                                                          nu, j, slot_new, part);              \
+    break;
+    HPS_AA_REDUCE(0) HPS_AA_REDUCE(1) HPS_AA_REDUCE(2) HPS_AA_REDUCE(3) HPS_AA_REDUCE(4)
+    HPS_AA_REDUCE(5) HPS_AA_REDUCE(6) HPS_AA_REDUCE(7) HPS_AA_REDUCE(8)
+#undef HPS_AA_REDUCE
+    default: return;  // beyond kAaMaxDepth: rejected by the caller
+  }
   k_aa_colsum<<<(unsigned)ncol, 32, 0, st>>>(cols, part, colsum);
 }
 
@@ -199,8 +214,17 @@ void aa_update(const AaCol* cols, const int* col_of, int ncol, int64_t nchunks, 
   if (ncol <= 0 || nchunks <= 0) return;
   prof::Scope sc("refine_update", st, 2.0 * nslots * (double)nu,
                  (double)nu * (8.0 + 16.0 + 8.0 + 8.0 * nslots));
-  k_aa_update<<<(unsigned)nchunks, kThreads, 0, st>>>(cols, col_of, F, dWlast, G, nu, nslots,
-                                                     coef);
+  switch (nslots) {
+#define HPS_AA_UPDATE(NS)                                                                     \
+  case NS:                                                                                    \
+    k_aa_update<NS><<<(unsigned)nchunks, kThreads, 0, st>>>(cols, col_of, F, dWlast, G, nu, \
+                                                          coef);                            \
+    break;
+    HPS_AA_UPDATE(0) HPS_AA_UPDATE(1) HPS_AA_UPDATE(2) HPS_AA_UPDATE(3) HPS_AA_UPDATE(4)
+    HPS_AA_UPDATE(5) HPS_AA_UPDATE(6) HPS_AA_UPDATE(7) HPS_AA_UPDATE(8)
+#undef HPS_AA_UPDATE
+    default: return;
+  }
 }
 
 }  // namespace hps
