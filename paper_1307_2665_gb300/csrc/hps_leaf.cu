@@ -386,6 +386,9 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
 // r = -(A w_full) at the interior Chebyshev nodes of each leaf, in FP64, from
 // the coefficient samples and D (O(p^3) per leaf and right-hand side):
 //   A w = -c11 Dxx w - 2 c12 Dy (Dx w) - c22 Dyy w + c1 Dx w + c2 Dy w + c w.
+// The leaf's scalings (2/h) and the signs are folded once per leaf into per-node
+// coefficients, so a node's terms combine with one FMA each (the FP64 pipe,
+// 2 per clock per SM, bounds this kernel).
 // Output rbuf[l*ni*nrhs + i + r*ni] in the element type of the correction solve.
 template <typename R>
 __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int p, int rb,
@@ -399,7 +402,8 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   double* D = sm;
   double* D2 = D + pp;
   double* W = D2 + pp;       // rb x pp: w of this block of right-hand sides
-  double* Wx = W + rb * pp;  // rb x pp: Dx w (only with the mixed term)
+  double* Wx = W + rb * pp;  // rb x pp: Dx w, unscaled (only with the mixed term)
+  double* K = Wx + rb * pp;  // 6 x pp: per-node coefficients of the unscaled derivatives
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
   const double* wl = wptr[l];
@@ -413,14 +417,25 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
     D2[e] = s;
   }
   R* rl = rbuf + (size_t)jl * ni * nrhs;
-  const bool has12 = cp.c[1] != nullptr, has1 = cp.c[3] != nullptr, has2 = cp.c[4] != nullptr,
+  const bool has11 = cp.c[0] != nullptr, has12 = cp.c[1] != nullptr,
+             has22 = cp.c[2] != nullptr, has1 = cp.c[3] != nullptr, has2 = cp.c[4] != nullptr,
              has0 = cp.c[5] != nullptr;
-  const double* c11 = cp.c[0] ? cp.c[0] + (size_t)jl * pp : nullptr;
-  const double* c12 = has12 ? cp.c[1] + (size_t)jl * pp : nullptr;
-  const double* c22 = cp.c[2] ? cp.c[2] + (size_t)jl * pp : nullptr;
-  const double* c1 = has1 ? cp.c[3] + (size_t)jl * pp : nullptr;
-  const double* c2 = has2 ? cp.c[4] + (size_t)jl * pp : nullptr;
-  const double* c0 = has0 ? cp.c[5] + (size_t)jl * pp : nullptr;
+  // r = k11 Dxx w + k22 Dyy w + k12 Dy Dx w + k1 Dx w + k2 Dy w + k0 w, D unscaled
+  double* k11 = K;
+  double* k22 = K + pp;
+  double* k12 = K + 2 * pp;
+  double* k1 = K + 3 * pp;
+  double* k2 = K + 4 * pp;
+  double* k0 = K + 5 * pp;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    const size_t g = (size_t)jl * pp + e;
+    k11[e] = has11 ? cp.c[0][g] * sx * sx : 0.0;
+    k22[e] = has22 ? cp.c[2][g] * sy * sy : 0.0;
+    k12[e] = has12 ? 2.0 * cp.c[1][g] * sx * sy : 0.0;
+    k1[e] = has1 ? -cp.c[3][g] * sx : 0.0;
+    k2[e] = has2 ? -cp.c[4][g] * sy : 0.0;
+    k0[e] = has0 ? -cp.c[5][g] : 0.0;
+  }
   // right-hand sides in blocks of rb; threads take (node, right-hand side) pairs
   for (int r0 = 0; r0 < nrhs; r0 += rb) {
     const int nb = min(rb, nrhs - r0);
@@ -434,7 +449,7 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
         const double* Wr = W + (e / pp) * pp;
         double s = 0.0;
         for (int d = 0; d < p; ++d) s = fma(D[b * p + d], Wr[a * p + d], s);
-        Wx[e] = sx * s;
+        Wx[e] = s;
       }
       __syncthreads();
     }
@@ -452,7 +467,6 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
           dx = Wx[rr * pp + node];
         } else {
           for (int k = 0; k < p; ++k) dx = fma(D[b * p + k], Wr[a * p + k], dx);
-          dx *= sx;
         }
       }
       if (has2)
@@ -461,18 +475,14 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
         const double* Wxr = Wx + rr * pp;
         for (int k = 0; k < p; ++k) dxy = fma(D[a * p + k], Wxr[k * p + b], dxy);
       }
-      dxx *= sx * sx;
-      dyy *= sy * sy;
-      dy *= sy;
-      dxy *= sy;
-      double Aw = 0.0;
-      if (c11) Aw -= c11[node] * dxx;
-      if (c22) Aw -= c22[node] * dyy;
-      if (has12) Aw -= 2.0 * c12[node] * dxy;
-      if (has1) Aw += c1[node] * dx;
-      if (has2) Aw += c2[node] * dy;
-      if (has0) Aw += c0[node] * Wr[node];
-      rl[ri + (size_t)(r0 + rr) * ni] = (R)(-Aw);
+      double r = 0.0;
+      if (has11) r = fma(k11[node], dxx, r);
+      if (has22) r = fma(k22[node], dyy, r);
+      if (has12) r = fma(k12[node], dxy, r);
+      if (has1) r = fma(k1[node], dx, r);
+      if (has2) r = fma(k2[node], dy, r);
+      if (has0) r = fma(k0[node], Wr[node], r);
+      rl[ri + (size_t)(r0 + rr) * ni] = (R)r;
     }
   }
 }
@@ -486,9 +496,9 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
   // right-hand sides per block: up to 4, as many as fit next to D and D^2
   const int pp = p * p;
-  const int cap = (int)((200 * 1024 / 8 - 2 * pp) / (2 * pp));
+  const int cap = (int)((200 * 1024 / 8 - 8 * pp) / (2 * pp));
   const int rb = std::max(1, std::min(4, cap));
-  const size_t smem = (size_t)(2 * pp + 2 * rb * pp) * sizeof(double);
+  const size_t smem = (size_t)(8 * pp + 2 * rb * pp) * sizeof(double);
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_residual<R>), 200 * 1024))
     return;  // reported by the caller's launch check
   const double ppd = (double)pp, ni = (double)(p - 2) * (p - 2);
