@@ -399,22 +399,23 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
                                                        R* __restrict__ rbuf) {
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi;
+  const int lp = p + 1;      // padded row pitch of D and D^2: rows walked across threads
   double* D = sm;
-  double* D2 = D + pp;
-  double* W = D2 + pp;       // rb x pp: w of this block of right-hand sides
+  double* D2 = D + p * lp;
+  double* W = D2 + p * lp;   // rb x pp: w of this block of right-hand sides
   double* Wx = W + rb * pp;  // rb x pp: Dx w, unscaled (only with the mixed term)
   double* K = Wx + rb * pp;  // 6 x pp: per-node coefficients of the unscaled derivatives
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
   const double* wl = wptr[l];
   const int64_t wstride = wrs[l];
-  for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) D[(e / p) * lp + e % p] = gD[e];
   __syncthreads();
   for (int e = threadIdx.x; e < pp; e += blockDim.x) {
     int i = e / p, jj = e % p;
     double s = 0.0;
-    for (int k = 0; k < p; ++k) s = fma(D[i * p + k], D[k * p + jj], s);
-    D2[e] = s;
+    for (int k = 0; k < p; ++k) s = fma(D[i * lp + k], D[k * lp + jj], s);
+    D2[i * lp + jj] = s;
   }
   R* rl = rbuf + (size_t)jl * ni * nrhs;
   const bool has11 = cp.c[0] != nullptr, has12 = cp.c[1] != nullptr,
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
         const int node = e % pp, a = node / p, b = node % p;
         const double* Wr = W + (e / pp) * pp;
         double s = 0.0;
-        for (int d = 0; d < p; ++d) s = fma(D[b * p + d], Wr[a * p + d], s);
+        for (int d = 0; d < p; ++d) s = fma(D[b * lp + d], Wr[a * p + d], s);
         Wx[e] = s;
       }
       __syncthreads();
@@ -459,21 +460,21 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
       const double* Wr = W + rr * pp;
       double dxx = 0.0, dyy = 0.0, dx = 0.0, dy = 0.0, dxy = 0.0;
       for (int k = 0; k < p; ++k) {
-        dxx = fma(D2[b * p + k], Wr[a * p + k], dxx);
-        dyy = fma(D2[a * p + k], Wr[k * p + b], dyy);
+        dxx = fma(D2[b * lp + k], Wr[a * p + k], dxx);
+        dyy = fma(D2[a * lp + k], Wr[k * p + b], dyy);
       }
       if (has1) {
         if (has12) {
           dx = Wx[rr * pp + node];
         } else {
-          for (int k = 0; k < p; ++k) dx = fma(D[b * p + k], Wr[a * p + k], dx);
+          for (int k = 0; k < p; ++k) dx = fma(D[b * lp + k], Wr[a * p + k], dx);
         }
       }
       if (has2)
-        for (int k = 0; k < p; ++k) dy = fma(D[a * p + k], Wr[k * p + b], dy);
+        for (int k = 0; k < p; ++k) dy = fma(D[a * lp + k], Wr[k * p + b], dy);
       if (has12) {
         const double* Wxr = Wx + rr * pp;
-        for (int k = 0; k < p; ++k) dxy = fma(D[a * p + k], Wxr[k * p + b], dxy);
+        for (int k = 0; k < p; ++k) dxy = fma(D[a * lp + k], Wxr[k * p + b], dxy);
       }
       double r = 0.0;
       if (has11) r = fma(k11[node], dxx, r);
@@ -496,9 +497,10 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
   // right-hand sides per block: up to 4, as many as fit next to D and D^2
   const int pp = p * p;
-  const int cap = (int)((200 * 1024 / 8 - 8 * pp) / (2 * pp));
+  const int lp = p + 1;
+  const int cap = (int)((200 * 1024 / 8 - 2 * p * lp - 6 * pp) / (2 * pp));
   const int rb = std::max(1, std::min(4, cap));
-  const size_t smem = (size_t)(8 * pp + 2 * rb * pp) * sizeof(double);
+  const size_t smem = (size_t)(2 * p * lp + 6 * pp + 2 * rb * pp) * sizeof(double);
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_residual<R>), 200 * 1024))
     return;  // reported by the caller's launch check
   const double ppd = (double)pp, ni = (double)(p - 2) * (p - 2);
@@ -529,16 +531,18 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
                                                    int64_t ext_total, double* __restrict__ hp) {
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
+  const int lp = p + 1;      // padded row pitch: column walks hit distinct banks
+  const int vs = p * lp;     // one right-hand side's grid
   double* D = sm;
-  double* Pc = D + pp;     // q x p
-  double* V = Pc + q * p;  // rb x pp
-  double* F = V + rb * pp; // rb x 4p
+  double* Pc = D + pp;       // q x p, pitch lp
+  double* V = Pc + q * lp;   // rb x (p x p), pitch lp
+  double* F = V + rb * vs;   // rb x 4p
   const int l = blockIdx.x;  // group-local leaf
   const double sx = hsc[l0 + l].x, sy = hsc[l0 + l].y;
   const double* wl = wptr[l0 + l];
   const int64_t wstride = wrs[l0 + l];
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[e] = gD[e];
-  for (int e = threadIdx.x; e < q * p; e += blockDim.x) Pc[e] = gPc2g[e];
+  for (int e = threadIdx.x; e < q * p; e += blockDim.x) Pc[(e / p) * lp + e % p] = gPc2g[e];
   const R* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
   const int64_t off = leaf_off[l0 + l];
   // right-hand sides in blocks of rb, so every phase keeps the CTA busy
@@ -550,20 +554,20 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
       double v = wl[(size_t)r * wstride + node];
       if (zl && a > 0 && a < p - 1 && b > 0 && b < p - 1)
         v += (double)zl[(a - 1) * pi + (b - 1) + (size_t)r * ni];
-      V[e] = v;
+      V[(e / pp) * vs + a * lp + b] = v;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 4 * p * nb; e += blockDim.x) {
       const int sj = e % (4 * p), s = sj / p, j = sj % p;
-      const double* Vr = V + (e / (4 * p)) * pp;
+      const double* Vr = V + (e / (4 * p)) * vs;
       double acc = 0.0;
       if (s == 0 || s == 2) {
         const int row = (s == 0) ? 0 : p - 1;
-        for (int a = 0; a < p; ++a) acc = fma(D[row * p + a], Vr[a * p + j], acc);
+        for (int a = 0; a < p; ++a) acc = fma(D[row * p + a], Vr[a * lp + j], acc);
         acc *= sy;
       } else {
         const int col = (s == 1) ? p - 1 : 0;
-        for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], Vr[j * p + b], acc);
+        for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], Vr[j * lp + b], acc);
         acc *= sx;
       }
       F[e] = acc;
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
       const int g = e % nq, rr = e / nq, s = g / q, k = g % q;
       const double* Fr = F + rr * 4 * p;
       double acc = 0.0;
-      for (int j = 0; j < p; ++j) acc = fma(Pc[k * p + j], Fr[s * p + j], acc);
+      for (int j = 0; j < p; ++j) acc = fma(Pc[k * lp + j], Fr[s * p + j], acc);
       hp[(size_t)(r0 + rr) * ext_total + off + g] = acc;
     }
   }
@@ -585,9 +589,10 @@ void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int 
                const int64_t* leaf_off, int64_t ext_total, double* hp, cudaStream_t st) {
   if (nl <= 0 || nrhs <= 0) return;
   const int pp = p * p;
-  const int cap = (int)((200 * 1024 / 8 - pp - q * p) / (pp + 4 * p));
+  const int lp = p + 1;
+  const int cap = (int)((200 * 1024 / 8 - pp - q * lp) / (p * lp + 4 * p));
   const int rb = std::max(1, std::min(8, cap));
-  const size_t smem = (size_t)(pp + q * p + rb * (pp + 4 * p)) * sizeof(double);
+  const size_t smem = (size_t)(pp + q * lp + rb * (p * lp + 4 * p)) * sizeof(double);
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_flux<R>), 200 * 1024))
     return;  // reported by the caller's launch check
   prof::Scope sc("leaf_flux<f64>", st, (double)nl * nrhs * (8.0 * p * p + 8.0 * q * p),
