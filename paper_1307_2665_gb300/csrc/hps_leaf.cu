@@ -103,15 +103,39 @@ __global__ void __launch_bounds__(256) k_leaf_assemble(CoefPtrs cp, int l0, int 
     const int a = ri / pi + 1, b = ri % pi + 1, r = a * p + b;
     const double fxx = rf[ri], fx = rf[ni + ri], fyy = rf[2 * ni + ri], fy = rf[3 * ni + ri],
                  fxy = rf[4 * ni + ri];
+    if (!has12) {
+      // a row reaches only the nodes of its own grid row (c == a) and column
+      // (d == b): zeros first, then those entries.  No branch on a node's
+      // position, whose FP64 work would run for every lane of a warp.
+      for (int ci = 0; ci < ni; ++ci) {
+        Al[ri + (size_t)ci * ni] = R(0);
+        if (with_identity)  // columns nq .. nq+ni-1: the identity, so the solve also returns A_ii^{-1}
+          Yl[(size_t)ni * nq + ri + (size_t)ci * ni] = (ri == ci) ? R(1) : R(0);
+      }
+      for (int d = 1; d < p - 1; ++d) {  // c == a
+        double v = fxx * D2[b * p + d] + fx * D[b * p + d];
+        if (d == b) {
+          v += fyy * D2[a * p + a] + fy * D[a * p + a];
+          v += c0[r];
+        }
+        Al[ri + (size_t)((a - 1) * pi + d - 1) * ni] = (R)v;
+      }
+      for (int c = 1; c < p - 1; ++c) {  // d == b, c != a
+        if (c == a) continue;
+        const double v = fyy * D2[a * p + c] + fy * D[a * p + c];
+        Al[ri + (size_t)((c - 1) * pi + b - 1) * ni] = (R)v;
+      }
+      continue;
+    }
     int c = 1, d = 1;
-    for (int ci = 0; ci < ni; ++ci) {
+    for (int ci = 0; ci < ni; ++ci) {  // the mixed term reaches every node
       double v = 0.0;
       if (a == c) v += fxx * D2[b * p + d] + fx * D[b * p + d];
       if (b == d) v += fyy * D2[a * p + c] + fy * D[a * p + c];
-      if (has12) v += fxy * D[a * p + c] * D[b * p + d];
+      v += fxy * D[a * p + c] * D[b * p + d];
       if (a == c && b == d) v += c0[r];
       Al[ri + (size_t)ci * ni] = (R)v;
-      if (with_identity)  // columns nq .. nq+ni-1: the identity, so the solve also returns A_ii^{-1}
+      if (with_identity)
         Yl[(size_t)ni * nq + ri + (size_t)ci * ni] = (ri == ci) ? R(1) : R(0);
       if (++d == p - 1) {
         d = 1;
