@@ -340,46 +340,64 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
       bnd[e] = v;
     }
     __syncthreads();
-    for (int node = threadIdx.x; node < pp; node += blockDim.x) {
-      const int a = node / p, b = node % p;
-      double out[RC];
-      if (a > 0 && a < p - 1 && b > 0 && b < p - 1) {
-        // interior: Y u_e (+ z) in the precision of Y
-        const int ri = (a - 1) * pi + (b - 1);
-        R acc[RC];
+    // interior nodes: Y u_e (+ z) in the precision of Y.  Interior and
+    // boundary nodes run in separate loops, so no warp issues the other
+    // kind's FP64 work for lanes that do not need it.
+    for (int ri = threadIdx.x; ri < ni; ri += blockDim.x) {
+      const int node = (ri / pi + 1) * p + ri % pi + 1;
+      R acc[RC];
 #pragma unroll
-        for (int rr = 0; rr < RC; ++rr) acc[rr] = R(0);
-        for (int g = 0; g < nq; ++g) {
-          const R y = Yl[ri + (size_t)g * ni];
+      for (int rr = 0; rr < RC; ++rr) acc[rr] = R(0);
+      for (int g = 0; g < nq; ++g) {
+        const R y = Yl[ri + (size_t)g * ni];
 #pragma unroll
-          for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(y, uer[g * RC + rr], acc[rr]);
-        }
-        if (zl)
-          for (int rr = 0; rr < nr; ++rr) acc[rr] += zl[ri + (size_t)(r0 + rr) * ni];
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) out[rr] = (double)acc[rr];
-      } else {
-        // boundary: the side value (S row a = 0 and N row a = p-1 indexed by b,
-        // E column b = p-1 and W column b = 0 indexed by a), a corner the mean
-        // of its two sides
-        const int sides[4][2] = {{0, b}, {2, b}, {1, a}, {3, a}};
-        const bool on[4] = {a == 0, a == p - 1, b == p - 1, b == 0};
-        int s1 = -1, s2 = -1;
-        for (int t = 0; t < 4; ++t)
-          if (on[t]) {
-            const int idx = sides[t][0] * p + sides[t][1];
-            if (s1 < 0)
-              s1 = idx;
-            else
-              s2 = idx;
-          }
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr)
-          out[rr] = s2 < 0 ? bnd[s1 * RC + rr] : 0.5 * (bnd[s1 * RC + rr] + bnd[s2 * RC + rr]);
+        for (int rr = 0; rr < RC; ++rr) acc[rr] = fma(y, uer[g * RC + rr], acc[rr]);
       }
+      if (zl)
+        for (int rr = 0; rr < nr; ++rr) acc[rr] += zl[ri + (size_t)(r0 + rr) * ni];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) {
+        if (rr < nr) {
+          double* up = wl + (size_t)(r0 + rr) * wstride + node;
+          double v = (double)acc[rr];
+          if (accumulate) v += *up;
+          *up = v;
+        }
+      }
+    }
+    // boundary nodes: the side value (S row a = 0 and N row a = p-1 indexed by
+    // b, E column b = p-1 and W column b = 0 indexed by a), a corner the mean
+    // of its two sides
+    for (int t = threadIdx.x; t < 4 * (p - 1); t += blockDim.x) {
+      int a, b;
+      if (t < p) {
+        a = 0;
+        b = t;
+      } else if (t < 2 * p) {
+        a = p - 1;
+        b = t - p;
+      } else if (t < 3 * p - 2) {
+        a = t - 2 * p + 1;
+        b = 0;
+      } else {
+        a = t - 3 * p + 3;
+        b = p - 1;
+      }
+      const int node = a * p + b;
+      const int sides[4][2] = {{0, b}, {2, b}, {1, a}, {3, a}};
+      const bool on[4] = {a == 0, a == p - 1, b == p - 1, b == 0};
+      int s1 = -1, s2 = -1;
+      for (int u = 0; u < 4; ++u)
+        if (on[u]) {
+          const int idx = sides[u][0] * p + sides[u][1];
+          if (s1 < 0)
+            s1 = idx;
+          else
+            s2 = idx;
+        }
       for (int rr = 0; rr < nr; ++rr) {
         double* up = wl + (size_t)(r0 + rr) * wstride + node;
-        double v = out[rr];
+        double v = s2 < 0 ? bnd[s1 * RC + rr] : 0.5 * (bnd[s1 * RC + rr] + bnd[s2 * RC + rr]);
         if (accumulate) v += *up;
         *up = v;
       }
