@@ -38,6 +38,9 @@ const char* tname(const char* f64, const char* f32) {
   return sizeof(R) == 8 ? f64 : f32;
 }
 
+// Side visited at slot t of a derivative pass: S, N (d/dy), E, W (d/dx).
+__device__ __forceinline__ int side_order(int t) { return t == 1 ? 2 : (t == 2 ? 1 : t); }
+
 }  // namespace
 
 // One CTA per leaf.
@@ -246,8 +249,9 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
     __syncthreads();
     // Step 3: fluxes at the Chebyshev points of each side
     for (int e = threadIdx.x; e < 4 * p * nc; e += blockDim.x) {
+      // sides in the order S, N, E, W: a warp's lanes take one branch
       const int sj = e % (4 * p), cc = e / (4 * p);
-      const int s = sj / p, j = sj % p;
+      const int s = side_order(sj / p), j = sj % p;
       double acc = 0.0;
       const double* Wc = W + cc * pp;
       if (s == 0 || s == 2) {  // d/dy at node (0 or p-1, j)
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
         for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], Wc[j * p + b], acc);
         acc *= sx;
       }
-      F[sj + cc * 4 * p] = acc;
+      F[s * p + j + cc * 4 * p] = acc;
     }
     __syncthreads();
     // Step 4: Gauss values of each side's flux interpolant
@@ -600,7 +604,8 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 4 * p * nb; e += blockDim.x) {
-      const int sj = e % (4 * p), s = sj / p, j = sj % p;
+      // sides in the order S, N, E, W: a warp's lanes take one branch
+      const int sj = e % (4 * p), s = side_order(sj / p), j = sj % p;
       const double* Vr = V + (e / (4 * p)) * vs;
       double acc = 0.0;
       if (s == 0 || s == 2) {
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(256) k_leaf_flux(double* const* __restrict__ w
         for (int b = 0; b < p; ++b) acc = fma(D[col * p + b], Vr[j * lp + b], acc);
         acc *= sx;
       }
-      F[e] = acc;
+      F[(e / (4 * p)) * 4 * p + s * p + j] = acc;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nq * nb; e += blockDim.x) {
