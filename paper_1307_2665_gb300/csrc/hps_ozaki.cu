@@ -302,7 +302,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
     const bool group_end = (kb % kGroup) == kGroup - 1 || kb == g.nkb - 1;
     // ---- products of block kb (thread 0)
     if (tid == 0 && !pfail) {
-      if (!mbar_wait(&bar_ld[b], par)) pfail = true;
+      // first refill the other stage with block kb + 1, once block kb - 1 (which
+      // used it) has finished multiplying: the copy then runs while block kb's
+      // products execute, however long their issue takes
+      if (kb >= 1 && kb + 1 < g.nkb) {
+        const int ob = (kb - 1) & 1;
+        if (!mbar_wait(&bar_mma[ob], (uint32_t)(((kb - 1) >> 1) & 1))) pfail = true;
+        if (!pfail) load_block(kb + 1);
+      }
+      if (!pfail && !mbar_wait(&bar_ld[b], par)) pfail = true;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!pfail) {
         const uint64_t da0 = smem_desc(smem_u32(stage[b]));
@@ -333,13 +341,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                   smem_u32(&bar_grp))
               : "memory");
-      }
-      // refill the other stage with block kb + 1 once block kb - 1 (which used
-      // it) has finished multiplying
-      if (!pfail && kb >= 1 && kb + 1 < g.nkb) {
-        const int ob = (kb - 1) & 1;
-        if (!mbar_wait(&bar_mma[ob], (uint32_t)(((kb - 1) >> 1) & 1))) pfail = true;
-        if (!pfail) load_block(kb + 1);
       }
       if (pfail) s_fail = 1;
     }
