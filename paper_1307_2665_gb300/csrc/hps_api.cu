@@ -160,6 +160,9 @@ struct Stager {
   }
 };
 
+// Smallest FP32 merge (interface unknowns) whose S is formed as W [-T31 | T32].
+constexpr int kNBw = 32;
+
 // Raw pushes through the stager (callback form for the two-level LU).
 struct StagerCtx {
   Stager* stg;
@@ -338,20 +341,24 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   std::vector<int> hn(nm);
   double gather_bytes = 0.0, schur_flops = 0.0, schur_bytes = 0.0;
   int64_t ot = 0;
-  // Mixed mode, FP64 merges large enough for the tensor cores: the LU solves
-  // for W = (T33^a - T33^b)^{-1} only (identity right-hand side, 2 m^3 flops
-  // instead of 2 m^2 ne) and S = W [-T31^a | T32^b] is one tensor-core product.
-  // An explicit inverse is not backward stable (its residual can be cond times
-  // that of the substitution); the refinement absorbs that, so FP64 mode keeps
-  // the substitution.  [-T31^a | T32^b] is gathered into a temporary.  The
-  // choice depends on the merge's own shape.
-  const bool w_first = H.mixed && sizeof(R) == 8;
+  // Mixed mode: the LU solves for W = (T33^a - T33^b)^{-1} only (identity
+  // right-hand side, 2 m^3 flops instead of 2 m^2 ne) and S = W [-T31^a |
+  // T32^b] is one product: on the tensor cores for FP64 merges large enough,
+  // by the FP32 tile GEMM for FP32 merges.  An explicit inverse is not
+  // backward stable (its residual can be cond times that of the
+  // substitution); the refinement absorbs that, so FP64 mode keeps the
+  // substitution.  [-T31^a | T32^b] is gathered into a temporary.  The choice
+  // depends on the merge's own shape.
+  const bool w_first = H.mixed;
   std::vector<OzDesc> sw;
+  std::vector<GemmDesc<R>> swf;  // FP32: S = W [-T31^a | T32^b] by the tile GEMM
+  double swf_flops = 0.0, swf_bytes = 0.0;
+  int swf_m = 0, swf_n = 0;
   int64_t tmp_tot = 0;
   std::vector<int64_t> tmp_off(nm, -1);
   for (int i = 0; i < nm && w_first; ++i) {
     const MergeShape& sh = pl.shapes[pl.boxes[L.boxes[i]].shape];
-    if (oz_eligible(sh.m, sh.ne, sh.m)) {
+    if (sizeof(R) == 8 ? oz_eligible(sh.m, sh.ne, sh.m) : sh.m >= kNBw) {
       tmp_off[i] = tmp_tot;
       tmp_tot += (int64_t)sh.m * sh.ne;
     }
@@ -391,7 +398,7 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
     lu[i].ldb = sh.m;
     lu[i].box = b;
     hn[i] = lu[i].nrhs;
-    if (wf) {
+    if (wf && sizeof(R) == 8) {
       OzDesc o;
       o.A = reinterpret_cast<const double*>(g.W);
       o.B = reinterpret_cast<const double*>(g.S);
@@ -403,6 +410,22 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
       o.ldb = sh.m;
       o.ldc = sh.m;
       sw.push_back(o);
+    } else if (wf) {
+      GemmDesc<R> q;
+      q.A = g.W;
+      q.B = g.S;
+      q.C = S_final;
+      q.M = sh.m;
+      q.N = sh.ne;
+      q.K = sh.m;
+      q.lda = sh.m;
+      q.ldb = sh.m;
+      q.ldc = sh.m;
+      swf.push_back(q);
+      swf_flops += 2.0 * sh.m * (double)sh.m * sh.ne;
+      swf_bytes += sizeof(R) * ((double)sh.m * sh.m + 2.0 * sh.m * (double)sh.ne);
+      swf_m = std::max(swf_m, sh.m);
+      swf_n = std::max(swf_n, sh.ne);
     }
     gather_bytes += (sizeof(R) + 8.0) *
                     ((double)sh.m * sh.m + 2.0 * sh.m * sh.ne + (tp ? (double)sh.ne * sh.ne : 0.0));
@@ -469,6 +492,12 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
     ow.alloc(wb, st);
     OzDesc* dz = stg.push(sw, st);
     ck(oz_gemm(dz, sw, ow.p, wb, 1.0, 0.0, H.status.as<int>(), st, "gemm_s_tc<f64>"));
+  }
+  if (!swf.empty()) {  // S = W [-T31^a | T32^b], FP32
+    GemmDesc<R>* dg = stg.push(swf, st);
+    gemm_batched<R>(dg, (int)swf.size(), swf_m, swf_n, R(1), R(0), st, "gemm_s<f32>", swf_flops,
+                    swf_bytes);
+    ck(cudaGetLastError());
   }
   // FP64 products large enough go to the tensor cores (exact BF16 splitting);
   // the choice depends on each product's own shape only
@@ -1695,6 +1724,7 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
         if (mixed) sres += (int64_t)sh.ne * sh.m * bm;
         if (B.parent >= 0 || opt.form_root_dtn) t_at[h] += (int64_t)sh.ne * sh.ne * bm;
         tmp_at[h] += (int64_t)sh.m * sh.m * bm + (mixed ? 0 : (int64_t)sh.ne * sh.m * bm);
+        if (bm == 4 && mixed && sh.m >= kNBw) tmp_at[h] += (int64_t)sh.m * sh.ne * 4;  // [-T31 | T32]
         if (bm == 8) {  // tensor-core products: S's temporaries, split operands
           const int64_t m = sh.m, ne = sh.ne, kp = (m + 31) / 32 * 32;
           if (mixed && oz_eligible(sh.m, sh.ne, sh.m))
