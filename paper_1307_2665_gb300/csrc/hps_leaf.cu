@@ -303,7 +303,7 @@ void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const d
 // u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or has it added in
 // FP64 (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior values
 // (ld ni).
-template <typename R>
+template <typename R, int RC>
 __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int64_t ys, int l0,
                                                    const double* __restrict__ uext,
                                                    const int64_t* __restrict__ leaf_off,
@@ -312,7 +312,6 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
                                                    const R* __restrict__ z, int accumulate,
                                                    double* const* __restrict__ wptr,
                                                    const int64_t* __restrict__ wrs) {
-  constexpr int RC = 16;
   extern __shared__ __align__(16) double smd[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
   double* Pg = smd;                               // p x q
@@ -415,17 +414,35 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
                double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z,
                int accumulate) {
   if (nleaves <= 0 || nrhs <= 0) return;
-  const size_t smem = (size_t)(p * q + 4 * q * 16 + 4 * p * 16) * sizeof(double) +
-                      (size_t)4 * q * 16 * sizeof(R);
-  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_post<R>), 200 * 1024))
+  // right-hand sides per block: the smallest power of two covering nrhs, at most
+  // 16 (padded columns would still run their FMAs; per column the arithmetic
+  // does not depend on the block width)
+  const int rc = nrhs >= 16 ? 16 : nrhs > 4 ? (nrhs > 8 ? 16 : 8) : nrhs > 2 ? 4 : nrhs;
+  const size_t smem = (size_t)(p * q + 4 * q * rc + 4 * p * rc) * sizeof(double) +
+                      (size_t)4 * q * rc * sizeof(R);
+  auto opt = [](const void* k) { return opt_in_smem(k, 200 * 1024); };
+  if (!opt(reinterpret_cast<const void*>(&k_leaf_post<R, 1>)) ||
+      !opt(reinterpret_cast<const void*>(&k_leaf_post<R, 2>)) ||
+      !opt(reinterpret_cast<const void*>(&k_leaf_post<R, 4>)) ||
+      !opt(reinterpret_cast<const void*>(&k_leaf_post<R, 8>)) ||
+      !opt(reinterpret_cast<const void*>(&k_leaf_post<R, 16>)))
     return;  // reported by the caller's launch check
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
   prof::Scope sc(tname<R>("leaf_post<f64>", "leaf_post<f32>"), st,
                  (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
                  (double)nleaves * (ni * nq * sizeof(R) +
                                     nrhs * (nq + (double)p * p * (accumulate ? 2 : 1)) * 8.0));
-  k_leaf_post<R><<<nleaves, 256, smem, st>>>(Y, ys, l0, uext, leaf_ext_off, ext_total, p, q, nrhs,
-                                             d_Pg2c, z, accumulate, wptr, wrs);
+#define HPS_LEAF_POST(RC)                                                                     \
+  k_leaf_post<R, RC><<<nleaves, 256, smem, st>>>(Y, ys, l0, uext, leaf_ext_off, ext_total, p, q, \
+                                                 nrhs, d_Pg2c, z, accumulate, wptr, wrs)
+  switch (rc) {
+    case 1: HPS_LEAF_POST(1); break;
+    case 2: HPS_LEAF_POST(2); break;
+    case 4: HPS_LEAF_POST(4); break;
+    case 8: HPS_LEAF_POST(8); break;
+    default: HPS_LEAF_POST(16); break;
+  }
+#undef HPS_LEAF_POST
 }
 
 // ------------------------------------------------------------ FP64 residual
