@@ -416,12 +416,15 @@ __global__ void __launch_bounds__(512) k_lu_panel(const LuDesc<R>* __restrict__ 
 // panel's rows split into kPanelCl slices, each staged in its CTA's shared
 // memory, so the rank-1 updates of a column run on kPanelCl SMs (FP64 FMAs are
 // 2 per clock per SM: one SM bounds a tall panel).  Per column: every CTA
-// offers its best row (largest |value|, ties to the smaller row), all read the
-// kPanelCl offers over distributed shared memory and take the same pivot; a
-// swap reads both rows before a cluster barrier and writes them after it; the
-// pivot row is read by every CTA and each updates its own rows.  Same pivots,
+// offers its best row (pivot key, row, value), one lane per CTA reads the
+// offers over distributed shared memory and the lanes reduce them by shuffles,
+// so all CTAs take the same pivot and form the same reciprocal; every CTA
+// reads the pivot row, the owner of the pivot row also reads row jj, and after
+// one cluster barrier (only when rows are interchanged) the two owners write
+// the rows back swapped.  A thread owns the same rows in the argmax and in the
+// update, so no block barrier separates them.  Same pivots, same reciprocal,
 // same FMAs in the same order per element: the factors equal k_lu_panel's bit
-// for bit.  Cluster barriers: one per column, three when rows are swapped, and
+// for bit.  Cluster barriers: one per column, two when rows are swapped, and
 // one before exit (no CTA leaves while others may still read its memory).
 constexpr int kPanelCl = 8;
 
@@ -441,8 +444,9 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
   extern __shared__ __align__(16) unsigned char smraw[];
   R* P = reinterpret_cast<R*>(smraw);  // own rows r0..r1-1 (relative to k0), column-major, ld chunk
   using Key = PivotKey<R>;
-  __shared__ Key cand_v[2];  // this CTA's offer per column parity (pivot key)
+  __shared__ Key cand_v[2];  // this CTA's offer per column parity: pivot key, row, value
   __shared__ int cand_i[2];
+  __shared__ R cand_x[2];
   __shared__ Key red_v[8];
   __shared__ int red_i[8];
   __shared__ int s_piv;
@@ -460,7 +464,8 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
     const int par = jj & 1;
     Key best = -1;
     int bi = jj;
-    for (int i = max(jj, r0) + threadIdx.x; i < r1; i += blockDim.x) {
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      if (i < jj) continue;
       const Key v = pivot_key(P[(i - r0) + jj * chunk]);
       if (v > best) {
         best = v;
@@ -491,60 +496,71 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
         }
       cand_v[par] = bv;
       cand_i[par] = bx;
+      // the offered row's value (any own row when this CTA has none left)
+      cand_x[par] = bv >= 0 ? P[(bx - r0) + jj * chunk] : R(0);
     }
     cl.sync();  // offers visible
-    if (threadIdx.x == 0) {
+    if (wid == 0) {  // lane r reads rank r's offer; the 8 lanes reduce
       Key bv = -1;
-      int bx = jj;
-      for (int r = 0; r < kPanelCl; ++r) {
-        const Key v = *cl.map_shared_rank(&cand_v[par], r);
-        const int x = *cl.map_shared_rank(&cand_i[par], r);
-        if (v > bv || (v == bv && x < bx)) {
-          bv = v;
-          bx = x;
+      int bx = 0x7fffffff;
+      R xv = R(0);
+      if (lane < kPanelCl) {
+        bv = *cl.map_shared_rank(&cand_v[par], lane);
+        bx = *cl.map_shared_rank(&cand_i[par], lane);
+        xv = *cl.map_shared_rank(&cand_x[par], lane);
+      }
+#pragma unroll
+      for (int o = kPanelCl / 2; o > 0; o >>= 1) {
+        const Key ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ox = __shfl_xor_sync(0xffffffffu, bx, o);
+        const R oxv = __shfl_xor_sync(0xffffffffu, xv, o);
+        if (ov > bv || (ov == bv && ox < bx)) {
+          bv = ov;
+          bx = ox;
+          xv = oxv;
         }
       }
-      s_piv = bx;
-      if (rank == 0) D.ipiv[k0 + jj] = k0 + bx;
+      if (lane == 0) {
+        // a CTA without rows >= jj offers key -1, which every real row beats
+        s_piv = bx;
+        if (rank == 0) D.ipiv[k0 + jj] = k0 + bx;
+        const bool bad = !(xv != R(0)) || !isfinite(xv);
+        if (bad && rank == 0 && status) atomicCAS(status, 0, D.box + 1);
+        s_inv = bad ? R(0) : R(1) / xv;
+      }
     }
     __syncthreads();
     const int piv = s_piv;
     const int og = jj / chunk;  // owner of row jj
+    const int op = piv / chunk;  // owner of the pivot row
+    R vg = R(0), vp = R(0);
+    if (threadIdx.x < nbk) {
+      const int c = threadIdx.x;
+      vp = cl.map_shared_rank(P, op)[(piv - op * chunk) + c * chunk];
+      prow[c] = vp;  // the pivot row becomes row jj
+      if (piv != jj && rank == op) vg = cl.map_shared_rank(P, og)[(jj - og * chunk) + c * chunk];
+    }
     if (piv != jj) {  // the same decision in every CTA
-      const int op = piv / chunk;
-      R vg = R(0), vp = R(0);
-      if (threadIdx.x < nbk) {
-        const int c = threadIdx.x;
-        if (rank == og) vp = cl.map_shared_rank(P, op)[(piv - op * chunk) + c * chunk];
-        if (rank == op) vg = cl.map_shared_rank(P, og)[(jj - og * chunk) + c * chunk];
-      }
-      cl.sync();  // both rows read before either is written
+      cl.sync();  // both rows read everywhere before either is written
       if (threadIdx.x < nbk) {
         const int c = threadIdx.x;
         if (rank == og) P[(jj - r0) + c * chunk] = vp;
         if (rank == op) P[(piv - r0) + c * chunk] = vg;
       }
-      cl.sync();  // swapped rows visible
-    }
-    if (threadIdx.x < nbk)
-      prow[threadIdx.x] = cl.map_shared_rank(P, og)[(jj - og * chunk) + threadIdx.x * chunk];
-    __syncthreads();
-    if (threadIdx.x == 0) {  // the reciprocal once per CTA
-      const R pv = prow[jj];
-      const bool bad = !(pv != R(0)) || !isfinite(pv);
-      if (bad && rank == 0 && status) atomicCAS(status, 0, D.box + 1);
-      s_inv = bad ? R(0) : R(1) / pv;
     }
     __syncthreads();
     const R inv = s_inv;
-    for (int i = max(jj + 1, r0) + threadIdx.x; i < r1; i += blockDim.x) {
+    for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      if (i <= jj) continue;
       const int li = i - r0;
       R l = P[li + jj * chunk] * inv;
       P[li + jj * chunk] = l;
       for (int c = jj + 1; c < nbk; ++c) P[li + c * chunk] = fma(-l, prow[c], P[li + c * chunk]);
     }
-    __syncthreads();
+    // no block barrier: each thread's rows are its own in the next argmax,
+    // and prow / the offers are rewritten only after the next barriers
   }
+  __syncthreads();
   for (int e = threadIdx.x; e < nown * nbk; e += blockDim.x) {
     const int i = e % nown, c = e / nown;
     A0[(r0 + i) + (size_t)c * D.lda] = P[i + c * chunk];
@@ -553,8 +569,9 @@ __global__ void __cluster_dims__(kPanelCl, 1, 1) __launch_bounds__(256)
 }
 
 // One panel launch: a cluster per matrix for tall panels of few matrices (the
-// top merges; below 512 rows the cluster barriers cost what the spread saves),
-// else one CTA per matrix.  Both give the same factors.
+// top merges), from 256 rows in FP64 and 512 in FP32 (below, the cluster
+// barriers cost what spreading the FMAs saves), else one CTA per matrix.  Both
+// give the same factors.
 template <typename R>
 bool launch_panel(const LuDesc<R>* d_desc, int nd, int max_m, int k0, int* d_status,
                   cudaStream_t st, double fl, double by) {
@@ -564,7 +581,7 @@ bool launch_panel(const LuDesc<R>* d_desc, int nd, int max_m, int k0, int* d_sta
   const long long cl_bytes = (long long)chunk * std::min(kNB, rows) * (long long)sizeof(R);
   prof::Scope sc(TName<R>::panel(), st, fl, by);
   // the opt-in is cached per kernel: always ask for the same (largest) size
-  if (rows >= 512 && nd <= 32) {
+  if (rows >= (sizeof(R) == 8 ? 256 : 512) && nd <= 32) {
     if (cl_bytes <= smem_max &&
       opt_in_smem(reinterpret_cast<const void*>(&k_lu_panel_cl<R>), smem_max)) {
       k_lu_panel_cl<R><<<(unsigned)(nd * kPanelCl), 256, (size_t)cl_bytes, st>>>(d_desc, k0,
