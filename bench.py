@@ -245,11 +245,7 @@ def alu_peak_tflops(name, sm_mhz):
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the same kernel's launch in the same workload step; a kernel
 # changed since its capture has no entry.
-TRAFFIC_PER_LAUNCH = {
-    # first refinement launch of the 64x64 convection-diffusion step, 16 RHS
-    # (profiles/leaf_residual_convdiff64.md): 167.9 MB read + 32.2 MB written
-    ("convdiff64", "leaf_residual<f64>"): 200134912,
-}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def roofline_of(stats, t_total_ms, sm_mhz, workload=None):

@@ -450,10 +450,16 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
 // the coefficient samples and D (O(p^3) per leaf and right-hand side):
 //   A w = -c11 Dxx w - 2 c12 Dy (Dx w) - c22 Dyy w + c1 Dx w + c2 Dy w + c w.
 // The leaf's scalings (2/h) and the signs are folded once per leaf into per-node
-// coefficients, so a node's terms combine with one FMA each (the FP64 pipe,
-// 2 per clock per SM, bounds this kernel).
+// coefficients (the FP64 pipe, 2 per clock per SM, bounds this kernel).  With
+// kMerged, the second- and first-order terms of a direction, which act on the
+// same grid line, are merged once per leaf into one row per interior node:
+// Mx(node, k) = k11 D2(b, k) + k1 D(b, k), My(node, k) = k22 D2(a, k) + k2 D(a, k);
+// each right-hand side then costs p FMAs per direction and node instead of 2p
+// (the rows take 2 p (p-2)^2 doubles of shared memory, so the host merges only
+// when both orders are present and the rows fit).  The mixed term goes
+// through Dx w at every node.
 // Output rbuf[l*ni*nrhs + i + r*ni] in the element type of the correction solve.
-template <typename R>
+template <typename R, bool kMerged>
 __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int p, int rb,
                                                        const double2* __restrict__ hsc,
                                                        const double* __restrict__ gD,
@@ -467,7 +473,8 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   double* D2 = D + p * lp;
   double* W = D2 + p * lp;   // rb x pp: w of this block of right-hand sides
   double* Wx = W + rb * pp;  // rb x pp: Dx w, unscaled (only with the mixed term)
-  double* K = Wx + rb * pp;  // 6 x pp: per-node coefficients of the unscaled derivatives
+  double* K = Wx + rb * pp;  // merged: 2 x ni (k12, k0 per interior node), then Mx, My
+                             // (p x ni each, k-major); else 6 x pp per-node coefficients
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
   const double* wl = wptr[l];
@@ -484,21 +491,42 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   const bool has11 = cp.c[0] != nullptr, has12 = cp.c[1] != nullptr,
              has22 = cp.c[2] != nullptr, has1 = cp.c[3] != nullptr, has2 = cp.c[4] != nullptr,
              has0 = cp.c[5] != nullptr;
-  // r = k11 Dxx w + k22 Dyy w + k12 Dy Dx w + k1 Dx w + k2 Dy w + k0 w, D unscaled
-  double* k11 = K;
-  double* k22 = K + pp;
-  double* k12 = K + 2 * pp;
-  double* k1 = K + 3 * pp;
-  double* k2 = K + 4 * pp;
-  double* k0 = K + 5 * pp;
-  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
-    const size_t g = (size_t)jl * pp + e;
-    k11[e] = has11 ? cp.c[0][g] * sx * sx : 0.0;
-    k22[e] = has22 ? cp.c[2][g] * sy * sy : 0.0;
-    k12[e] = has12 ? 2.0 * cp.c[1][g] * sx * sy : 0.0;
-    k1[e] = has1 ? -cp.c[3][g] * sx : 0.0;
-    k2[e] = has2 ? -cp.c[4][g] * sy : 0.0;
-    k0[e] = has0 ? -cp.c[5][g] : 0.0;
+  const bool hasx = has11 || has1, hasy = has22 || has2;
+  double* Mx = K + 2 * ni;
+  double* My = Mx + p * ni;
+  if constexpr (kMerged) {
+    // r = Mx w + My w + k12 Dy Dx w + k0 w, D unscaled
+    __syncthreads();  // D2 complete
+    for (int e = threadIdx.x; e < ni * p; e += blockDim.x) {
+      const int ri = e % ni, k = e / ni;
+      const int a = ri / pi + 1, b = ri % pi + 1;
+      const size_t g = (size_t)jl * pp + a * p + b;
+      if (hasx) {
+        const double k11 = has11 ? cp.c[0][g] * sx * sx : 0.0;
+        const double k1 = has1 ? -cp.c[3][g] * sx : 0.0;
+        Mx[e] = fma(k1, D[b * lp + k], k11 * D2[b * lp + k]);
+      }
+      if (hasy) {
+        const double k22 = has22 ? cp.c[2][g] * sy * sy : 0.0;
+        const double k2 = has2 ? -cp.c[4][g] * sy : 0.0;
+        My[e] = fma(k2, D[a * lp + k], k22 * D2[a * lp + k]);
+      }
+      if (k == 0) {
+        K[ri] = has12 ? 2.0 * cp.c[1][g] * sx * sy : 0.0;
+        K[ni + ri] = has0 ? -cp.c[5][g] : 0.0;
+      }
+    }
+  } else {
+    // r = k11 Dxx w + k22 Dyy w + k12 Dy Dx w + k1 Dx w + k2 Dy w + k0 w, D unscaled
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+      const size_t g = (size_t)jl * pp + e;
+      K[e] = has11 ? cp.c[0][g] * sx * sx : 0.0;
+      K[pp + e] = has22 ? cp.c[2][g] * sy * sy : 0.0;
+      K[2 * pp + e] = has12 ? 2.0 * cp.c[1][g] * sx * sy : 0.0;
+      K[3 * pp + e] = has1 ? -cp.c[3][g] * sx : 0.0;
+      K[4 * pp + e] = has2 ? -cp.c[4][g] * sy : 0.0;
+      K[5 * pp + e] = has0 ? -cp.c[5][g] : 0.0;
+    }
   }
   // right-hand sides in blocks of rb; threads take (node, right-hand side) pairs
   for (int r0 = 0; r0 < nrhs; r0 += rb) {
@@ -521,31 +549,43 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
       const int ri = e % ni, rr = e / ni;
       const int a = ri / pi + 1, b = ri % pi + 1, node = a * p + b;
       const double* Wr = W + rr * pp;
-      double dxx = 0.0, dyy = 0.0, dx = 0.0, dy = 0.0, dxy = 0.0;
-      for (int k = 0; k < p; ++k) {
-        dxx = fma(D2[b * lp + k], Wr[a * p + k], dxx);
-        dyy = fma(D2[a * lp + k], Wr[k * p + b], dyy);
-      }
-      if (has1) {
-        if (has12) {
-          dx = Wx[rr * pp + node];
-        } else {
-          for (int k = 0; k < p; ++k) dx = fma(D[b * lp + k], Wr[a * p + k], dx);
-        }
-      }
-      if (has2)
-        for (int k = 0; k < p; ++k) dy = fma(D[a * lp + k], Wr[k * p + b], dy);
+      double dxy = 0.0;
       if (has12) {
         const double* Wxr = Wx + rr * pp;
         for (int k = 0; k < p; ++k) dxy = fma(D[a * lp + k], Wxr[k * p + b], dxy);
       }
       double r = 0.0;
-      if (has11) r = fma(k11[node], dxx, r);
-      if (has22) r = fma(k22[node], dyy, r);
-      if (has12) r = fma(k12[node], dxy, r);
-      if (has1) r = fma(k1[node], dx, r);
-      if (has2) r = fma(k2[node], dy, r);
-      if (has0) r = fma(k0[node], Wr[node], r);
+      if constexpr (kMerged) {
+        double sxv = 0.0, syv = 0.0;
+        if (hasx)
+          for (int k = 0; k < p; ++k) sxv = fma(Mx[k * ni + ri], Wr[a * p + k], sxv);
+        if (hasy)
+          for (int k = 0; k < p; ++k) syv = fma(My[k * ni + ri], Wr[k * p + b], syv);
+        r = sxv + syv;
+        if (has12) r = fma(K[ri], dxy, r);
+        if (has0) r = fma(K[ni + ri], Wr[node], r);
+      } else {
+        double dxx = 0.0, dyy = 0.0, dx = 0.0, dy = 0.0;
+        for (int k = 0; k < p; ++k) {
+          dxx = fma(D2[b * lp + k], Wr[a * p + k], dxx);
+          dyy = fma(D2[a * lp + k], Wr[k * p + b], dyy);
+        }
+        if (has1) {
+          if (has12) {
+            dx = Wx[rr * pp + node];
+          } else {
+            for (int k = 0; k < p; ++k) dx = fma(D[b * lp + k], Wr[a * p + k], dx);
+          }
+        }
+        if (has2)
+          for (int k = 0; k < p; ++k) dy = fma(D[a * lp + k], Wr[k * p + b], dy);
+        if (has11) r = fma(K[node], dxx, r);
+        if (has22) r = fma(K[pp + node], dyy, r);
+        if (has12) r = fma(K[2 * pp + node], dxy, r);
+        if (has1) r = fma(K[3 * pp + node], dx, r);
+        if (has2) r = fma(K[4 * pp + node], dy, r);
+        if (has0) r = fma(K[5 * pp + node], Wr[node], r);
+      }
       rl[ri + (size_t)(r0 + rr) * ni] = (R)r;
     }
   }
@@ -558,24 +598,46 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
   if (nl <= 0 || nrhs <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
-  // right-hand sides per block: up to 4, as many as fit next to D and D^2
   const int pp = p * p;
   const int lp = p + 1;
-  const int cap = (int)((200 * 1024 / 8 - 2 * p * lp - 6 * pp) / (2 * pp));
-  const int rb = std::max(1, std::min(4, cap));
-  const size_t smem = (size_t)(2 * p * lp + 6 * pp + 2 * rb * pp) * sizeof(double);
-  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_residual<R>), 200 * 1024))
-    return;  // reported by the caller's launch check
-  const double ppd = (double)pp, ni = (double)(p - 2) * (p - 2);
-  // FP64 flops actually issued: Dxx, Dyy at the interior nodes, plus the terms
-  // of the coefficients present (Dx w everywhere only for the mixed term)
-  double per = 4.0 * ni * p;
-  if (coef[1]) per += 2.0 * ppd * p + 2.0 * ni * p;
-  else if (coef[3]) per += 2.0 * ni * p;
-  if (coef[4]) per += 2.0 * ni * p;
-  prof::Scope sc("leaf_residual<f64>", st, (double)nl * nrhs * per,
-                 (double)nl * (nrhs * (ppd * 8.0 + ni * sizeof(R)) + 6.0 * ppd * 8.0));
-  k_leaf_residual<R><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs, nrhs, rbuf);
+  const int ni = (p - 2) * (p - 2);
+  constexpr int kCap = 200 * 1024 / 8;  // doubles of shared memory
+  // merged rows when a direction has both orders and they fit beside D, D^2
+  // and one right-hand side
+  const int fixed_m = 2 * p * lp + 2 * ni + 2 * p * ni;
+  const bool merged = ((coef[0] && coef[3]) || (coef[2] && coef[4])) && fixed_m + 2 * pp <= kCap;
+  // right-hand sides per block: up to 4, as many as fit
+  const int fixed = merged ? fixed_m : 2 * p * lp + 6 * pp;
+  const int rb = std::max(1, std::min(4, (kCap - fixed) / (2 * pp)));
+  const size_t smem = (size_t)(fixed + 2 * rb * pp) * sizeof(double);
+  const void* kern = merged ? reinterpret_cast<const void*>(&k_leaf_residual<R, true>)
+                            : reinterpret_cast<const void*>(&k_leaf_residual<R, false>);
+  if (!opt_in_smem(kern, 200 * 1024)) return;  // reported by the caller's launch check
+  const double ppd = (double)pp, nid = (double)ni;
+  // FP64 flops actually issued per leaf and right-hand side: merged, p FMAs
+  // per direction present and interior node (plus the rows once per leaf);
+  // else Dxx and Dyy always and Dx, Dy for the first-order terms present; the
+  // mixed term adds Dx w everywhere and Dy of it at the interior nodes
+  const bool hx = coef[0] || coef[3], hy = coef[2] || coef[4];
+  double per, once = 2.0 * p * ppd;  // D^2
+  if (merged) {
+    per = 2.0 * ((hx ? 1 : 0) + (hy ? 1 : 0)) * nid * p + nid;
+    once += 3.0 * ((hx ? 1 : 0) + (hy ? 1 : 0)) * nid * p;
+    if (coef[1]) per += 2.0 * ppd * p + 2.0 * nid * p + 2.0 * nid;
+  } else {
+    per = 4.0 * nid * p;
+    if (coef[1]) per += 2.0 * ppd * p + 2.0 * nid * p;
+    else if (coef[3]) per += 2.0 * nid * p;
+    if (coef[4]) per += 2.0 * nid * p;
+  }
+  prof::Scope sc("leaf_residual<f64>", st, (double)nl * (nrhs * per + once),
+                 (double)nl * (nrhs * (ppd * 8.0 + nid * sizeof(R)) + 6.0 * ppd * 8.0));
+  if (merged)
+    k_leaf_residual<R, true><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs, nrhs,
+                                                    rbuf);
+  else
+    k_leaf_residual<R, false><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs, nrhs,
+                                                     rbuf);
 }
 
 // ------------------------------------------------- flux offsets of the leaves
