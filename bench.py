@@ -233,6 +233,24 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------ ranks
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job's time); the identity on one rank."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(world, units_per_rank, steps, t_ms):
+    """Whole-job throughput: the units all ranks processed (each rank the same
+    count, its own independent input) over the slowest rank's time."""
+    return world * units_per_rank * steps / (t_ms / 1e3)
+
+
 # ---------------------------------------------------------------- native
 # ALU peaks of a GB300 at a given SM clock: FP64 is 2 DFMA per SM per clock
 # (measured 1.198 TFLOP/s with 152 SMs at 1987 MHz), FP32 128 FFMA per SM per
@@ -377,10 +395,7 @@ def run_native(args):
         launches = hps.hps_kernel_launches() - launches0
         stats = hps.hps_profile_read()
         hps.hps_profile_enable(False)
-        if world > 1:
-            t = torch.tensor([t_build, t_solve], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_build, t_solve = t.tolist()
+        t_build, t_solve = max_over_ranks([t_build, t_solve], dist, dev)
         results[mname] = {"t_build": t_build, "t_solve": t_solve, "iters": iters, "stats": stats,
                           "launches": launches, "u": [u.clone() for u in run.u_d]}
     clocks = sampler.stop() if rank == 0 else None
@@ -406,10 +421,7 @@ def run_native(args):
         stream.synchronize()
         t_e2e += e0.elapsed_time(e1)
         h.close()
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = t.item()
+    t_e2e, = max_over_ranks([t_e2e], dist, dev)
     assert all(np.isfinite(u).all() for u in u_h)
     rel_diff = None
     if "mixed" in results and "fp64" in results:
@@ -424,9 +436,9 @@ def run_native(args):
 
     def summary(r):
         tt = r["t_build"] + r["t_solve"]
-        return {"dof_per_s": world * W.dof * args.steps / (tt / 1e3),
-                "build_dof_per_s": world * W.dof * args.steps / (r["t_build"] / 1e3),
-                "solves_per_s": world * W.nrhs * len(W.probs) * args.steps / (r["t_solve"] / 1e3),
+        return {"dof_per_s": job_rate(world, W.dof, args.steps, tt),
+                "build_dof_per_s": job_rate(world, W.dof, args.steps, r["t_build"]),
+                "solves_per_s": job_rate(world, W.nrhs * len(W.probs), args.steps, r["t_solve"]),
                 "build_ms": r["t_build"] / args.steps, "solve_ms": r["t_solve"] / args.steps,
                 "refine_iterations": r["iters"],
                 "gpu_launches": int(r["launches"] // args.steps),
@@ -447,7 +459,7 @@ def run_native(args):
             "build_dof_per_s": H["build_dof_per_s"], "solves_per_s": H["solves_per_s"],
             "build_ms": H["build_ms"], "solve_ms": H["solve_ms"],
             "clocks": clocks, "gpu_launches": H["gpu_launches"],
-            "e2e": {"value": world * W.dof * e2e_steps / (t_e2e / 1e3), "unit": "DOF/s",
+            "e2e": {"value": job_rate(world, W.dof, e2e_steps, t_e2e), "unit": "DOF/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "roofline": H["roofline"]}
     if "fp64" in summ and head != "fp64":

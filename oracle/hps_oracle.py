@@ -28,7 +28,7 @@ oracle writes that system out and solves it by sparse LU:
 Non-zero F and G (a body load and a flux jump) are not in the paper; they are
 the right-hand sides of the correction equation of iterative refinement.
 
-Readings where the paper is silent or garbled (listed in the design doc as well):
+Readings where the paper is silent or garbled:
   * Chebyshev nodes are the p extreme (Lobatto) points, so the boundary holds
     4(p-1) nodes and the interior (p-2)^2 (Section 3.1).
   * "Gaussian nodes" are Gauss-Legendre points.
@@ -46,7 +46,9 @@ the edge system); it is pinned to `solve_global` in the tests and is used where
 the assembled system is too large.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py
-(closed forms, invariants, brute force, the paper's printed Table 3 values).
+(closed forms, invariants, brute force, and the node counts N and N_tot that
+Tables 1 and 3 print).  The point values of Table 3 are not reproduced by the
+problems as Section 9.2 states them, so none of them serves as a pin.
 """
 from __future__ import annotations
 
