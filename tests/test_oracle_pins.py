@@ -4,6 +4,8 @@ Each test names what it pins and why a plausible mistake in the oracle (a
 dropped term, a wrong sign, a transposed operand, a wrong scaling, a wrong
 corner rule) would fail it.  No value here comes from the CUDA path.
 """
+from pathlib import Path
+
 import numpy as np
 import pytest
 import scipy.special
@@ -11,6 +13,7 @@ import scipy.special
 from oracle import hps_oracle as O
 from paper_1307_2665_gb300 import inputs as I
 
+GOLDEN = Path(__file__).resolve().parent / "golden"
 UNIT = (0.0, 1.0, 0.0, 1.0)
 SKEW = (-0.3, 0.9, 0.1, 1.7)  # hx != hy on every grid below
 
@@ -55,13 +58,21 @@ def test_interp_matrix_exact_and_cardinal():
 
 # ---------------------------------------------------------------- P7 counting
 def test_node_counts_match_tables():
-    """Tables 1 and 3 print N and N_tot for q = p = 21; N = 2n(n+1)q and
-    N_tot = N + (n(p-1)+1)^2 reproduce every pair."""
-    rows = [(16, 11424, 114465), (32, 44352, 455233), (64, 174720, 1815681),
-            (128, 693504, 7252225), (256, 2763264, 28987905), (512, 11031552, 115909633)]
-    for n, N, Ntot in rows:
-        assert O.gauss_count(n, 21) == N
-        assert O.total_count(n, 21, 21) == Ntot
+    """Tables 1 and 3 print N and N_tot for q = p = 21 (tests/golden/
+    node_counts_tables_1_3.txt).  Each N is 2n(n+1)q for an integer n, and
+    N_tot = N + (n(p-1)+1)^2 for that n: the oracle's counting convention
+    (Gauss nodes on every leaf edge, Chebyshev nodes shared between leaves)
+    reproduces every printed pair."""
+    rows = []
+    for ln in (GOLDEN / "node_counts_tables_1_3.txt").read_text().splitlines():
+        if ln.strip() and not ln.startswith("#"):
+            ntot, n_gauss, _src = ln.split()
+            rows.append((int(ntot), int(n_gauss)))
+    assert len(rows) == 9
+    for Ntot, N in rows:
+        n = int(round((-1 + np.sqrt(1 + 4 * N / (2 * 21))) / 2))
+        assert O.gauss_count(n, 21) == N, (N, n)
+        assert O.total_count(n, 21, 21) == Ntot, (Ntot, n)
     # the oracle's own numbering agrees with the formula
     pr = O.Problem(UNIT, 5, 5, 21, 21, {})
     assert O.EdgeNumbering(pr).N == O.gauss_count(5, 21)
