@@ -97,8 +97,9 @@ def gauss_points(q):
 
 def interp_matrix(src, dst):
     """Lagrange interpolation: row i evaluates at dst[i] the polynomial of degree
-    < len(src) through values at src.  Written as V_dst V_src^{-1} in the
-    Legendre basis."""
+    < len(src) through values at src (the re-tabulations of Section 3.2, Steps 1
+    and 4, between a side's Gauss and Chebyshev nodes).  Written as
+    V_dst V_src^{-1} in the Legendre basis."""
     n = len(src)
     Vs = npleg.legvander(np.asarray(src), n - 1)
     Vd = npleg.legvander(np.asarray(dst), n - 1)
@@ -134,7 +135,8 @@ class Problem:
 
 
 def cheb_grid(domain, nx, ny, p):
-    """Coordinates of every leaf's p x p Chebyshev grid: shape (ny*nx, p, p, 2)."""
+    """Coordinates of every leaf's p x p Chebyshev grid (Section 3.1, the
+    tensor grid of a leaf): shape (ny*nx, p, p, 2)."""
     x0, x1, y0, y1 = domain
     hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
     t = (cheb_points(p) + 1.0) / 2.0
@@ -193,8 +195,8 @@ class EdgeNumbering:
         return xy
 
     def leaf_sides(self, ix, iy):
-        """The leaf's 4q exterior Gauss nodes, sides S, E, N, W, each in
-        increasing coordinate."""
+        """The leaf's 4q exterior Gauss nodes (its index set I_e, Section 2),
+        sides S, E, N, W, each in increasing coordinate."""
         return np.concatenate([self.h(iy, ix), self.v(ix + 1, iy),
                                self.h(iy + 1, ix), self.v(ix, iy)])
 
@@ -210,7 +212,7 @@ class EdgeNumbering:
         return b
 
     def gamma_order(self):
-        """Global ids of the boundary nodes counter-clockwise from (x0, y0):
+        """Global ids of the Gauss nodes on Gamma (eq. basic), counter-clockwise from (x0, y0):
         south (increasing x), east (increasing y), north (decreasing x),
         west (decreasing y).  This is the order of the Dirichlet data f."""
         pr = self.prob
@@ -222,7 +224,7 @@ class EdgeNumbering:
 
 
 def boundary_points(prob: Problem):
-    """Coordinates of the Dirichlet nodes on Gamma in the order of f."""
+    """Coordinates of the Dirichlet nodes on Gamma (eq. basic) in the order of f."""
     en = EdgeNumbering(prob)
     return en.coords()[en.gamma_order()]
 
@@ -324,13 +326,17 @@ def _as2d(a, rows):
 
 @dataclass
 class Solution:
-    """w_full on every leaf: (nrhs, n_leaves, p, p); u at all Gauss nodes (N, nrhs)."""
+    """w_full on every leaf (the Chebyshev values of Section 3.1):
+    (nrhs, n_leaves, p, p); u at all Gauss nodes (Section 2): (N, nrhs)."""
     w: np.ndarray
     u_gauss: np.ndarray
 
 
 def solve_global(prob: Problem, f, F=None, G=None, dense=False):
-    """Assemble (E1, E2) and solve.  f: Dirichlet data in gamma order, (nbnd,) or
+    """Assemble (E1, E2) and solve: E1 is the collocation condition of Section
+    3.1 (eq. A_interior) at every leaf's interior nodes, E2 the flux continuity
+    v3^alpha = v3^beta of Section 4 that eq. U_parent solves, at every interior
+    Gauss node.  f: Dirichlet data in gamma order, (nbnd,) or
     (nbnd, nrhs).  F: body load at interior Chebyshev nodes, (n_leaves, (p-2)^2,
     nrhs) or None.  G: flux jumps at the interior Gauss nodes, indexed by global
     Gauss id, (N, nrhs) or None (boundary entries ignored)."""
@@ -384,7 +390,8 @@ def solve_global(prob: Problem, f, F=None, G=None, dense=False):
     Gb = None if G is None else _as2d(G, en.N)
 
     def flux_rows(l, side):
-        """Rows of flux = F w_full on one side, as (coeffs on u_e, coeffs on w_i)."""
+        """Rows of flux = F w_full on one side (Section 3.2, Steps 3-4), as
+        (coeffs on u_e, coeffs on w_i)."""
         Fs = ops.F[side * q:(side + 1) * q]
         return Fs @ ops.L1, Fs[:, ops.Ji]
 
@@ -545,7 +552,8 @@ def leaf_dtn(prob: Problem, l=0):
 
 
 def residual(prob: Problem, sol: Solution, f, F=None, G=None):
-    """FP64 residual of (E1, E2) for a candidate solution, matrix-free.
+    """FP64 residual of (E1, E2) (Section 3.1 eq. A_interior; Section 4 flux
+    continuity) for a candidate solution, matrix-free.
 
     Returns (r1, r2): r1[l, i, rhs] = F_i - (A w_full)_i at each leaf's interior
     Chebyshev nodes; r2[k, rhs] = G_k - (flux^alpha - flux^beta)_k at each
@@ -652,7 +660,8 @@ def sampled_residual(prob: Problem, w, f, leaves):
 
 
 def point_values(prob: Problem, w, x, y, tol=1e-12):
-    """Values of the per-leaf solution w (n_leaves, p, p) at the point (x, y)
+    """Values of the per-leaf solution w (n_leaves, p, p) (Section 5.3: the
+    solution on every leaf's Chebyshev grid) at the node (x, y)
     from every leaf whose Chebyshev grid contains it (a leaf corner belongs to
     up to four leaves, whose corner values may differ at discretisation level)."""
     xy = cheb_grid(prob.domain, prob.nx, prob.ny, prob.p)
@@ -705,15 +714,17 @@ def boundary_flux(prob: Problem, w):
 
 
 def dtn_apply(prob: Problem, f):
-    """T^1 f for Dirichlet data f (nrhs, nbnd): the boundary fluxes of the
-    global system's solution (sparse LU, solve_global)."""
+    """T^1 f for Dirichlet data f (nrhs, nbnd), T^1 the DtN map of the whole
+    domain (the root map of Algorithm 1; Section 9.1 times it as T_apply): the
+    boundary fluxes of the global system's solution (sparse LU, solve_global)."""
     f = np.atleast_2d(np.asarray(f, np.float64))
     sol, _, _ = solve_global(prob, f.T)
     return boundary_flux(prob, sol.w)
 
 
 def lagrange_basis(nodes, t):
-    """Values at t of the Lagrange polynomials of the nodes, in product form:
+    """Values at t of the Lagrange polynomials of the nodes (the leaf
+    interpolant of Section 5.3), in product form:
     l_j(t) = prod_{k != j} (t - t_k) / (t_j - t_k)."""
     nodes = np.asarray(nodes, np.float64)
     out = np.ones(len(nodes))
@@ -761,7 +772,8 @@ def total_count(n, p, q):
 
 
 def make_problem(domain, nx, ny, p, q, coeff_fn):
-    """Sample coeff_fn(x, y) -> dict at this oracle's own Chebyshev grid."""
+    """Sample coeff_fn(x, y) -> dict of the coefficients of eq. defA at this
+    oracle's own Chebyshev grid (the collocation nodes of Section 3.1)."""
     xy = cheb_grid(domain, nx, ny, p)
     coeffs = coeff_fn(xy[..., 0], xy[..., 1])
     return Problem(domain=tuple(domain), nx=nx, ny=ny, p=p, q=q,
