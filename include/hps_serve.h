@@ -77,12 +77,16 @@ int hps_server_destroy(hps_server s);
 
 /* Queue a build of one problem (host coefficient arrays, copied here; the
  * options' device_ptrs and stream are ignored).  Returns the request id,
- * which is also the operator id, or a negative status. */
+ * which is also the operator id, or a negative status: HPS_ENOMEM when the
+ * build's estimated peak (hps_estimate_bytes) exceeds hbm_budget, since it
+ * could never start. */
 int64_t hps_server_submit_build(hps_server s, const hps_problem* prob, const hps_options* opt);
 
 /* Queue a solve on operator `op` of nrhs data sets f (host, nrhs * nbnd in
  * the layout of hps_solve, copied here).  Returns the request id or a
- * negative status (HPS_EINVAL for an unknown operator). */
+ * negative status (HPS_EINVAL for an unknown operator).  A solve whose
+ * workspace and result do not fit in hbm_budget next to its own resident
+ * operator completes with HPS_ENOMEM instead of waiting. */
 int64_t hps_server_submit_solve(hps_server s, int64_t op, const double* f, int nrhs);
 
 /* Wait until request `req` completes or timeout_s seconds pass (< 0: no

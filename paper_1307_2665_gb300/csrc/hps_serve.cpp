@@ -37,6 +37,7 @@ enum OpState { kPending, kBuilding, kReady, kFailed, kEvicted };
 struct Result {
   void* p = nullptr;
   int64_t bytes = 0;
+  int holders = 0;  // requests not yet released that share it (guarded by the server mutex)
   cudaStream_t free_stream = nullptr;
   ~Result() {
     if (p) cudaFreeAsync(p, free_stream);
@@ -194,6 +195,14 @@ bool pick(hps_server_s& S, Job& job) {
       total -= S.reqs.at(S.queue[idx.back()])->nrhs;
       idx.pop_back();
     }
+    if (idx.size() == 1 && o.resident + need(total) > S.opt.hbm_budget) {
+      // too large even with everything else evicted and released: it can never start
+      o.queued -= 1;
+      complete(S, r, HPS_ENOMEM);
+      S.queue.erase(S.queue.begin() + qi);
+      S.cv_done.notify_all();
+      continue;
+    }
     if (S.used + need(total) > S.opt.hbm_budget && !make_room(S, need(total), o.id)) {
       ++qi;
       continue;
@@ -290,6 +299,7 @@ void run_solve(hps_server_s& S, Job& job, cudaStream_t ws) {
     if (res) {
       r->res = res;
       r->res_off = r0 * op->dof;
+      res->holders += 1;
     }
     r0 += r->nrhs;
     std::vector<double>().swap(r->f);
@@ -449,6 +459,7 @@ int64_t hps_server_submit_build(hps_server S, const hps_problem* prob, const hps
   int64_t peak = 0, resident = 0, work = 0;
   const int est = hps_estimate_bytes(prob, 1, &r->opt, 1, &peak, &resident, &work);
   if (est != HPS_OK) return est;
+  if (peak > S->opt.hbm_budget) return HPS_ENOMEM;  // could never start
   r->est_peak = peak;
   const int64_t n = (int64_t)prob->nx * prob->ny * prob->p * prob->p;
   const double* c[6] = {prob->c11, prob->c12, prob->c22, prob->c1, prob->c2, prob->c};
@@ -533,7 +544,7 @@ int hps_server_release(hps_server S, int64_t req) {
   auto it = S->reqs.find(req);
   if (it == S->reqs.end() || it->second->status == 1) return HPS_EINVAL;
   auto& res = it->second->res;
-  if (res && res.use_count() == 1) S->used -= res->bytes;
+  if (res && --res->holders == 0) S->used -= res->bytes;
   S->reqs.erase(it);
   S->cv_work.notify_all();
   return HPS_OK;

@@ -105,3 +105,31 @@ def test_admission_evicts_idle_operators():
     st = srv.stats()
     assert st["evicted_ops"] >= 1 and st["peak_bytes_in_use"] <= st["budget"]
     srv.close()
+
+
+def test_work_that_can_never_fit_is_refused():
+    """A build whose estimated peak exceeds the budget is refused when it is
+    submitted, and a solve too large to sit beside its own resident operator
+    completes with HPS_ENOMEM; neither waits for memory that can never come,
+    and the server keeps serving what fits."""
+    pr = problem(8, 12, I.laplace)
+    peak, res, work = hps.hps_estimate_bytes([pr], nrhs=1)
+    srv = hps.Server(hbm_budget=int(peak // 2), workers=1)
+    try:
+        with pytest.raises(hps.HpsError) as e:
+            srv.submit_build(pr)
+        assert e.value.status == hps.HPS_ENOMEM
+    finally:
+        srv.close()
+    srv = hps.Server(hbm_budget=int(peak + 4096), workers=1)
+    try:
+        a = srv.submit_build(pr)
+        assert srv.wait(a).status == hps.HPS_OK
+        dof = pr["nx"] * pr["ny"] * pr["p"] ** 2
+        nbig = int((peak + 4096) // (8 * dof)) + 2  # its result alone exceeds the budget
+        big = srv.submit_solve(a, data(pr, nbig, 0))
+        assert srv.wait(big, timeout=60.0).status == hps.HPS_ENOMEM
+        ok = srv.submit_solve(a, data(pr, 2, 0))
+        assert srv.wait(ok, timeout=60.0).status == hps.HPS_OK
+    finally:
+        srv.close()
