@@ -86,44 +86,60 @@ def _problem(hps, I, dom, nx, ny, p, q, fn, nrhs, seed0):
     return dict(domain=dom, nx=nx, ny=ny, p=p, q=q, coeffs=co, f=f)
 
 
-def make_workload(name, leaves, rank):
-    from paper_1307_2665_gb300 import hps
-    from paper_1307_2665_gb300 import inputs as I
+def describe_workload(name, leaves, rank=0):
+    """The workload's description (the JSON line's `config` core), its
+    right-hand sides per problem and, for batch64, each problem's (n, p); no
+    arrays are sampled, so both arms can name the same workload."""
     if name == "convdiff64":
         n = leaves or 64
         nrhs = 16
-        pr = _problem(hps, I, UNIT_SQ, n, n, 16, 14, I.convection_diffusion, nrhs, nrhs * rank)
         desc = {"workload": f"convection-diffusion c1=-100cos(4pi y), c2=100sin(4pi x) on [0,1]^2, "
                             f"{n}x{n} leaves, p=16, q=14, {nrhs} RHS (20-mode Fourier data), "
                             f"build+solve", "leaves": f"{n}x{n}", "p": 16, "q": 14}
-        return Workload(name, desc, [pr], nrhs, I.convection_diffusion)
+        return desc, nrhs, [(n, 16)]
     if name == "helmholtz256":
         n = leaves or 256
         nrhs = 64
-        pr = _problem(hps, I, UNIT_SQ, n, n, 16, 14, I.gaussian_bump_helmholtz, nrhs, nrhs * rank)
         desc = {"workload": f"variable-speed Helmholtz -Lap u - 80^2 (1 - 0.5 exp(-|x-c|^2/0.02)) u = 0 "
                             f"on [0,1]^2, {n}x{n} leaves, p=16, q=14, {nrhs} RHS (20-mode Fourier "
                             f"data), build+solve", "leaves": f"{n}x{n}", "p": 16, "q": 14}
-        return Workload(name, desc, [pr], nrhs, I.gaussian_bump_helmholtz)
+        return desc, nrhs, [(n, 16)]
     if name == "batch64":
         nprob = 64
         nmax = leaves or 128
         nrhs = 16
         rng = np.random.Generator(np.random.PCG64(20240 + rank))
-        probs = []
-        for k in range(nprob):
+        shapes = []
+        for _ in range(nprob):
             n = int(round(np.exp(rng.uniform(np.log(8), np.log(nmax)))))
-            p = int(rng.choice([12, 16, 20]))
-            seed = 1000 * rank + k
-            fn = (lambda s: (lambda x, y: I.random_smooth_operator(s, x, y)))(seed)
-            probs.append(_problem(hps, I, UNIT_SQ, n, n, p, p - 2, fn, nrhs, 100 * seed))
+            shapes.append((n, int(rng.choice([12, 16, 20]))))
         desc = {"workload": f"{nprob} independent problems, n x n leaves with n log-uniform in "
                             f"[8, {nmax}], p in {{12, 16, 20}}, q = p - 2, random smooth c11, c22, "
                             f"c12, c1, c2 (c = 0), {nrhs} RHS each, one batched build+solve",
-                "sizes": [pr["nx"] for pr in probs], "orders": [pr["p"] for pr in probs]}
-        return Workload(name, desc, probs, nrhs,
-                        lambda x, y: I.random_smooth_operator(0, x, y))
+                "sizes": [n for n, _ in shapes], "orders": [p for _, p in shapes]}
+        return desc, nrhs, shapes
     raise ValueError(name)
+
+
+def make_workload(name, leaves, rank):
+    from paper_1307_2665_gb300 import hps
+    from paper_1307_2665_gb300 import inputs as I
+    desc, nrhs, shapes = describe_workload(name, leaves, rank)
+    if name == "convdiff64":
+        (n, _), = shapes
+        pr = _problem(hps, I, UNIT_SQ, n, n, 16, 14, I.convection_diffusion, nrhs, nrhs * rank)
+        return Workload(name, desc, [pr], nrhs, I.convection_diffusion)
+    if name == "helmholtz256":
+        (n, _), = shapes
+        pr = _problem(hps, I, UNIT_SQ, n, n, 16, 14, I.gaussian_bump_helmholtz, nrhs, nrhs * rank)
+        return Workload(name, desc, [pr], nrhs, I.gaussian_bump_helmholtz)
+    # batch64
+    probs = []
+    for k, (n, p) in enumerate(shapes):
+        seed = 1000 * rank + k
+        fn = (lambda s: (lambda x, y: I.random_smooth_operator(s, x, y)))(seed)
+        probs.append(_problem(hps, I, UNIT_SQ, n, n, p, p - 2, fn, nrhs, 100 * seed))
+    return Workload(name, desc, probs, nrhs, lambda x, y: I.random_smooth_operator(0, x, y))
 
 
 # ---------------------------------------------------------------- clocks
@@ -222,8 +238,9 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample_leaves": f"{n}x{n}", "p": 16, "q": 14,
-                       "nrhs": 16},
+            "config": dict(describe_workload(args.workload, args.leaves)[0],
+                           sample=f"oracle on {n}x{n} leaves of the workload's coefficient "
+                                  f"field, p=16, q=14, 16 RHS per step"),
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": os.cpu_count(),
                              "kind": "oracle",
                              "sample": f"{n}x{n} leaves of the workload's field per step"},

@@ -101,3 +101,7 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     assert line["value"] > 0 and line["unit"] == "DOF/s"
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    # the same workload name as the native arm's line
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert line["config"]["workload"] == bench.describe_workload("convdiff64", 0)[0]["workload"]
