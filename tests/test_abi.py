@@ -110,3 +110,32 @@ def test_server_without_device_fails_cleanly():
     with pytest.raises(hps.HpsError) as e:
         hps.Server()
     assert e.value.status == hps.HPS_EDEVICE
+
+
+def _declarations():
+    """(return type, name, parameter count) of every function the headers declare."""
+    out = []
+    for hdr in sorted((ROOT / "include").glob("*.h")):
+        txt = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
+        for ret, name, params in re.findall(
+                r"^\s*((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**)\s*(hps_[a-z_]+)\s*\(([^)]*)\)\s*;",
+                txt, flags=re.M):
+            params = " ".join(params.split())
+            n = 0 if params in ("", "void") else params.count(",") + 1
+            out.append((" ".join(ret.split()), name, n))
+    return out
+
+
+def test_binding_types_match_the_headers():
+    """Every ctypes prototype of the binding has the header's return type
+    (an int64_t result left at ctypes' default int would be truncated) and its
+    number of parameters."""
+    decls = _declarations()
+    assert {d[1] for d in decls} == set(hps.EXPORTS)
+    ret_map = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "void": None,
+               "const char*": ctypes.c_char_p, "const char *": ctypes.c_char_p}
+    L = hps.lib()
+    for ret, name, n in decls:
+        fn = getattr(L, name)
+        assert fn.restype is ret_map[ret], (name, ret, fn.restype)
+        assert fn.argtypes is not None and len(fn.argtypes) == n, (name, n, fn.argtypes)
