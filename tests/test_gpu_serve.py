@@ -121,12 +121,13 @@ def test_work_that_can_never_fit_is_refused():
         assert e.value.status == hps.HPS_ENOMEM
     finally:
         srv.close()
-    srv = hps.Server(hbm_budget=int(peak + 4096), workers=1)
+    budget = int(peak + res)  # room for the build, then for the operator and small solves
+    srv = hps.Server(hbm_budget=budget, workers=1)
     try:
         a = srv.submit_build(pr)
         assert srv.wait(a).status == hps.HPS_OK
         dof = pr["nx"] * pr["ny"] * pr["p"] ** 2
-        nbig = int((peak + 4096) // (8 * dof)) + 2  # its result alone exceeds the budget
+        nbig = budget // (8 * dof) + 2  # its result alone exceeds the budget
         big = srv.submit_solve(a, data(pr, nbig, 0))
         assert srv.wait(big, timeout=60.0).status == hps.HPS_ENOMEM
         ok = srv.submit_solve(a, data(pr, 2, 0))
