@@ -280,6 +280,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
   for (int j = 0; j < 32; ++j) uhi[j] = ulo[j] = 0;
   bool gfail = false;
   bool pfail = false;  // thread 0 only
+  // thread 0 only: blocks whose copies / products were issued, and how many of
+  // each are known complete (what a failed CTA must still wait for)
+  int ld_issued = 0, ld_done = 0, mma_issued = 0, mma_done = 0;
 
   auto load_block = [&](int kb) {  // thread 0: all slices of block kb into stage kb & 1
     const int b = kb & 1;
@@ -290,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
               (uint32_t)(kS * kABlock * 2), &bar_ld[b]);
     bulk_load(Bs, work + g.b_off + ((int64_t)tn * g.nkb + kb) * kS * kBBlock,
               (uint32_t)(kS * kBBlock * 2), &bar_ld[b]);
+    ++ld_issued;
   };
   if (tid == 0) {
     load_block(0);
@@ -308,9 +312,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
       if (kb >= 1 && kb + 1 < g.nkb) {
         const int ob = (kb - 1) & 1;
         if (!mbar_wait(&bar_mma[ob], (uint32_t)(((kb - 1) >> 1) & 1))) pfail = true;
+        else mma_done = kb;  // products complete in issue order
         if (!pfail) load_block(kb + 1);
       }
       if (!pfail && !mbar_wait(&bar_ld[b], par)) pfail = true;
+      if (!pfail) ld_done = kb + 1;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (!pfail) {
         const uint64_t da0 = smem_desc(smem_u32(stage[b]));
@@ -336,6 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&bar_mma[b]))
             : "memory");
+        mma_issued = kb + 1;
         if (group_end)
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -349,6 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
       const uint32_t gpar = (uint32_t)((kb / kGroup) & 1);
       const bool ok = !gfail && __all_sync(0xffffffffu, mbar_wait(&bar_grp, gpar));
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (ok && tid == 0) mma_done = kb + 1;
       if (ok) {
 #pragma unroll 1
         for (int dd = 2; dd <= kS + 1; ++dd) {
@@ -402,8 +410,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(const OzDesc* __restric
         *cp = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *cp);
       }
     }
-  } else if (tid == 0 && status) {
-    atomicCAS(status, 0, -1);  // a wait gave up: reported as a device error
+  } else if (tid == 0) {
+    // a wait gave up: before this CTA's shared and tensor memory are released,
+    // let its own copies and products still in flight finish (each wait is
+    // bounded again), then report a device error
+    for (int j = ld_done; j < ld_issued; ++j) mbar_wait(&bar_ld[j & 1], (uint32_t)((j >> 1) & 1));
+    for (int j = mma_done; j < mma_issued; ++j)
+      mbar_wait(&bar_mma[j & 1], (uint32_t)((j >> 1) & 1));
+    if (status) atomicCAS(status, 0, -1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
