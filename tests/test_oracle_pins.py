@@ -56,6 +56,40 @@ def test_interp_matrix_exact_and_cardinal():
         assert np.max(np.abs(Q @ t ** k - g ** k)) < 1e-12
 
 
+# ------------------------------------------------------- Step 1 and its corners
+@pytest.mark.parametrize("p,q", [(12, 10), (9, 9), (16, 14)])
+def test_step1_sides_and_averaged_corners(p, q):
+    """Section 3.2, Step 1: each side's q Gauss values define the polynomial of
+    degree q-1 through them, evaluated at the side's p Chebyshev points, and a
+    corner takes the mean of its two sides' values.  The side data here are
+    random, so the two sides disagree at every corner and only the averaging
+    rule passes (taking one side's value, or summing, fails).  The reference
+    values come from SciPy's barycentric interpolator, not the oracle's
+    Legendre-Vandermonde route.  Interior rows of L1 are zero."""
+    from scipy.interpolate import BarycentricInterpolator
+    ops = O.LeafOps(p, q, 0.3, 0.7)
+    tc = O.cheb_points(p)
+    tg, _ = O.gauss_points(q)
+    rng = np.random.default_rng(p * 100 + q)
+    ue = rng.standard_normal(4 * q)
+    w = (ops.L1 @ ue).reshape(p, p)  # w[a, b], a along y, b along x
+    side = {name: BarycentricInterpolator(tg, ue[k * q:(k + 1) * q])(tc)
+            for k, name in enumerate("SENW")}
+    ref = np.zeros((p, p))
+    ref[0, :] = side["S"]        # y = -1, along x
+    ref[:, p - 1] = side["E"]    # x = +1, along y
+    ref[p - 1, :] = side["N"]    # y = +1, along x
+    ref[:, 0] = side["W"]        # x = -1, along y
+    ref[0, 0] = 0.5 * (side["S"][0] + side["W"][0])
+    ref[0, p - 1] = 0.5 * (side["S"][p - 1] + side["E"][0])
+    ref[p - 1, p - 1] = 0.5 * (side["N"][p - 1] + side["E"][p - 1])
+    ref[p - 1, 0] = 0.5 * (side["N"][0] + side["W"][p - 1])
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(w - ref)) < 1e-12 * scale
+    # the two sides really disagree at the corners
+    assert abs(side["S"][0] - side["W"][0]) > 1e-3
+
+
 # ---------------------------------------------------------------- P7 counting
 def test_node_counts_match_tables():
     """Tables 1 and 3 print N and N_tot for q = p = 21 (tests/golden/
