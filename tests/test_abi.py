@@ -103,6 +103,30 @@ def test_estimate_bytes_host_only():
         hps.hps_estimate_bytes([dict(pr, q=17)])
 
 
+def _s_entries(nx, ny, q):
+    """Entries of S summed over the merges of an nx x ny leaf grid: the tree
+    splits a box's longer side at floor(n/2) (ties: x), and a merge's S is
+    m x n_e with m the shared edge's Gauss nodes and n_e the parent's exterior."""
+    if nx == 1 and ny == 1:
+        return 0
+    if nx >= ny:
+        m, kids = ny * q, [(nx // 2, ny), (nx - nx // 2, ny)]
+    else:
+        m, kids = nx * q, [(nx, ny // 2), (nx, ny - ny // 2)]
+    return m * 2 * (nx + ny) * q + sum(_s_entries(x, y, q) for x, y in kids)
+
+
+@pytest.mark.parametrize("nx,ny,p,q", [(64, 64, 16, 14), (7, 3, 12, 10), (1, 5, 8, 6)])
+def test_resident_estimate_is_s_plus_y(nx, ny, p, q):
+    """An FP64 handle keeps S of every merge (eq. U_parent) and Y of every leaf
+    (eq. leaf_solve, (p-2)^2 x 4q), plus index maps of a few percent at most:
+    the plan's estimate agrees with a count made here from the tree alone."""
+    pr = dict(domain=(0, 1, 0, 1), nx=nx, ny=ny, p=p, q=q, coeffs={})
+    _, res, _ = hps.hps_estimate_bytes([pr], nrhs=1)
+    sy = 8 * (_s_entries(nx, ny, q) + nx * ny * (p - 2) ** 2 * 4 * q)
+    assert sy <= res <= 1.02 * sy + 65536, (res, sy)
+
+
 def test_server_without_device_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
