@@ -293,7 +293,7 @@ def roofline_of(stats, t_total_ms, sm_mhz, workload=None):
             "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get((workload, name)),
             "peak_source": f"{'FP64 DFMA' if per == FP64_DFMA_PER_SM_CLK else 'FP32 FFMA'}: "
                            f"{N_SM} SMs x {per}/clk x 2 flop x {sm_mhz:.0f} MHz (max SM clock; "
-                           f"per-clock rate measured by an FMA probe on this pool)",
+                           f"per-clock rate measured on a GB300 by an FMA throughput probe)",
             "flops_per_launch": per_launch_flops, "launches": st["launches"],
             "ms_per_launch": per_launch_s * 1e3, "share_of_step": st["ms"] / max(t_total_ms, 1e-9)}
 
