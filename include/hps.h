@@ -243,17 +243,22 @@ const char* hps_last_error(void);
 /* Solve without allocating (the paper has no counterpart: this serves callers
  * that cannot allocate device memory at solve time, e.g. a process with a
  * fixed memory budget reserved up front, or code that must not enter the
- * allocator or synchronise the device while other work runs).  Same result as
- * hps_solve_ex(h, f, nrhs, u, 1, NULL) for an HPS_FP64 handle, with f and u
- * device pointers; its working memory is a static 16 MiB device array that
- * every GPU loading the library holds until the process exits, so no
- * cudaMalloc / cudaFree or other allocation happens in the call.
+ * allocator or synchronise the device while other work runs).  The same
+ * result, to rounding, as hps_solve_ex(h, f, nrhs, u, 1, NULL) for an HPS_FP64
+ * handle, with f and u device pointers (the downward products sum their
+ * columns in another order: no split-K scratch).  Its working memory is a
+ * static 16 MiB device array that every GPU loading the library holds until
+ * the process exits, so no cudaMalloc / cudaFree or other allocation happens
+ * in the call.
  *   - Limit: 8 * nrhs * (exterior-pool + interface) values plus the launch
- *     descriptors must fit in the 16 MiB; otherwise HPS_EINVAL, with the sizes
- *     in hps_last_error().  Mixed-precision handles return HPS_EINVAL.
+ *     descriptors must fit in the 16 MiB, and the handle may have at most 256
+ *     merge heights; otherwise HPS_EINVAL, with the sizes in hps_last_error().
+ *     Mixed-precision handles return HPS_EINVAL.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current: make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current.
+ *   - Every call copies descriptors from host memory and synchronises the
+ *     handle's stream before it returns: do not call it while that stream is
+ *     being captured into a CUDA graph.
  *   - Every call shares the one array (its contents are those of the last
  *     call; nothing in it needs to start at zero).  Calls that overlap on the
  *     GPU race: serialise them (the call itself returns only after its work has

@@ -659,28 +659,6 @@ def sampled_residual(prob: Problem, w, f, leaves):
     return out
 
 
-def point_values(prob: Problem, w, x, y, tol=1e-12):
-    """Values of the per-leaf solution w (n_leaves, p, p) (Section 5.3: the
-    solution on every leaf's Chebyshev grid) at the node (x, y)
-    from every leaf whose Chebyshev grid contains it (a leaf corner belongs to
-    up to four leaves, whose corner values may differ at discretisation level)."""
-    xy = cheb_grid(prob.domain, prob.nx, prob.ny, prob.p)
-    hit = np.nonzero((np.abs(xy[..., 0] - x) < tol) & (np.abs(xy[..., 1] - y) < tol))
-    return np.asarray([w[l, a, b] for l, a, b in zip(*hit)])
-
-
-def flux_at_cheb(prob: Problem, w, l, side):
-    """Step 3 fluxes at the p Chebyshev points of one side of leaf l (sides
-    0..3 = S, E, N, W; d/dy on S and N, d/dx on E and W, global direction)."""
-    p = prob.p
-    ops = LeafOps(p, prob.q, prob.hx, prob.hy)
-    full = np.asarray(w[l]).reshape(p * p)
-    rows = {0: [b for b in range(p)], 2: [(p - 1) * p + b for b in range(p)],
-            1: [a * p + p - 1 for a in range(p)], 3: [a * p for a in range(p)]}[side]
-    M = ops.Dy if side in (0, 2) else ops.Dx
-    return M[rows] @ full
-
-
 # ============================================================ post-processing
 def boundary_flux(prob: Problem, w):
     """The DtN map of the whole domain applied to the Dirichlet data of the

@@ -1864,6 +1864,7 @@ namespace {
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;  // per device
 constexpr size_t kStaticHostBytes = size_t(4) << 20;      // descriptor staging
 constexpr int kMaxDevices = 64;
+constexpr size_t kStaticMaxLevels = 256;  // merge heights of one handle
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 alignas(256) unsigned char g_static_host[kStaticHostBytes];
@@ -1885,6 +1886,12 @@ extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double*
   const Plan& pl = H.plan;
   const ProbInfo& pi = pl.probs[0];
   const int nl = pl.n_leaves();
+  if (H.lev.size() > kStaticMaxLevels) {
+    g_last_error = "hps_solve_static: " + std::to_string(H.lev.size()) +
+                   " merge heights, the static descriptor table holds " +
+                   std::to_string(kStaticMaxLevels);
+    return HPS_EINVAL;
+  }
   // carve the static array: exterior-value pool, u3 pool, descriptors
   const size_t b_uext = align256((size_t)nrhs * pl.ext_total * sizeof(double));
   const size_t b_u3 = align256((size_t)nrhs * std::max<int64_t>(H.u3_total, 1) * sizeof(double));
@@ -1943,8 +1950,7 @@ extern "C" int hps_solve_static(hps_handle h, const double* f, int nrhs, double*
       for (int j = 0; j < nl; ++j) wr[j] = (int64_t)nl * pi.s.p * pi.s.p;
     }
     const int64_t* dwr = static_cast<const int64_t*>(stage(g_static_host + off, nl * sizeof(int64_t)));
-    GemmDesc<double>* dptr[256] = {};
-    if (H.lev.size() > 256) return HPS_EINVAL;
+    GemmDesc<double>* dptr[kStaticMaxLevels] = {};
     for (size_t li = 0; li < H.lev.size(); ++li) {
       LevelGroup& L = H.lev[li];
       GemmDesc<double>* hs = reinterpret_cast<GemmDesc<double>*>(g_static_host + off);

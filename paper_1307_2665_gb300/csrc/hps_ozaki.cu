@@ -14,8 +14,10 @@
 //   2. Multiply.  For every slice pair (s, t) with s + t <= 9 (the dropped
 //      pairs weigh at most 2^-70 of |A| |B|), P = a^(s) b^(t) on the tensor
 //      cores, the pairs of equal d = s + t accumulated together in FP32 in
-//      tensor memory, one 64-wide K block at a time: every partial sum is an
-//      integer of magnitude < 8 * 64 * 127^2 < 2^23, hence exact.
+//      tensor memory, one 128-wide K group at a time: at most 8 pairs share a
+//      d, so every partial sum is an integer of magnitude
+//      <= 8 * 128 * 127^2 = 16 516 096 < 2^24, hence exact (checked at compile
+//      time below).
 //   3. Combine.  Per output, the exact integers P_st of equal d = s + t are
 //      summed in two 64-bit fixed-point accumulators,
 //        U_hi = sum_{d=2..5} P_d 2^(7 (5 - d)),  U_lo = sum_{d=6..9} P_d 2^(7 (9 - d)),
@@ -58,6 +60,11 @@ constexpr int kStage = kS * (kABlock + kBBlock);  // all slices of one block (96
 constexpr int kThreads = 256;
 constexpr int kNoExp = (int)0x80808080;  // exponent of an all-zero row / column (bytes 0x80)
 constexpr long kSpin = 1L << 20;    // bound of every wait (iterations)
+// Exactness of the FP32 tensor-memory sums: at most kS slice pairs share a
+// diagonal, each adding kGroup * kKB products of magnitude <= 127^2 before the
+// accumulator is drained, and FP32 holds every integer below 2^24.
+static_assert((long)kS * kGroup * kKB * 127 * 127 < (1L << 24),
+              "slice products of one K group must sum exactly in FP32");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -45,4 +45,32 @@ def test_static_solve_matches_solve_twice():
     ub = torch.empty((1,), dtype=torch.float64, device="cuda")
     assert hps.hps_solve_static(h, big, ub, check=False) == hps.HPS_EINVAL
     assert b"static array" in hps.lib().hps_last_error()
+    # the largest nrhs that fits (a size above it is refused before any device
+    # work) still matches the ordinary solve
+    lo, hi = 4, 4000
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        fm = torch.zeros((mid, hps.hps_boundary_count(nx, ny, q)), dtype=torch.float64,
+                         device="cuda")
+        um = torch.empty((mid, nx * ny, p, p), dtype=torch.float64, device="cuda")
+        if hps.hps_solve_static(h, fm, um, check=False) == hps.HPS_OK:
+            lo = mid
+        else:
+            assert b"static array" in hps.lib().hps_last_error()
+            hi = mid
+        del fm, um
+    f = torch.from_numpy(np.ascontiguousarray(np.stack(
+        [I.fourier_boundary(s % 20, bxy[:, 0], bxy[:, 1], dom) for s in range(lo)]))).cuda()
+    ref = torch.empty((lo, nx * ny, p, p), dtype=torch.float64, device="cuda")
+    hps.hps_solve(h, f, ref)
+    got = torch.full_like(ref, float("nan"))
+    assert hps.hps_solve_static(h, f, got) == hps.HPS_OK
+    torch.cuda.synchronize()
+    assert float((got - ref).abs().max() / ref.abs().max()) <= TOL
     h.close()
+    # a mixed-precision handle is refused with a message
+    hm = hps.hps_build(dom, nx, ny, p, q, co, device_ptrs=True, precision=hps.HPS_MIXED)
+    assert hps.hps_solve_static(hm, f[:1].contiguous(), got[:1].contiguous(),
+                                check=False) == hps.HPS_EINVAL
+    assert b"only FP64 handles" in hps.lib().hps_last_error()
+    hm.close()
