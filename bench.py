@@ -6,10 +6,12 @@ and all merges, Algorithm 1) followed by the solve of every right-hand side
 (Algorithm 2 and the leaf post-process; in mixed precision also the iterative
 refinement against the FP64 residual).  Workloads (--workload):
 
-  convdiff64    (default) convection-diffusion on [0,1]^2, 64 x 64 leaves,
-                p = 16, q = 14 (1 048 576 collocation nodes), 16 right-hand sides
-  helmholtz256  variable-speed Helmholtz, kappa = 80, 256 x 256 leaves, p = 16,
-                q = 14 (16.8 M nodes), 64 right-hand sides
+  helmholtz256  (default) variable-speed Helmholtz, kappa = 80, 256 x 256
+                leaves, p = 16, q = 14 (16.8 M nodes), 64 right-hand sides: the
+                largest single-GPU configuration and the one specified in mixed
+                precision
+  convdiff64    convection-diffusion on [0,1]^2, 64 x 64 leaves, p = 16,
+                q = 14 (1 048 576 collocation nodes), 16 right-hand sides
   batch64       64 independent problems of uneven size (n log-uniform in
                 [8, 128]) and order (p in {12, 16, 20}, q = p - 2) with random
                 smooth coefficient fields, 16 right-hand sides each, one batched
@@ -52,7 +54,7 @@ UNIT_SQ = (0.0, 1.0, 0.0, 1.0)
 FP64_DFMA_PER_SM_CLK = 2
 FP32_FFMA_PER_SM_CLK = 128
 N_SM = 152
-MAX_REFINE = 30  # refinement cap (tolerance 1e-11, Anderson depth 3: the library defaults)
+MAX_REFINE = 30  # refinement cap (tolerance 1e-11, plain refinement, leaf correction on: library defaults)
 
 
 # ------------------------------------------------------------- workloads
@@ -71,7 +73,8 @@ class Workload:
         return dict(self.desc, precision=precision, dof=self.dof, nrhs=self.nrhs,
                     problems=len(self.probs), leaves_total=self.leaves,
                     l2="flushed before every timed step (512 MiB write)",
-                    refinement="tol 1e-11 per RHS, Anderson depth 3, cap 30")
+                    refinement="tol 1e-11 per RHS (or the next correction predicted below it), "
+                               "plain refinement, cap 30; leaf operators corrected once in FP64")
 
 
 def _problem(hps, I, dom, nx, ny, p, q, fn, nrhs, seed0):
@@ -197,7 +200,8 @@ class ClockSampler:
 def oracle_step(n, fn, nrhs=16):
     """One oracle solve (static condensation + sparse LU, FP64) of the
     workload's coefficient field on n x n leaves, p = 16, q = 14; returns
-    seconds and DOF."""
+    seconds, DOF, the data f (nrhs, nbnd) and the oracle's solution
+    (nrhs, n*n, p, p)."""
     from oracle import hps_oracle as O
     from paper_1307_2665_gb300 import inputs as I
     prob = O.make_problem(UNIT_SQ, n, n, 16, 14, fn)
@@ -205,16 +209,66 @@ def oracle_step(n, fn, nrhs=16):
     f = np.stack([I.fourier_boundary(s, bxy[:, 0], bxy[:, 1], UNIT_SQ) for s in range(nrhs)],
                  axis=1)
     t0 = time.perf_counter()
-    O.solve_condensed(prob, f)
-    return time.perf_counter() - t0, n * n * 16 * 16
+    sol = O.solve_condensed(prob, f)
+    return time.perf_counter() - t0, n * n * 16 * 16, np.ascontiguousarray(f.T), sol.w
 
 
 def cpu_baseline(fn, n=32, nrhs=16):
-    t, dof = oracle_step(n, fn, nrhs)
-    return {"value": dof / t, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n}x{n} leaves of the workload's coefficient field, p=16, q=14, {nrhs} "
-                      f"RHS: FP64 static condensation (per-leaf dense solves, BLAS on all cores) "
-                      f"+ SuperLU of the edge system (single-threaded); {t:.2f} s per solve"}
+    """The oracle timed on a bounded sample of the workload; also returns the
+    sample's data and oracle solution for the accuracy check."""
+    t, dof, f, w = oracle_step(n, fn, nrhs)
+    return ({"value": dof / t, "unit": "DOF/s", "cores": os.cpu_count(), "kind": "oracle",
+             "sample": f"{n}x{n} leaves of the workload's coefficient field, p=16, q=14, {nrhs} "
+                       f"RHS: FP64 static condensation (per-leaf dense solves, BLAS on all "
+                       f"cores) + SuperLU of the edge system (single-threaded); {t:.2f} s per "
+                       f"solve"}, f, w)
+
+
+def sample_vs_oracle(hps, fn, n, f, w_oracle):
+    """The library on the oracle's sample (same field, data and leaf grid), in
+    both precisions, against the oracle's solution element by element: max
+    |u - u_oracle| / max |u_oracle| over every node of every right-hand side."""
+    from paper_1307_2665_gb300 import inputs as I
+    xy = hps.hps_cheb_nodes(UNIT_SQ, n, n, 16)
+    co = I.sample_on_leaf_grid(fn, xy[:n, 0, :, 0].reshape(-1), xy[::n, :, 0, 1].reshape(-1),
+                               n, n, 16)
+    out = {"leaves": f"{n}x{n}", "nrhs": int(f.shape[0])}
+    scale = float(np.max(np.abs(w_oracle)))
+    for name, prec in (("fp64", hps.HPS_FP64), ("mixed", hps.HPS_MIXED)):
+        h = hps.hps_build(UNIT_SQ, n, n, 16, 14, co, precision=prec, max_refine=MAX_REFINE)
+        info = hps.SolveInfo()
+        u = hps.hps_solve(h, f, info=info, check=False)
+        h.close()
+        out[f"max_rel_err_{name}"] = float(np.max(np.abs(u - w_oracle)) / scale)
+        if prec == hps.HPS_MIXED:
+            out["mixed_corrections"] = int(info.iterations)
+    return out
+
+
+def full_size_residual(W, u_by_mode, nrhs=2, seed=11, count=40):
+    """The oracle's leaf-local FP64 check (E1, E2, shared-side continuity,
+    Dirichlet data) of the benchmarked solutions at full size, on a fixed set
+    of leaves (seeded sample plus the corners and the centre) and the first
+    nrhs right-hand sides; only those leaves and their east and north
+    neighbours are copied to the host."""
+    from oracle import hps_oracle as O
+    pr = W.probs[0]
+    nx, ny, p = pr["nx"], pr["ny"], pr["p"]
+    nl = nx * ny
+    rng = np.random.default_rng(seed)
+    leaves = sorted(set(rng.choice(nl, min(count, nl), replace=False).tolist()) |
+                    {0, nx - 1, nx * (ny - 1), nl - 1, nx * (ny // 2) + nx // 2 - 1})
+    need = sorted({m for l in leaves for m in (l, l + 1, l + nx) if m < nl})
+    co = {k: (None if v is None else v.reshape(nl, p, p)) for k, v in pr["coeffs"].items()}
+    prob = O.Problem(pr["domain"], nx, ny, p, pr["q"], co)
+    k = min(nrhs, W.nrhs)
+    out = {"leaves": len(leaves), "nrhs": k}
+    for name, us in u_by_mode.items():
+        w = np.zeros((k, nl, p, p))
+        w[:, need] = us[0][:k, need].cpu().numpy()
+        out[name] = {key: float(v) for key, v in O.sampled_residual(prob, w, pr["f"][:k],
+                                                                    leaves).items()}
+    return out
 
 
 def run_reference(args):
@@ -230,7 +284,7 @@ def run_reference(args):
     ts = []
     dof = 0
     for _ in range(args.steps):
-        t, dof = oracle_step(n, fn)
+        t, dof, _, _ = oracle_step(n, fn)
         ts.append(t)
     tot = sum(ts)
     value = dof * args.steps / tot
@@ -489,9 +543,18 @@ def run_native(args):
         line["fp64"]["kernels"] = F["kernels"]
     line["rel_diff_mixed_vs_fp64"] = rel_diff
     line["refine_iterations"] = H["refine_iterations"]
-    line["kernels"] = H["kernels"]
+    # accuracy of the benchmarked run: mixed against FP64 at full size, both
+    # against the oracle's leaf-local FP64 residual at full size, and both
+    # against the oracle's solution on the cpu_baseline sample
+    acc = {"rel_diff_mixed_vs_fp64": rel_diff}
+    if len(W.probs) == 1:
+        acc["full_size_residual"] = full_size_residual(W, {k: v["u"] for k, v in results.items()})
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(W.oracle_fn, args.ref_leaves)
+        cb, fs, ws = cpu_baseline(W.oracle_fn, args.ref_leaves)
+        line["cpu_baseline"] = cb
+        acc["oracle_sample"] = sample_vs_oracle(hps, W.oracle_fn, args.ref_leaves, fs, ws)
+    line["accuracy"] = acc
+    line["kernels"] = H["kernels"]
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -736,7 +799,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="convdiff64",
+    ap.add_argument("--workload", default="helmholtz256",
                     choices=["convdiff64", "helmholtz256", "batch64", "serve", "post"])
     ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: arrivals per second")

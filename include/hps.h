@@ -73,14 +73,19 @@ typedef struct {
   void* stream;           /* cudaStream_t to run on; NULL: the library's own stream */
   int form_root_dtn;      /* 1: also form the root DtN T^1 (not needed by hps_solve) */
   int refine_depth;       /* mixed mode: Anderson history length of the refinement, 0..8
-                             (default 3; 0: plain refinement u += delta) */
+                             (default 0: plain refinement u += delta, as fast as the
+                             accelerated one once the leaf operators are corrected) */
+  int leaf_refine;        /* mixed mode: 1 (default) corrects each leaf's FP32 solution
+                             operator Y once against its FP64 residual before the leaf
+                             DtN map is formed from it; 0: no correction */
 } hps_options;
 
 typedef struct {
   int status;             /* HPS_OK or the failing status */
   int iterations;         /* refinement corrections computed, the most over all
                              right-hand sides (0 in FP64 mode) */
-  double last_update;     /* largest over right-hand sides of the last max|delta| / max|u| */
+  double last_update;     /* largest over right-hand sides of the last max|delta| / max|u|
+                             (the last correction applied) */
   int bad_box;            /* box index of a singular pivot, or -1 */
 } hps_solve_info;
 
@@ -157,7 +162,10 @@ int hps_boundary_nodes(hps_handle h, double* xy);
  * corrections and iterates that best cancels delta (the GMRES iterate of the
  * same Krylov space, for this linear map); with m = 0 it is u + delta.  Every
  * right-hand side of every problem is refined on its own: it stops when its
- * max|delta| <= refine_tol * max|u| (then u += delta), when delta no longer
+ * max|delta| <= refine_tol * max|u| (then u += delta), when the last two
+ * corrections shrink by a ratio r < 1/4 with r * max|delta| <= refine_tol *
+ * max|u| (then u += delta: the next correction, the error left, is predicted
+ * below the tolerance and is not computed), when delta no longer
  * shrinks to half of the smaller of the two previous ones (the iterate has
  * reached the accuracy the FP64 residual resolves for this conditioning), or
  * after max_refine corrections, and its result does not depend on the other

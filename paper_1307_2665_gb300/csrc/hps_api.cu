@@ -205,6 +205,8 @@ struct LevelGroup {
   void* gemm_down = nullptr;        // per solve configuration
   void* gemm_w = nullptr;
   void* gemm_hpar = nullptr;
+  int n_hpar = 0;                   // merges with a parent (a root's offsets are never read)
+  int built_f64 = 0;                // mixed mode: factored in FP64, solved with FP32 copies
   double down_flops1 = 0, down_bytes = 0;
 };
 
@@ -266,10 +268,15 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
   const int ni = G.ni, nq = G.nq, nl = G.nl;
   // mixed mode also solves for A_ii^{-1} (identity columns after -A_ie L1)
   const int nrhs_leaf = nq + (H.mixed ? ni : 0);
+  // mixed mode: one correction of Y against its FP64 residual before T is
+  // formed; the residual and the correction reuse the factors' memory
+  const bool yref = H.mixed && H.opt.leaf_refine > 0;
   G.ys = (int64_t)ni * nrhs_leaf;
   G.Y->alloc((size_t)nl * G.ys * sizeof(R), st);
   PoolBuf Aii, piv;
-  Aii.alloc((size_t)nl * ni * ni * sizeof(R), st);
+  Aii.alloc((size_t)nl * std::max<int64_t>((int64_t)ni * ni, yref ? 2LL * ni * nq : 0) *
+                sizeof(R),
+            st);
   piv.alloc((size_t)nl * ni * sizeof(int), st);
   const double2* hsc = H.hsc.as<double2>();
   leaf_assemble<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(), G.dPg2c->as<double>(),
@@ -289,9 +296,38 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
   LuDesc<R>* dl = stg.push(ld, st);
   lu_solve_batched<R>(dl, nl, ni, nrhs_leaf, kLuFactor, H.status.as<int>(), st, nullptr, nullptr);
   ck(cudaGetLastError());
+  R* dY = nullptr;
+  if (yref) {
+    // Rl = -A_ie L1 - A_ii Y_l in FP64 (rounded to R), dY_l = A_ii^{-1} Rl.  The
+    // low-precision LU leaves Y with an error of about cond(A_ii) units of
+    // rounding, which the side derivatives of T amplify; T formed from Y + dY
+    // in FP64 carries only the rounding of T itself.
+    R* Rb = Aii.as<R>();
+    dY = Rb + (size_t)nl * ni * nq;
+    leaf_y_residual<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(),
+                       G.dPg2c->as<double>(), G.Y->as<R>(), G.ys, Rb, st);
+    ck(cudaGetLastError());
+    std::vector<GemmDesc<R>> gd(nl);
+    for (int j = 0; j < nl; ++j) {
+      gd[j].A = G.Y->as<R>() + (size_t)j * G.ys + (size_t)ni * nq;  // A_ii^{-1}
+      gd[j].B = Rb + (size_t)j * ni * nq;
+      gd[j].C = dY + (size_t)j * ni * nq;
+      gd[j].M = ni;
+      gd[j].N = nq;
+      gd[j].K = ni;
+      gd[j].lda = ni;
+      gd[j].ldb = ni;
+      gd[j].ldc = ni;
+    }
+    GemmDesc<R>* dg = stg.push(gd, st);
+    gemm_batched<R>(dg, nl, ni, nq, R(1), R(0), st, "gemm_yref<f32>",
+                    2.0 * nl * (double)ni * ni * nq, (double)nl * ni * (ni + 2.0 * nq) * sizeof(R));
+    ck(cudaGetLastError());
+  }
   T0.alloc((size_t)nl * nq * nq * sizeof(R), st);
   leaf_dtn<R>(G.Y->as<R>(), G.ys, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(),
-              G.dPg2c->as<double>(), G.dPc2g->as<double>(), T0.as<R>(), st);
+              G.dPg2c->as<double>(), G.dPc2g->as<double>(), T0.as<R>(), st, dY,
+              (int64_t)ni * nq);
   ck(cudaGetLastError());
   for (int j = 0; j < nl; ++j) {
     Tref[pl.leaf_box[G.l0 + j]].p = T0.as<R>() + (size_t)j * nq * nq;
@@ -610,7 +646,8 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
   // descriptor staging (upper bound of every array pushed below)
   const size_t nb = pl.boxes.size();
   Stager stg;
-  size_t bytes = 8 * 256 + stage_bytes<LuDesc<double>>(nl_tot) + 256 * H.lg.size();
+  size_t bytes = 8 * 256 + stage_bytes<LuDesc<double>>(nl_tot) +
+                 stage_bytes<GemmDesc<double>>(nl_tot) + 512 * H.lg.size();
   for (auto& L : H.lev) {
     bytes += stage_bytes<MergeDesc<double>>(L.boxes.size()) +
              2 * stage_bytes<LuDesc<double>>(L.boxes.size()) +
@@ -741,6 +778,28 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
     for (size_t j = 0; j < i; ++j)
       if (last_use[j] == (int)i) Tlev[j]->release();
   }
+  // ---- mixed mode: the heights factored in FP64 (the ill-conditioned top
+  // interface systems) keep FP32 copies of S, W and [T13; T23] for the solve.
+  // Their factorisation and the T they passed up were formed in FP64; the
+  // solve only needs a correction accurate to a few digits, which the
+  // refinement then removes, so rounding the stored operators costs no
+  // accuracy and halves their bytes and the solve's FP64 work.
+  if (H.mixed) {
+    for (auto& L : H.lev) {
+      if (!L.f64) continue;
+      auto demote = [&](PoolPtr& b) {
+        const int64_t n = (int64_t)(b->bytes / sizeof(double));
+        PoolPtr d = new_buf();
+        d->alloc((size_t)n * sizeof(float), st);
+        f64_to_f32(b->as<double>(), d->as<float>(), n, st);
+        b = std::move(d);  // the FP64 copy is released in stream order
+      };
+      demote(L.S);
+      demote(L.Cw);
+      L.f64 = 0;
+      L.built_f64 = 1;
+    }
+  }
   // ---- solve-side structures that do not depend on nrhs
   for (auto& L : H.lev) {
     std::vector<SolveScatterDesc> sd;
@@ -865,6 +924,7 @@ void push_body(hps_handle_s& H, LevelGroup& L, int nrhs) {
     w.ldb = sh.m;
     w.ldc = sh.m;
     gw.push_back(w);
+    if (pl.boxes[b].parent < 0) continue;  // a root's flux offsets are never read
     GemmDesc<R, R, double> g;  // h^tau += [T13^a; T23^b] z
     g.A = L.Cw->as<R>() + L.cw_off[i];
     g.B = z + L.z_off[i] * nrhs;
@@ -879,6 +939,7 @@ void push_body(hps_handle_s& H, LevelGroup& L, int nrhs) {
   }
   L.gemm_w = H.solve_st.push(gw, H.stream);
   L.gemm_hpar = H.solve_st.push(gh, H.stream);
+  L.n_hpar = (int)gh.size();
 }
 
 template <typename R>
@@ -1041,14 +1102,16 @@ void up_level(hps_handle_s& H, LevelGroup& L, int nrhs) {
   double flw = 0, flc = 0;
   for (int i = 0; i < nm; ++i) {
     flw += 2.0 * L.hm[i] * (double)L.hm[i] * nrhs;
-    flc += 2.0 * L.hne[i] * (double)L.hm[i] * nrhs;
+    if (pl.boxes[L.boxes[i]].parent >= 0) flc += 2.0 * L.hne[i] * (double)L.hm[i] * nrhs;
   }
   gemm_batched<R>(static_cast<GemmDesc<R>*>(L.gemm_w), nm, L.max_m, nrhs, R(1), R(0), st,
                   sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flw, 0.0, L.max_m, ws,
                   wse);
-  // parents' flux offsets (a root's are never read; computing them is harmless)
+  // parents' flux offsets: [h1^a; h2^b] copied for every merge (a root's copy
+  // is never read and costs little), the product only where a parent reads it
   merge_hpar(L.body, nm, L.max_ne, H.hpool.as<double>(), pl.ext_total, nrhs, st);
-  gemm_batched<R>(static_cast<GemmDesc<R, R, double>*>(L.gemm_hpar), nm, L.max_ne, nrhs, R(1),
+  if (L.n_hpar == 0) return;
+  gemm_batched<R>(static_cast<GemmDesc<R, R, double>*>(L.gemm_hpar), L.n_hpar, L.max_ne, nrhs, R(1),
                   R(1), st, sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flc, 0.0,
                   L.max_m, ws, wse);
 }
@@ -1148,7 +1211,8 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
     leaf_out(H, cp.fptr, cp.wrs, nrhs, true);  // F_j, the correction at w_j
     const int nslots = m > 0 ? std::min(j, m) : 0;
     const int slot_new = (m > 0 && j >= 1) ? (j - 1) % m : -1;
-    aa_reduce(cp.cols, cp.col_of, ncol, cp.nchunks, rb->F.as<double>(), rb->Fprev.as<double>(),
+    aa_reduce(cp.cols, cp.col_of, ncol, cp.nchunks, rb->F.as<double>(),
+              m > 0 ? rb->Fprev.as<double>() : nullptr,
               rb->dWlast.as<double>(), rb->dF.as<float>(), rb->G.as<double>(), cp.nu,
               m > 0 ? j : 0, slot_new, nslots, rb->part.as<double>(), rb->colsum.as<double>(), st);
     ck(cudaGetLastError());
@@ -1181,6 +1245,13 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
         mode = 0;
         done = true;
       } else if (S.rel <= H.opt.refine_tol) {
+        S.converged = true;
+        mode = 2;
+        done = true;
+      } else if (j >= 1 && S.rel < 0.25 * S.rel1 && S.rel * (S.rel / S.rel1) <= H.opt.refine_tol) {
+        // the corrections contract by about rel / rel1 per step: after this one
+        // is applied, the error (the next correction) is predicted below the
+        // tolerance, so it is not computed
         S.converged = true;
         mode = 2;
         done = true;
@@ -1258,8 +1329,8 @@ CallPtrs stage_call(hps_handle_s& H, const double* const* f, double* const* u, i
   if (refine) {
     const int m = H.opt.refine_depth;
     rb->F.alloc((size_t)nu * sizeof(double), H.stream);
-    rb->Fprev.alloc((size_t)nu * sizeof(double), H.stream);
     if (m > 0) {
+      rb->Fprev.alloc((size_t)nu * sizeof(double), H.stream);
       rb->dWlast.alloc((size_t)nu * sizeof(double), H.stream);
       rb->dF.alloc((size_t)m * nu * sizeof(float), H.stream);
       rb->G.alloc((size_t)m * nu * sizeof(double), H.stream);
@@ -1390,7 +1461,8 @@ int build_entry(const hps_problem* probs, int nprob, const hps_options* opt_in, 
   if (opt.precision != HPS_FP64 && opt.precision != HPS_MIXED) return HPS_EINVAL;
   if (opt.precision == HPS_MIXED &&
       (!(opt.refine_tol > 0) || opt.max_refine < 0 || opt.fp64_top_levels < 0 ||
-       opt.refine_depth < 0 || opt.refine_depth > kAaMaxDepth))
+       opt.refine_depth < 0 || opt.refine_depth > kAaMaxDepth || opt.leaf_refine < 0 ||
+       opt.leaf_refine > 1))
     return HPS_EINVAL;
   g_last_error.clear();
   hps_handle_s* H = nullptr;
@@ -1464,7 +1536,8 @@ void hps_default_options(hps_options* opt) {
   opt->device_ptrs = 0;
   opt->stream = nullptr;
   opt->form_root_dtn = 0;
-  opt->refine_depth = 3;
+  opt->refine_depth = 0;
+  opt->leaf_refine = 1;
 }
 
 int64_t hps_boundary_count(int nx, int ny, int q) { return 2LL * (nx + ny) * q; }
@@ -1704,13 +1777,17 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
     for (const auto& pi : pl.probs) {
       const int64_t ni = (int64_t)(pi.s.p - 2) * (pi.s.p - 2), nq = 4LL * pi.s.q;
       y += pi.nl * ni * (nq + (mixed ? ni : 0)) * bl;
-      leaf_tmp += pi.nl * (ni * ni + nq * nq) * bl;
+      const bool yref = mixed && opt.leaf_refine > 0;  // residual and correction of Y
+      leaf_tmp += pi.nl * (std::max(ni * ni, yref ? 2 * ni * nq : 0) + nq * nq) * bl;
       dof += (int64_t)pi.nl * pi.s.p * pi.s.p;
       nint += pi.nl * ni;
     }
     // per height: stored S (+ W, [T13; T23] in mixed mode), transient T, A_w
     std::vector<int64_t> t_at(pl.height + 1, 0), tmp_at(pl.height + 1, 0);
-    int64_t sres = 0, u3_rows = 0, max_level_rows = 0;
+    // sres: stored operators as built; sres_r: as resident after the build (in
+    // mixed mode the FP64-factored heights keep FP32 copies); demote: those
+    // copies, held beside the FP64 originals while they are made
+    int64_t sres = 0, sres_r = 0, demote = 0, u3_rows = 0, max_level_rows = 0;
     t_at[0] = 0;
     for (const auto& pi : pl.probs) t_at[0] += pi.nl * 16LL * pi.s.q * pi.s.q * bl;
     for (int h = 1; h <= pl.height; ++h) {
@@ -1720,8 +1797,11 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
         const MergeShape& sh = pl.shapes[B.shape];
         const int ph = pl.probs[B.prob].height;
         const int64_t bm = (!mixed || h > ph - top) ? 8 : 4;
-        sres += (int64_t)sh.m * (sh.ne + (mixed ? sh.m : 0)) * bm;
-        if (mixed) sres += (int64_t)sh.ne * sh.m * bm;
+        const int64_t ops = (int64_t)sh.m * (sh.ne + (mixed ? sh.m : 0)) +
+                            (mixed ? (int64_t)sh.ne * sh.m : 0);
+        sres += ops * bm;
+        sres_r += ops * (mixed ? 4 : 8);
+        if (mixed && bm == 8) demote += ops * 4;
         if (B.parent >= 0 || opt.form_root_dtn) t_at[h] += (int64_t)sh.ne * sh.ne * bm;
         tmp_at[h] += (int64_t)sh.m * sh.m * bm + (mixed ? 0 : (int64_t)sh.ne * sh.m * bm);
         if (bm == 4 && mixed && sh.m >= kNBw) tmp_at[h] += (int64_t)sh.m * sh.ne * 4;  // [-T31 | T32]
@@ -1744,8 +1824,8 @@ int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* o
     }
     int64_t root_dtn = 0;  // form_root_dtn: the kept T^1 of every problem
     if (opt.form_root_dtn && nprob == 1) root_dtn = (int64_t)pl.probs[0].nbnd * pl.probs[0].nbnd * 8;
-    const int64_t res = y + sres + (mixed ? coef_bytes : 0) + root_dtn;
-    int64_t peak = leaf_tmp;
+    const int64_t res = y + sres_r + (mixed ? coef_bytes : 0) + root_dtn;
+    int64_t peak = std::max(leaf_tmp, demote);
     for (int h = 1; h <= pl.height; ++h) peak = std::max(peak, t_at[h - 1] + t_at[h] + tmp_at[h]);
     peak += y + sres + coef_bytes + root_dtn;
     int64_t work = (int64_t)nrhs * (pl.ext_total + u3_rows) * 8 + 2 * (int64_t)nrhs * max_level_rows * 8;

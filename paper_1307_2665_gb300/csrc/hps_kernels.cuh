@@ -128,10 +128,12 @@ template <typename R>
 void leaf_assemble(const double* const* coef, int l0, int nleaves, int p, int q,
                    const double2* hsc, const double* d_D, const double* d_Pg2c, R* Aii, R* Y,
                    int64_t ys, int with_identity, cudaStream_t st);
+// dY (optional, leaf stride dys): a correction of Y; T is formed from Y + dY
+// summed in FP64 and the rounded sum is written back to Y.
 template <typename R>
-void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2* hsc,
+void leaf_dtn(R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2* hsc,
               const double* d_D, const double* d_Pg2c, const double* d_Pc2g, R* T,
-              cudaStream_t st);
+              cudaStream_t st, const R* dY = nullptr, int64_t dys = 0);
 template <typename R>
 void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
@@ -141,6 +143,12 @@ template <typename R>
 void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
                    const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
                    cudaStream_t st);
+// FP64 residual of the leaf systems themselves: rbuf (leaf stride ni*4q, ld ni)
+// = -A_ie L1 - A_ii Y, Y read from Y + j*ys (ni x 4q, ld ni).
+template <typename R>
+void leaf_y_residual(const double* const* coef, int l0, int nl, int p, int q,
+                     const double2* hsc, const double* d_D, const double* d_Pg2c, const R* Y,
+                     int64_t ys, R* rbuf, cudaStream_t st);
 template <typename R>
 void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int nl, int p, int q,
                int nrhs, const double2* hsc, const double* d_D, const double* d_Pc2g,
@@ -205,6 +213,7 @@ size_t dtn_apply_ws_bytes(int n, int nrhs);
 cudaError_t dtn_apply(const double* T, int n, const int* rff, const double* f, int nrhs,
                       double* g, void* ws, size_t ws_bytes, int* status, cudaStream_t st);
 void f32_to_f64(const float* s, double* d, int64_t n, cudaStream_t st);
+void f64_to_f32(const double* s, float* d, int64_t n, cudaStream_t st);
 // The leaf grid of one problem, for point evaluation.
 struct InterpGrid {
   double x0, x1, y0, y1;

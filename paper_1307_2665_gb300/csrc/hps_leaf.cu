@@ -200,13 +200,18 @@ void leaf_assemble(const double* const* coef, int l0, int nleaves, int p, int q,
 
 // ------------------------------------------------------------------ leaf DtN
 // One CTA per leaf; the 4q columns of W are processed in chunks of CH.
+// With dY (a correction of Y from one refinement step against the FP64
+// residual, leaf stride dys), the interior rows are Y + dY summed in FP64, so T
+// is formed from the corrected operator before any rounding to R; the rounded
+// sum is written back to Y for the solve.
 template <typename R>
-__global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64_t ys, int l0,
-                                                  int p, int q, const double2* __restrict__ hsc,
+__global__ void __launch_bounds__(256) k_leaf_dtn(R* Y, int64_t ys, int l0, int p, int q,
+                                                  const double2* __restrict__ hsc,
                                                   const double* __restrict__ gD,
                                                   const double* __restrict__ gPg2c,
                                                   const double* __restrict__ gPc2g,
-                                                  R* __restrict__ T) {
+                                                  R* __restrict__ T, const R* __restrict__ dY,
+                                                  int64_t dys) {
   constexpr int CH = 8;
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
@@ -222,7 +227,8 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
     Pg[e] = gPg2c[e];
     Pc[e] = gPc2g[e];
   }
-  const R* Yl = Y + (size_t)l * ys;
+  R* Yl = Y + (size_t)l * ys;
+  const R* dYl = dY ? dY + (size_t)l * dys : nullptr;
   R* Tl = T + (size_t)l * nq * nq;
   for (int g0 = 0; g0 < nq; g0 += CH) {
     const int nc = min(CH, nq - g0);
@@ -233,7 +239,12 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
       const int a = node / p, b = node % p;
       double v = 0.0;
       if (a > 0 && a < p - 1 && b > 0 && b < p - 1) {
-        v = (double)Yl[(a - 1) * pi + (b - 1) + (size_t)g * ni];
+        const size_t idx = (a - 1) * pi + (b - 1) + (size_t)g * ni;
+        v = (double)Yl[idx];
+        if (dYl) {
+          v += (double)dYl[idx];
+          Yl[idx] = (R)v;
+        }
       } else {
         const int s = g / q, k = g % q;
         // the node lies on side s at position j?
@@ -278,9 +289,9 @@ __global__ void __launch_bounds__(256) k_leaf_dtn(const R* __restrict__ Y, int64
 }
 
 template <typename R>
-void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2* hsc,
+void leaf_dtn(R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2* hsc,
               const double* d_D, const double* d_Pg2c, const double* d_Pc2g, R* T,
-              cudaStream_t st) {
+              cudaStream_t st, const R* dY, int64_t dys) {
   if (nleaves <= 0) return;
   size_t smem = (size_t)(p * p + 2 * p * q + p * p * 8 + 4 * p * 8) * sizeof(double);
   if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_dtn<R>), 200 * 1024))
@@ -289,7 +300,8 @@ void leaf_dtn(const R* Y, int64_t ys, int l0, int nleaves, int p, int q, const d
   prof::Scope sc(tname<R>("leaf_dtn<f64>", "leaf_dtn<f32>"), st,
                  (double)nleaves * nq * (8.0 * p * p + 2.0 * nq * p),
                  (double)nleaves * (ni * nq + nq * nq) * sizeof(R));
-  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, ys, l0, p, q, hsc, d_D, d_Pg2c, d_Pc2g, T);
+  k_leaf_dtn<R><<<nleaves, 256, smem, st>>>(Y, ys, l0, p, q, hsc, d_D, d_Pg2c, d_Pc2g, T, dY,
+                                             dys);
 }
 
 // ------------------------------------------------------------ post-process
@@ -459,26 +471,37 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
 // when both orders are present and the rows fit).  The mixed term goes
 // through Dx w at every node.
 // Output rbuf[l*ni*nrhs + i + r*ni] in the element type of the correction solve.
-template <typename R, bool kMerged>
+//
+// kFromY: the grids are the columns of W = [L1 ; Y] of a leaf (Section 3.2,
+// Step 1 and eq. leaf_solve), nrhs = 4q of them: boundary rows from L1 (the
+// side's Gauss interpolant, corners averaged), interior rows from the leaf's
+// low-precision Y (ld ni, leaf stride ys).  Then -(A W)_i = -A_ie L1 - A_ii Y is
+// the FP64 residual of the leaf system A_ii Y = -A_ie L1 that the LU solved.
+template <typename R, bool kMerged, bool kFromY>
 __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int p, int rb,
                                                        const double2* __restrict__ hsc,
                                                        const double* __restrict__ gD,
                                                        double* const* __restrict__ wptr,
                                                        const int64_t* __restrict__ wrs, int nrhs,
-                                                       R* __restrict__ rbuf) {
+                                                       R* __restrict__ rbuf,
+                                                       const R* __restrict__ Ysrc, int64_t ys,
+                                                       int q, const double* __restrict__ gPg2c) {
   extern __shared__ __align__(16) double sm[];
   const int pp = p * p, pi = p - 2, ni = pi * pi;
   const int lp = p + 1;      // padded row pitch of D and D^2: rows walked across threads
   double* D = sm;
   double* D2 = D + p * lp;
-  double* W = D2 + p * lp;   // rb x pp: w of this block of right-hand sides
+  double* Pg = D2 + p * lp;  // kFromY: p x q side interpolation (Step 1)
+  double* W = Pg + (kFromY ? p * q : 0);  // rb x pp: w of this block of right-hand sides
   double* Wx = W + rb * pp;  // rb x pp: Dx w, unscaled (only with the mixed term)
   double* K = Wx + rb * pp;  // merged: 2 x ni (k12, k0 per interior node), then Mx, My
                              // (p x ni each, k-major); else 6 x pp per-node coefficients
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
-  const double* wl = wptr[l];
-  const int64_t wstride = wrs[l];
+  const double* wl = kFromY ? nullptr : wptr[l];
+  const int64_t wstride = kFromY ? 0 : wrs[l];
+  if constexpr (kFromY)
+    for (int e = threadIdx.x; e < p * q; e += blockDim.x) Pg[e] = gPg2c[e];
   for (int e = threadIdx.x; e < pp; e += blockDim.x) D[(e / p) * lp + e % p] = gD[e];
   __syncthreads();
   for (int e = threadIdx.x; e < pp; e += blockDim.x) {
@@ -532,8 +555,27 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   for (int r0 = 0; r0 < nrhs; r0 += rb) {
     const int nb = min(rb, nrhs - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < pp * nb; e += blockDim.x)
-      W[e] = wl[(size_t)(r0 + e / pp) * wstride + e % pp];
+    if constexpr (kFromY) {
+      for (int e = threadIdx.x; e < pp * nb; e += blockDim.x) {
+        const int g = r0 + e / pp, node = e % pp, a = node / p, b = node % p;
+        double v = 0.0;
+        if (a > 0 && a < p - 1 && b > 0 && b < p - 1) {
+          v = (double)Ysrc[(size_t)jl * ys + (a - 1) * pi + (b - 1) + (size_t)g * ni];
+        } else {  // column g is Gauss node k of side s: L1's entry at this node
+          const int s = g / q, k = g % q;
+          int j = -1;
+          if (s == 0 && a == 0) j = b;
+          if (s == 2 && a == p - 1) j = b;
+          if (s == 1 && b == p - 1) j = a;
+          if (s == 3 && b == 0) j = a;
+          if (j >= 0) v = ((j == 0 || j == p - 1) ? 0.5 : 1.0) * Pg[j * q + k];
+        }
+        W[e] = v;
+      }
+    } else {
+      for (int e = threadIdx.x; e < pp * nb; e += blockDim.x)
+        W[e] = wl[(size_t)(r0 + e / pp) * wstride + e % pp];
+    }
     __syncthreads();
     if (has12) {  // Dx w at every node: the mixed term differentiates it along y
       for (int e = threadIdx.x; e < pp * nb; e += blockDim.x) {
@@ -591,10 +633,15 @@ __global__ void __launch_bounds__(256) k_leaf_residual(CoefPtrs cp, int l0, int 
   }
 }
 
-template <typename R>
-void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
-                   const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
-                   cudaStream_t st) {
+namespace {
+
+// Shared launcher of k_leaf_residual: kFromY takes the grids from a leaf's
+// [L1 ; Y] (nrhs = 4q), otherwise from wptr / wrs.
+template <typename R, bool kFromY>
+void launch_residual(const double* const* coef, int l0, int nl, int p, int q,
+                     const double2* hsc, const double* d_D, double* const* wptr,
+                     const int64_t* wrs, int nrhs, R* rbuf, const R* Y, int64_t ys,
+                     const double* d_Pg2c, const char* name, cudaStream_t st) {
   if (nl <= 0 || nrhs <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
@@ -602,16 +649,17 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
   const int lp = p + 1;
   const int ni = (p - 2) * (p - 2);
   constexpr int kCap = 200 * 1024 / 8;  // doubles of shared memory
+  const int extra = kFromY ? p * q : 0;
   // merged rows when a direction has both orders and they fit beside D, D^2
   // and one right-hand side
-  const int fixed_m = 2 * p * lp + 2 * ni + 2 * p * ni;
+  const int fixed_m = 2 * p * lp + 2 * ni + 2 * p * ni + extra;
   const bool merged = ((coef[0] && coef[3]) || (coef[2] && coef[4])) && fixed_m + 2 * pp <= kCap;
   // right-hand sides per block: up to 4, as many as fit
-  const int fixed = merged ? fixed_m : 2 * p * lp + 6 * pp;
+  const int fixed = merged ? fixed_m : 2 * p * lp + 6 * pp + extra;
   const int rb = std::max(1, std::min(4, (kCap - fixed) / (2 * pp)));
   const size_t smem = (size_t)(fixed + 2 * rb * pp) * sizeof(double);
-  const void* kern = merged ? reinterpret_cast<const void*>(&k_leaf_residual<R, true>)
-                            : reinterpret_cast<const void*>(&k_leaf_residual<R, false>);
+  const void* kern = merged ? reinterpret_cast<const void*>(&k_leaf_residual<R, true, kFromY>)
+                            : reinterpret_cast<const void*>(&k_leaf_residual<R, false, kFromY>);
   if (!opt_in_smem(kern, 200 * 1024)) return;  // reported by the caller's launch check
   const double ppd = (double)pp, nid = (double)ni;
   // FP64 flops actually issued per leaf and right-hand side: merged, p FMAs
@@ -630,14 +678,33 @@ void leaf_residual(const double* const* coef, int l0, int nl, int p, const doubl
     else if (coef[3]) per += 2.0 * nid * p;
     if (coef[4]) per += 2.0 * nid * p;
   }
-  prof::Scope sc("leaf_residual<f64>", st, (double)nl * (nrhs * per + once),
-                 (double)nl * (nrhs * (ppd * 8.0 + nid * sizeof(R)) + 6.0 * ppd * 8.0));
+  const double in_bytes = kFromY ? nid * sizeof(R) : ppd * 8.0;
+  prof::Scope sc(name, st, (double)nl * (nrhs * per + once),
+                 (double)nl * (nrhs * (in_bytes + nid * sizeof(R)) + 6.0 * ppd * 8.0));
   if (merged)
-    k_leaf_residual<R, true><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs, nrhs,
-                                                    rbuf);
+    k_leaf_residual<R, true, kFromY><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs,
+                                                            nrhs, rbuf, Y, ys, q, d_Pg2c);
   else
-    k_leaf_residual<R, false><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs, nrhs,
-                                                     rbuf);
+    k_leaf_residual<R, false, kFromY><<<nl, 256, smem, st>>>(cp, l0, p, rb, hsc, d_D, wptr, wrs,
+                                                             nrhs, rbuf, Y, ys, q, d_Pg2c);
+}
+
+}  // namespace
+
+template <typename R>
+void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
+                   const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
+                   cudaStream_t st) {
+  launch_residual<R, false>(coef, l0, nl, p, 1, hsc, d_D, wptr, wrs, nrhs, rbuf, nullptr, 0,
+                            nullptr, "leaf_residual<f64>", st);
+}
+
+template <typename R>
+void leaf_y_residual(const double* const* coef, int l0, int nl, int p, int q,
+                     const double2* hsc, const double* d_D, const double* d_Pg2c, const R* Y,
+                     int64_t ys, R* rbuf, cudaStream_t st) {
+  launch_residual<R, true>(coef, l0, nl, p, q, hsc, d_D, nullptr, nullptr, 4 * q, rbuf, Y, ys,
+                           d_Pg2c, "leaf_yresid<f64>", st);
 }
 
 // ------------------------------------------------- flux offsets of the leaves
@@ -732,14 +799,17 @@ void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int 
   template void leaf_assemble<R>(const double* const*, int, int, int, int, const double2*,       \
                                  const double*, const double*, R*, R*, int64_t, int,            \
                                  cudaStream_t);                                                 \
-  template void leaf_dtn<R>(const R*, int64_t, int, int, int, int, const double2*, const double*, \
-                            const double*, const double*, R*, cudaStream_t);                    \
+  template void leaf_dtn<R>(R*, int64_t, int, int, int, int, const double2*, const double*,       \
+                            const double*, const double*, R*, cudaStream_t, const R*, int64_t); \
   template void leaf_post<R>(const R*, int64_t, int, const double*, const int64_t*, int64_t, int, \
                              int, int, int, const double*, double* const*, const int64_t*,      \
                              cudaStream_t, const R*, int);                                      \
   template void leaf_residual<R>(const double* const*, int, int, int, const double2*,           \
                                  const double*, double* const*, const int64_t*, int, R*,        \
                                  cudaStream_t);                                                 \
+  template void leaf_y_residual<R>(const double* const*, int, int, int, int, const double2*,     \
+                                   const double*, const double*, const R*, int64_t, R*,         \
+                                   cudaStream_t);                                               \
   template void leaf_flux<R>(double* const*, const int64_t*, const R*, int, int, int, int, int,  \
                              const double2*, const double*, const double*, const int64_t*,      \
                              int64_t, double*, cudaStream_t);

@@ -115,6 +115,11 @@ __global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, int64
   if (e < n) d[e] = (double)s[e];
 }
 
+__global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) d[e] = (float)s[e];
+}
+
 // Barycentric Lagrange basis of the p Chebyshev points of the second kind
 // ts (increasing), at t; exactly 1 / 0 when t is a node.
 __device__ void cheb_basis(double t, int p, const double* ts, double* ell) {
@@ -254,6 +259,12 @@ void f32_to_f64(const float* s, double* d, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
   prof::Scope sc("f32_to_f64", st, 0.0, 12.0 * n);
   k_f2d<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, d, n);
+}
+
+void f64_to_f32(const double* s, float* d, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  prof::Scope sc("f64_to_f32", st, 0.0, 12.0 * n);
+  k_d2f<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, d, n);
 }
 
 void interp_points(const double* u, int nrhs, const InterpGrid& s, const double* xy,

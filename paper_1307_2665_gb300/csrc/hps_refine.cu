@@ -63,7 +63,7 @@ template <int NS>
 __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict__ cols,
                                                         const int* __restrict__ col_of,
                                                         const double* __restrict__ F,
-                                                        double* __restrict__ Fprev,
+                                                        double* Fprev,
                                                         const double* __restrict__ dWlast,
                                                         float* __restrict__ dF,
                                                         double* __restrict__ G, int64_t nu, int j,
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_aa_reduce(const AaCol* __restrict_
       dF[(int64_t)slot_new * nu + i] = dfn;
       G[(int64_t)slot_new * nu + i] = dWlast[i] + d;
     }
-    Fprev[i] = fv;
+    if (Fprev) Fprev[i] = fv;  // null for plain refinement (no history)
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       const float d = (s == slot_new) ? dfn : dF[(int64_t)s * nu + i];

@@ -58,7 +58,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("refine_tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("fp64_top_levels", ctypes.c_int),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("form_root_dtn", ctypes.c_int), ("refine_depth", ctypes.c_int)]
+                ("form_root_dtn", ctypes.c_int), ("refine_depth", ctypes.c_int),
+                ("leaf_refine", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -247,7 +248,7 @@ class Handle:
 
 
 def _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
-             form_root_dtn, refine_depth=None):
+             form_root_dtn, refine_depth=None, leaf_refine=None):
     opt = default_options()
     opt.precision = precision
     opt.device_ptrs = 1 if device_ptrs else 0
@@ -261,6 +262,8 @@ def _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_le
         opt.fp64_top_levels = fp64_top_levels
     if refine_depth is not None:
         opt.refine_depth = refine_depth
+    if leaf_refine is not None:
+        opt.leaf_refine = leaf_refine
     return opt
 
 
@@ -286,10 +289,10 @@ class BatchHandle:
 
 def hps_build_batch(problems, precision=HPS_FP64, device_ptrs=False, stream=None,
                     refine_tol=None, max_refine=None, fp64_top_levels=None, form_root_dtn=False,
-                    refine_depth=None, check=True):
+                    refine_depth=None, leaf_refine=None, check=True):
     """Batch build.  problems: list of dicts with keys domain, nx, ny, p, q, coeffs."""
     opt = _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
-                   form_root_dtn, refine_depth)
+                   form_root_dtn, refine_depth, leaf_refine)
     arr = (Problem * len(problems))()
     for i, pr in enumerate(problems):
         arr[i].d = _domain(pr["domain"])
@@ -321,11 +324,11 @@ def hps_solve_batch(h: BatchHandle, fs, us, info=None, check=True):
 
 def hps_build(domain, nx, ny, p, q, coeffs, precision=HPS_FP64, device_ptrs=False, stream=None,
               refine_tol=None, max_refine=None, fp64_top_levels=None, form_root_dtn=False,
-              refine_depth=None, check=True):
+              refine_depth=None, leaf_refine=None, check=True):
     """Build stage.  coeffs: dict name -> array of nx*ny*p*p values (or None).
     Returns a Handle, or raises HpsError (returns the status when check=False)."""
     opt = _options(precision, device_ptrs, stream, refine_tol, max_refine, fp64_top_levels,
-                   form_root_dtn, refine_depth)
+                   form_root_dtn, refine_depth, leaf_refine)
     arrs = [coeffs.get(k) for k in COEFF_NAMES]
     out = ctypes.c_void_p()
     st = lib().hps_build(_domain(domain), nx, ny, p, q, *[_ptr(a) for a in arrs],
@@ -451,7 +454,8 @@ def _problem_struct(pr):
 def hps_estimate_bytes(problems, nrhs=1, precision=HPS_FP64, **kw):
     """(build_peak, resident, solve_workspace) in bytes for a list of problem dicts."""
     opt = _options(precision, False, None, kw.get("refine_tol"), kw.get("max_refine"),
-                   kw.get("fp64_top_levels"), kw.get("form_root_dtn", False), kw.get("refine_depth"))
+                   kw.get("fp64_top_levels"), kw.get("form_root_dtn", False), kw.get("refine_depth"),
+                   kw.get("leaf_refine"))
     arr = (Problem * len(problems))(*[_problem_struct(pr) for pr in problems])
     out = [ctypes.c_int64() for _ in range(3)]
     st = lib().hps_estimate_bytes(arr, len(problems), ctypes.byref(opt), nrhs,
@@ -479,7 +483,8 @@ class Server:
     def submit_build(self, pr, precision=HPS_FP64, **kw):
         """pr: dict with domain, nx, ny, p, q and host coefficient arrays in 'coeffs'."""
         opt = _options(precision, False, None, kw.get("refine_tol"), kw.get("max_refine"),
-                       kw.get("fp64_top_levels"), False, kw.get("refine_depth"))
+                       kw.get("fp64_top_levels"), False, kw.get("refine_depth"),
+                       kw.get("leaf_refine"))
         P = _problem_struct(pr)
         rid = lib().hps_server_submit_build(self.ptr, ctypes.byref(P), ctypes.byref(opt))
         if rid < 0:

@@ -104,4 +104,4 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     # the same workload name as the native arm's line
     sys.path.insert(0, str(ROOT))
     import bench
-    assert line["config"]["workload"] == bench.describe_workload("convdiff64", 0)[0]["workload"]
+    assert line["config"]["workload"] == bench.describe_workload("helmholtz256", 0)[0]["workload"]
