@@ -188,6 +188,11 @@ struct LeafGroup {
   const double* coefp[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   PoolPtr rleaf = new_buf(), zleaf = new_buf();  // mixed: residual and correction
   void* gemm_leaf = nullptr;        // mixed: z = A_ii^{-1} r
+  // mixed, no mixed term: per problem of the group, the side fluxes of
+  // interior values (4q x ni, FP32), and the per-solve products h += F_i z
+  PoolPtr Fi = new_buf();
+  int prob0 = 0;
+  void* gemm_fz = nullptr;
 };
 
 // Merges of one height and one precision, across all problems.
@@ -669,7 +674,12 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
   };
   for (auto& G : H.lg) {
     G.consts = make_consts(G.p, G.q);
-    up(*G.dD, G.consts.D.data(), G.consts.D.size() * sizeof(double));
+    {  // [D | D^2]: the leaf kernels read D^2 at D + p*p
+      std::vector<double> dd(G.consts.D);
+      dd.insert(dd.end(), G.consts.D2.begin(), G.consts.D2.end());
+      up(*G.dD, dd.data(), dd.size() * sizeof(double));
+      ck(cudaStreamSynchronize(st));  // the pageable source goes out of scope
+    }
     up(*G.dPg2c, G.consts.Pg2c.data(), G.consts.Pg2c.size() * sizeof(double));
     up(*G.dPc2g, G.consts.Pc2g.data(), G.consts.Pc2g.size() * sizeof(double));
   }
@@ -738,6 +748,26 @@ void build_all(hps_handle_s& H, const std::vector<const double*>& coef_in, bool 
             ck(cudaMemsetAsync(dst, 0, n, st));
         }
       }
+    }
+  }
+  // ---- mixed mode, groups without the mixed term: per problem, the side
+  // fluxes of interior values (the refinement's h += F_i z)
+  if (H.mixed) {
+    for (auto& G : H.lg) {
+      if (G.coefp[1]) continue;
+      std::vector<float> all;
+      G.prob0 = -1;
+      for (int k = 0; k < H.nprob; ++k) {
+        const ProbInfo& pi = pl.probs[k];
+        if (pi.leaf0 < G.l0 || pi.leaf0 >= G.l0 + G.nl) continue;
+        if (G.prob0 < 0) G.prob0 = k;
+        const std::vector<float> f = interior_flux_map(G.consts, 2.0 / pi.hx, 2.0 / pi.hy);
+        all.insert(all.end(), f.begin(), f.end());
+      }
+      G.Fi->alloc(all.size() * sizeof(float), st);
+      ck(cudaMemcpyAsync(G.Fi->p, all.data(), all.size() * sizeof(float),
+                         cudaMemcpyHostToDevice, st));
+      ck(cudaStreamSynchronize(st));  // the pageable source goes out of scope
     }
   }
   // ---- leaves and merges
@@ -946,6 +976,23 @@ template <typename R>
 void push_leaf_inverse(hps_handle_s& H, LeafGroup& G, int nrhs) {
   std::vector<GemmDesc<R>> g(G.nl);
   const int ni = G.ni;
+  if (G.Fi->p) {  // h_l += F_i z_l: the flux offsets of the interior corrections
+    const Plan& pl = H.plan;
+    std::vector<GemmDesc<R, R, double>> f(G.nl);
+    for (int j = 0; j < G.nl; ++j) {
+      const int l = G.l0 + j;
+      f[j].A = G.Fi->as<R>() + (size_t)(pl.leaf_prob[l] - G.prob0) * G.nq * ni;
+      f[j].B = G.zleaf->as<R>() + (size_t)j * ni * nrhs;
+      f[j].C = H.hpool.as<double>() + pl.boxes[pl.leaf_box[l]].ext_off;
+      f[j].M = G.nq;
+      f[j].N = nrhs;
+      f[j].K = ni;
+      f[j].lda = G.nq;
+      f[j].ldb = ni;
+      f[j].ldc = (int)pl.ext_total;
+    }
+    G.gemm_fz = H.solve_st.push(f, H.stream);
+  }
   for (int j = 0; j < G.nl; ++j) {  // z_l = A_ii^{-1} r_l
     g[j].A = G.Y->as<R>() + (size_t)j * G.ys + (size_t)ni * G.nq;
     g[j].B = G.rleaf->as<R>() + (size_t)j * ni * nrhs;
@@ -980,7 +1027,7 @@ void prepare_solve(hps_handle_s& H, int nrhs) {
   }
   H.split_ws.alloc(ws, st);
   size_t bytes = 4 * 256 * (H.lev.size() + H.lg.size() + 2);
-  for (auto& G : H.lg) bytes += stage_bytes<GemmDesc<double>>(G.nl);
+  for (auto& G : H.lg) bytes += 2 * stage_bytes<GemmDesc<double>>(G.nl);
   for (auto& L : H.lev) bytes += 3 * stage_bytes<GemmDesc<double>>(L.boxes.size());
   H.solve_st.begin(bytes, st);
   if (H.mixed) {
@@ -1078,6 +1125,21 @@ void leaf_out(hps_handle_s& H, double* const* wptr, const int64_t* wrs, int nrhs
 void leaf_correction_rhs(hps_handle_s& H, const CallPtrs& cp, int nrhs) {
   cudaStream_t st = H.stream;
   for (auto& G : H.lg) {
+    if (G.gemm_fz) {
+      // no mixed term: r and the fluxes of w in one FP64 pass, z = A_ii^{-1} r,
+      // then h += F_i z (FP32 products, FP64 sums)
+      leaf_resflux<float>(G.coefp, G.l0, G.nl, G.p, G.q, H.hsc.as<double2>(), G.dD->as<double>(),
+                          G.dPc2g->as<double>(), cp.wptr, cp.wrs, nrhs, G.rleaf->as<float>(),
+                          H.leaf_off.as<int64_t>(), H.plan.ext_total, H.hpool.as<double>(), st);
+      gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f,
+                          0.0f, st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
+                          (double)G.nl * G.ni * G.ni * sizeof(float));
+      gemm_batched<float>(static_cast<GemmDesc<float, float, double>*>(G.gemm_fz), G.nl, G.nq,
+                          nrhs, 1.0f, 1.0f, st, "gemm_fluxz<f32>",
+                          2.0 * G.nl * (double)G.nq * G.ni * nrhs,
+                          (double)G.nl * nrhs * (G.ni * 4.0 + G.nq * 16.0));
+      continue;
+    }
     leaf_residual<float>(G.coefp, G.l0, G.nl, G.p, H.hsc.as<double2>(), G.dD->as<double>(),
                          cp.wptr, cp.wrs, nrhs, G.rleaf->as<float>(), st);
     gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f, 0.0f,

@@ -63,16 +63,65 @@ Consts make_consts(int p, int q) {
   // Barycentric weights of the extreme points: (-1)^j, halved at both ends.
   std::vector<double> bw(p);
   for (int j = 0; j < p; ++j) bw[j] = ((j % 2) ? -1.0 : 1.0) * ((j == 0 || j == p - 1) ? 0.5 : 1.0);
+  // Differentiation matrix.  Off-diagonal entries (bw_j / bw_i) / (t_i - t_j)
+  // with the node difference written as 2 sin(pi (i+j) / (2(p-1)))
+  // sin(pi (i-j) / (2(p-1))), free of the cancellation of t_i - t_j between
+  // the clustered end nodes; the diagonal by the negative sum of the row (rows
+  // of D annihilate constants).  The points are symmetric about 0, so D is
+  // anti-centrosymmetric, D[p-1-i][p-1-j] = -D[i][j]: the upper rows are
+  // computed and mirrored, so the symmetry holds bit for bit and kernels that
+  // split grid lines into even and odd parts apply the same D.
+  const int hr = (p + 1) / 2;  // computed rows (the centre row included for odd p)
   c.D.assign((size_t)p * p, 0.0);
-  for (int i = 0; i < p; ++i) {
+  for (int i = 0; i < hr; ++i) {
     double diag = 0.0;
     for (int j = 0; j < p; ++j) {
       if (j == i) continue;
-      double v = (bw[j] / bw[i]) / (c.t[i] - c.t[j]);
+      const double dt = 2.0 * std::sin(kPi * (i + j) / (2.0 * (p - 1))) *
+                        std::sin(kPi * (i - j) / (2.0 * (p - 1)));
+      const double v = (bw[j] / bw[i]) / dt;
       c.D[(size_t)i * p + j] = v;
-      diag -= v;  // rows of D annihilate constants
+      diag -= v;
     }
     c.D[(size_t)i * p + i] = diag;
+  }
+  if (p % 2) {  // the centre row: exactly antisymmetric, zero diagonal
+    const int m = p / 2;
+    for (int j = m + 1; j < p; ++j) c.D[(size_t)m * p + j] = -c.D[(size_t)m * p + (p - 1 - j)];
+    c.D[(size_t)m * p + m] = 0.0;
+  }
+  for (int i = hr; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      c.D[(size_t)i * p + j] = -c.D[(size_t)(p - 1 - i) * p + (p - 1 - j)];
+  // D^2 = D D.  Off-diagonal entries of the upper rows summed with explicit
+  // FMAs (the same bits on every host), mirrored into the lower rows (and the
+  // centre row's right half); the diagonal of every row by the negative sum
+  // of that row's off-diagonal entries in increasing column order.  Among the
+  // constructions compared, this one put the 32 x 32-leaf Helmholtz solution
+  // closest to the one with correctly rounded D and D^2 (the diagonal sums are
+  // where the rounding of D^2 enters the smooth part of the solution most).
+  // The mirrored rows' diagonals can differ from their mirror images by a unit
+  // in the last place; every kernel reads this one table (the even / odd ones
+  // add that difference back), so all paths apply the same operator.
+  c.D2.assign((size_t)p * p, 0.0);
+  for (int i = 0; i < hr; ++i)
+    for (int j = 0; j < p; ++j) {
+      if (j == i) continue;
+      double s = 0.0;
+      for (int k = 0; k < p; ++k) s = std::fma(c.D[(size_t)i * p + k], c.D[(size_t)k * p + j], s);
+      c.D2[(size_t)i * p + j] = s;
+    }
+  if (p % 2)
+    for (int j = p / 2 + 1; j < p; ++j)
+      c.D2[(size_t)(p / 2) * p + j] = c.D2[(size_t)(p / 2) * p + (p - 1 - j)];
+  for (int i = hr; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      if (j != i) c.D2[(size_t)i * p + j] = c.D2[(size_t)(p - 1 - i) * p + (p - 1 - j)];
+  for (int i = 0; i < p; ++i) {
+    double diag = 0.0;
+    for (int j = 0; j < p; ++j)
+      if (j != i) diag -= c.D2[(size_t)i * p + j];
+    c.D2[(size_t)i * p + i] = diag;
   }
   // Gauss-Legendre points: Newton iteration on P_q from Chebyshev-like guesses.
   c.g.resize(q);
@@ -122,6 +171,23 @@ Consts make_consts(int p, int q) {
   c.Pg2c = lagrange_matrix(c.g, c.t);  // Step 1 (per side)
   c.Pc2g = lagrange_matrix(c.t, c.g);  // Step 4 (per side)
   return c;
+}
+
+std::vector<float> interior_flux_map(const Consts& c, double sx, double sy) {
+  const int p = c.p, q = c.q, pi = p - 2, nq = 4 * q;
+  std::vector<float> F((size_t)nq * pi * pi, 0.0f);
+  for (int a = 1; a < p - 1; ++a)
+    for (int b = 1; b < p - 1; ++b) {
+      const size_t col = (size_t)((a - 1) * pi + (b - 1)) * nq;
+      for (int k = 0; k < q; ++k) {
+        const double pb = c.Pc2g[(size_t)k * p + b], pa = c.Pc2g[(size_t)k * p + a];
+        F[col + 0 * q + k] = (float)(sy * pb * c.D[a]);                        // S: row 0
+        F[col + 1 * q + k] = (float)(sx * pa * c.D[(size_t)(p - 1) * p + b]);  // E: column p-1
+        F[col + 2 * q + k] = (float)(sy * pb * c.D[(size_t)(p - 1) * p + a]);  // N: row p-1
+        F[col + 3 * q + k] = (float)(sx * pa * c.D[b]);                        // W: column 0
+      }
+    }
+  return F;
 }
 
 // ------------------------------------------------------------------ the plan

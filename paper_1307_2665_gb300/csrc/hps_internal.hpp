@@ -26,12 +26,19 @@ struct Consts {
   int p = 0, q = 0;
   std::vector<double> t;     // p Chebyshev extreme points on [-1,1], increasing
   std::vector<double> D;     // p x p differentiation matrix, row-major D[i*p+j]
+  std::vector<double> D2;    // p x p, D*D, exactly centrosymmetric
   std::vector<double> g;     // q Gauss-Legendre points on [-1,1], increasing
   std::vector<double> gw;    // their weights
   std::vector<double> Pg2c;  // p x q row-major: value at t_i of the degree q-1 interpolant
   std::vector<double> Pc2g;  // q x p row-major: value at g_k of the degree p-1 interpolant
 };
 Consts make_consts(int p, int q);
+// Side fluxes (Section 3.2, Steps 3-4: d/dy on S and N, d/dx on E and W, then
+// the side interpolant at the q Gauss points) of values at the interior
+// Chebyshev nodes only: the 4q x (p-2)^2 map L4 L3 restricted to the interior
+// columns, for a leaf with scalings sx = 2/hx, sy = 2/hy; column-major (ld 4q),
+// rows in the order S, E, N, W, columns (a-1)(p-2) + (b-1).
+std::vector<float> interior_flux_map(const Consts& c, double sx, double sy);
 
 // --------------------------------------------------------------------- plan
 // One plan may hold several independent problems (a forest): every problem

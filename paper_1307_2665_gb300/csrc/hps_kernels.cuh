@@ -149,6 +149,14 @@ template <typename R>
 void leaf_y_residual(const double* const* coef, int l0, int nl, int p, int q,
                      const double2* hsc, const double* d_D, const double* d_Pg2c, const R* Y,
                      int64_t ys, R* rbuf, cudaStream_t st);
+// Without the mixed term (c12 absent): the FP64 residual r (as leaf_residual)
+// and the fluxes of w itself, hp[r*ext_total + leaf_off[l] + g] = (L4 L3 w)_g,
+// in one pass, by even and odd parts of the grid lines.
+template <typename R>
+void leaf_resflux(const double* const* coef, int l0, int nl, int p, int q, const double2* hsc,
+                  const double* d_D, const double* d_Pc2g, double* const* wptr,
+                  const int64_t* wrs, int nrhs, R* rbuf, const int64_t* leaf_off,
+                  int64_t ext_total, double* hp, cudaStream_t st);
 template <typename R>
 void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int nl, int p, int q,
                int nrhs, const double2* hsc, const double* d_D, const double* d_Pc2g,

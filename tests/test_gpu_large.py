@@ -2,11 +2,20 @@
 256 x 256 leaves, p = 16, q = 14: 16.8 M collocation nodes), where the oracle
 cannot solve the whole system:
 
-  * the same coefficient field on 32 x 32 leaves against the oracle's solve,
-    in mixed precision (element by element, 1e-10 relative);
-  * at full size, mixed precision against FP64 (1e-10 relative), and both
-    against the oracle's leaf-local FP64 residual of (E1, E2), the continuity
-    of shared sides and the Dirichlet data, on sampled leaves.
+  * the same coefficient field on 32 x 32 and 64 x 64 leaves against the
+    oracle's solve, in both precisions (element by element, 1e-10 relative);
+  * at full size, both precisions against the oracle's leaf-local FP64
+    residual of (E1, E2), the continuity of shared sides and the Dirichlet
+    data, on sampled leaves, and mixed precision against FP64.
+
+This problem is close to resonance (the solution is about 30 times larger
+than its data) and its conditioning grows about 4.5 times per doubling of the
+leaf count.  Rounding-level changes of the differentiation matrices alone
+(correctly rounded D and D^2 against other exact-in-exact-arithmetic
+constructions) move the oracle's own solution by 1e-11 relative at 32 x 32
+leaves, so two FP64 solves of the 256 x 256 system, both with residuals at
+rounding level, differ by a few 1e-10: mixed against FP64 is held to 5e-10
+there, and the residual check carries the full-size evidence.
 """
 import numpy as np
 import pytest
@@ -38,17 +47,19 @@ def fourier(dom, n, q, nrhs, seed0=0):
                                           for s in range(nrhs)]))
 
 
-def test_helmholtz_field_32x32_mixed_vs_oracle():
-    n, p, q = 32, 16, 14
+@pytest.mark.parametrize("n", [32, 64])
+def test_helmholtz_field_vs_oracle(n):
+    p, q = 16, 14
     f = fourier(UNIT, n, q, 3)
-    h = hps.hps_build(UNIT, n, n, p, q, coeffs(UNIT, n, p, I.gaussian_bump_helmholtz),
-                      precision=hps.HPS_MIXED)
-    info = hps.SolveInfo()
-    u = hps.hps_solve(h, f, info=info)
-    h.close()
+    co = coeffs(UNIT, n, p, I.gaussian_bump_helmholtz)
     sol = O.solve_condensed(O.make_problem(UNIT, n, n, p, q, I.gaussian_bump_helmholtz), f.T)
-    err = np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w))
-    assert err < 1e-10, (err, info.iterations, info.last_update)
+    for prec in (hps.HPS_FP64, hps.HPS_MIXED):
+        h = hps.hps_build(UNIT, n, n, p, q, co, precision=prec, max_refine=30)
+        info = hps.SolveInfo()
+        u = hps.hps_solve(h, f, info=info)
+        h.close()
+        err = np.max(np.abs(u - sol.w)) / np.max(np.abs(sol.w))
+        assert err < 1e-10, (prec, err, info.iterations, info.last_update)
 
 
 def test_helmholtz_256_full_size():
@@ -71,7 +82,7 @@ def test_helmholtz_256_full_size():
                     {0, n - 1, n * (n - 1), n * n - 1, n * (n // 2) + n // 2 - 1})
     res = {name: O.sampled_residual(prob, u, f, leaves) for name, u in (("fp64", u64), ("mixed", umx))}
     msg = (rel, info.iterations, info.last_update, res)
-    assert rel < 1e-10, msg
+    assert rel < 5e-10, msg
     for r in res.values():
-        assert r["e1"] < 1e-12 and r["e2"] < 1e-12, msg
+        assert r["e1"] < 1e-14 and r["e2"] < 1e-14, msg
         assert r["cont"] < 1e-13 and r["gamma"] < 1e-13, msg
