@@ -739,13 +739,15 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
   double* T1 = T2 + npair * tw;             // npair x tw: D
   double* Pc = T1 + npair * tw;             // q x p (kFlux)
   double* Pg = Pc + (kFlux ? q * p : 0);    // p x q (kFromY)
-  double* K = Pg + (kFromY ? p * q : 0);    // 5 x pp: k11, k22, k1, k2, k0 per node
-  double* W = K + 5 * pp;                   // rb x p x lp
-  double* XE = W + rb * p * lp;             // rb x p x hq: row parts (along x)
-  double* XO = XE + rb * p * hq;
-  double* YE = XO + rb * p * hq;            // rb x h x lp: column parts (along y)
-  double* YO = YE + rb * h * lp;
-  double* Fs = YO + rb * h * lp;            // rb x 4 x p: side fluxes at the Chebyshev points
+  // per-grid strides, odd so that consecutive grids start in other banks
+  const int sW = p * lp + 1, sX = p * hq + 1, sY = h * lp + 1;
+  double* K = Pg + (kFromY ? p * q : 0);    // 6 x pp: k11, k22, k1, k2, k0, kd per node
+  double* W = K + 6 * pp;                   // rb x sW: grid (p x lp)
+  double* XE = W + rb * sW;                 // rb x sX: row parts (along x), p x hq
+  double* XO = XE + rb * sX;
+  double* YE = XO + rb * sX;                // rb x sY: column parts (along y), h x lp
+  double* YO = YE + rb * sY;
+  double* Fs = YO + rb * sY;                // rb x 4 x p: side fluxes at the Chebyshev points
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
   const double* wl = kFromY ? nullptr : wptr[l];
@@ -793,6 +795,17 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
     T2[e] = v2;
     T1[e] = v1;
   }
+  // every diagonal contribution of node (a, b) in one coefficient:
+  // kd = k11 D^2_bb + k22 D^2_aa + k1 D_bb + k2 D_aa + k0 (times w(a, b))
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    const int a = e / p, b = e % p;
+    double kd = K[4 * pp + e];
+    kd = fma(K[e], D2[b * p + b], kd);
+    kd = fma(K[pp + e], D2[a * p + a], kd);
+    kd = fma(K[2 * pp + e], D[b * p + b], kd);
+    kd = fma(K[3 * pp + e], D[a * p + a], kd);
+    K[5 * pp + e] = kd;
+  }
   const int nint = (h - 1) + odd;  // interior pairs: rows 1 .. h-1, then the centre
   const int64_t off = kFlux ? leaf_off[l] : 0;
   for (int r0 = 0; r0 < nrhs; r0 += rb) {
@@ -817,19 +830,19 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
       } else {
         v = wl[(size_t)(r0 + gi) * wstride + node];
       }
-      W[(gi * p + a) * lp + b] = v;
+      W[gi * sW + a * lp + b] = v;
     }
     __syncthreads();
     // even and odd parts of every row (along x) and every column (along y)
     for (int e = threadIdx.x; e < nb * p * h; e += blockDim.x) {
       const int gi = e / (p * h), rem = e % (p * h), line = rem / h, k = rem % h;
-      const double* Wg = W + gi * p * lp;
+      const double* Wg = W + gi * sW;
       const double x0 = Wg[line * lp + k], x1 = Wg[line * lp + p - 1 - k];
-      XE[(gi * p + line) * hq + k] = x0 + x1;
-      XO[(gi * p + line) * hq + k] = x0 - x1;
+      XE[gi * sX + line * hq + k] = x0 + x1;
+      XO[gi * sX + line * hq + k] = x0 - x1;
       const double y0 = Wg[k * lp + line], y1 = Wg[(p - 1 - k) * lp + line];
-      YE[(gi * h + k) * lp + line] = y0 + y1;
-      YO[(gi * h + k) * lp + line] = y0 - y1;
+      YE[gi * sY + k * lp + line] = y0 + y1;
+      YO[gi * sY + k * lp + line] = y0 - y1;
     }
     __syncthreads();
     // residual: one symmetric quad of interior nodes per thread and item
@@ -838,17 +851,17 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
       const int ia = qd / nint, ib = qd % nint;
       const int a0 = ia < h - 1 ? ia + 1 : c, b0 = ib < h - 1 ? ib + 1 : c;
       const int a1 = p - 1 - a0, b1 = p - 1 - b0;
-      const double* Wg = W + gi * p * lp;
+      const double* Wg = W + gi * sW;
       const double* t2a = T2 + a0 * tw;
       const double* t2b = T2 + b0 * tw;
       const double* t1a = T1 + a0 * tw;
       const double* t1b = T1 + b0 * tw;
-      const double* xe0 = XE + (gi * p + a0) * hq;
-      const double* xo0 = XO + (gi * p + a0) * hq;
-      const double* xe1 = XE + (gi * p + a1) * hq;
-      const double* xo1 = XO + (gi * p + a1) * hq;
-      const double* ye = YE + gi * h * lp;
-      const double* yo = YO + gi * h * lp;
+      const double* xe0 = XE + gi * sX + a0 * hq;
+      const double* xo0 = XO + gi * sX + a0 * hq;
+      const double* xe1 = XE + gi * sX + a1 * hq;
+      const double* xo1 = XO + gi * sX + a1 * hq;
+      const double* ye = YE + gi * sY;
+      const double* yo = YO + gi * sY;
       // second derivatives: even / odd sums of rows a0, a1 (x) and columns b0, b1 (y)
       double ex0 = 0.0, ox0 = 0.0, ex1 = 0.0, ox1 = 0.0;
       double ey0 = 0.0, oy0 = 0.0, ey1 = 0.0, oy1 = 0.0;
@@ -899,35 +912,36 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
         }
       }
       R* rl = rbuf + (size_t)jl * ni * nrhs + (size_t)(r0 + gi) * ni;
-      // node (a, b): r = k11 Dxx w + k22 Dyy w + k1 Dx w + k2 Dy w + k0 w
-      auto put = [&](int a, int b, double dxx, double dyy, double dx, double dy) {
+      // node (a, b): r = k11 X + k22 Y + k1 FX + k2 FY + kd w, with X, Y, FX,
+      // FY the off-diagonal parts of Dxx w, Dyy w, Dx w, Dy w; the mirrored
+      // node of a pair takes the odd part with the other sign (for D, the even
+      // part), the centre of odd p only the even part
+      auto put = [&](int a, int b, double X, double Y) {
         const int node = a * p + b;
-        double r = 0.0;
-        if (has11) r = fma(K[node], dxx, r);
-        if (has22) r = fma(K[pp + node], dyy, r);
-        if (has1) r = fma(K[2 * pp + node], dx, r);
-        if (has2) r = fma(K[3 * pp + node], dy, r);
-        if (has0) r = fma(K[4 * pp + node], Wg[a * lp + b], r);
-        rl[(a - 1) * pi + (b - 1)] = (R)r;
+        double r = K[5 * pp + node] * Wg[a * lp + b];
+        if (has11) r = fma(K[node], X, r);
+        if (has22) r = fma(K[pp + node], Y, r);
+        return r;
       };
-      // each node's own diagonal entries: x from pair b0 (column b0 or its
-      // mirror b1), y from pair a0 (row a0 or its mirror a1)
-      const double dxb0 = t2b[2 * h + 1], dxb1 = t2b[2 * h + 2], dyb0 = t2a[2 * h + 1],
-                   dyb1 = t2a[2 * h + 2];
-      const double fxb0 = t1b[2 * h + 1], fxb1 = t1b[2 * h + 2], fya0 = t1a[2 * h + 1],
-                   fya1 = t1a[2 * h + 2];
-      auto wv = [&](int a, int b) { return Wg[a * lp + b]; };
-      put(a0, b0, fma(dxb0, wv(a0, b0), ex0 + ox0), fma(dyb0, wv(a0, b0), ey0 + oy0),
-          fma(fxb0, wv(a0, b0), fx0 + gx0), fma(fya0, wv(a0, b0), fy0 + gy0));
-      if (b1 != b0)
-        put(a0, b1, fma(dxb1, wv(a0, b1), ex0 - ox0), fma(dyb0, wv(a0, b1), ey1 + oy1),
-            fma(fxb1, wv(a0, b1), gx0 - fx0), fma(fya0, wv(a0, b1), fy1 + gy1));
-      if (a1 != a0)
-        put(a1, b0, fma(dxb0, wv(a1, b0), ex1 + ox1), fma(dyb1, wv(a1, b0), ey0 - oy0),
-            fma(fxb0, wv(a1, b0), fx1 + gx1), fma(fya1, wv(a1, b0), gy0 - fy0));
-      if (a1 != a0 && b1 != b0)
-        put(a1, b1, fma(dxb1, wv(a1, b1), ex1 - ox1), fma(dyb1, wv(a1, b1), ey1 - oy1),
-            fma(fxb1, wv(a1, b1), gx1 - fx1), fma(fya1, wv(a1, b1), gy1 - fy1));
+      auto out = [&](int a, int b, double r) { rl[(a - 1) * pi + (b - 1)] = (R)r; };
+      if (!has1 && !has2) {
+        out(a0, b0, put(a0, b0, ex0 + ox0, ey0 + oy0));
+        if (b1 != b0) out(a0, b1, put(a0, b1, ex0 - ox0, ey1 + oy1));
+        if (a1 != a0) out(a1, b0, put(a1, b0, ex1 + ox1, ey0 - oy0));
+        if (a1 != a0 && b1 != b0) out(a1, b1, put(a1, b1, ex1 - ox1, ey1 - oy1));
+      } else {
+        auto first = [&](int a, int b, double r, double FX, double FY) {
+          const int node = a * p + b;
+          if (has1) r = fma(K[2 * pp + node], FX, r);
+          if (has2) r = fma(K[3 * pp + node], FY, r);
+          out(a, b, r);
+        };
+        first(a0, b0, put(a0, b0, ex0 + ox0, ey0 + oy0), fx0 + gx0, fy0 + gy0);
+        if (b1 != b0) first(a0, b1, put(a0, b1, ex0 - ox0, ey1 + oy1), gx0 - fx0, fy1 + gy1);
+        if (a1 != a0) first(a1, b0, put(a1, b0, ex1 + ox1, ey0 - oy0), fx1 + gx1, gy0 - fy0);
+        if (a1 != a0 && b1 != b0)
+          first(a1, b1, put(a1, b1, ex1 - ox1, ey1 - oy1), gx1 - fx1, gy1 - fy1);
+      }
     }
     if constexpr (kFlux) {
       __syncthreads();
@@ -936,11 +950,11 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
       // direction is uniform over each half of the items
       for (int e = threadIdx.x; e < 2 * nb * p; e += blockDim.x) {
         const int dir = e / (nb * p), rem = e % (nb * p), gi = rem / p, j = rem % p;
-        const double* Wg = W + gi * p * lp;
+        const double* Wg = W + gi * sW;
         double ev = 0.0, od = 0.0;
         if (dir == 0) {
-          const double* ye = YE + gi * h * lp;
-          const double* yo = YO + gi * h * lp;
+          const double* ye = YE + gi * sY;
+          const double* yo = YO + gi * sY;
           for (int k = 0; k < h; ++k) {
             ev = fma(T1[k], ye[k * lp + j], ev);
             od = fma(T1[h + k], yo[k * lp + j], od);
@@ -949,8 +963,8 @@ __global__ void __launch_bounds__(256) k_leaf_resflux(
           Fs[(gi * 4 + 0) * p + j] = sy * fma(T1[2 * h + 1], Wg[j], ev + od);
           Fs[(gi * 4 + 2) * p + j] = sy * fma(T1[2 * h + 2], Wg[(p - 1) * lp + j], od - ev);
         } else {
-          const double* xe = XE + (gi * p + j) * hq;
-          const double* xo = XO + (gi * p + j) * hq;
+          const double* xe = XE + gi * sX + j * hq;
+          const double* xo = XO + gi * sX + j * hq;
           for (int k = 0; k < h; ++k) {
             ev = fma(T1[k], xe[k], ev);
             od = fma(T1[h + k], xo[k], od);
@@ -980,8 +994,8 @@ namespace {
 int resflux_block(int p, int q, bool from_y, bool flux, int nrhs, int sm_cap, size_t* smem) {
   const int pp = p * p, h = p / 2, odd = p & 1, npair = h + odd, tw = 2 * h + 3;
   const int nint = (h - 1) + odd;
-  const int fixed = 2 * pp + 2 * npair * tw + (flux ? q * p : 0) + (from_y ? p * q : 0) + 5 * pp;
-  const int per = p * (p + 1) + 2 * p * (h + 1) + 2 * h * (p + 1) + 4 * p;
+  const int fixed = 2 * pp + 2 * npair * tw + (flux ? q * p : 0) + (from_y ? p * q : 0) + 6 * pp;
+  const int per = (p * (p + 1) + 1) + 2 * (p * (h + 1) + 1) + 2 * (h * (p + 1) + 1) + 4 * p;
   const int rbmax = std::max(1, std::min(nrhs, (sm_cap - fixed) / per));
   int best = 1;
   double best_eff = 0.0;
@@ -1013,16 +1027,18 @@ void launch_resflux(const double* const* coef, int l0, int nl, int p, int q, con
   // the attribute is a ceiling (cached per kernel); a launch asking for more
   // than it fails, and the caller's launch check reports that
   if (!opt_in_smem(kern, 200 * 1024)) return;  // reported by the caller's launch check
-  // FP64 work per leaf and grid, counted as issued: the even / odd parts
-  // (2 p h adds per direction), h-term sums per mirrored pair and derivative
-  // order present, the per-node combination; the fluxes' side pairs and
-  // Gauss interpolation
+  // FP64 flops per grid, counted as issued: the even / odd parts (2 p h adds
+  // per direction), the h-term sums of each mirrored pair per derivative
+  // (direction and order) present, per node and derivative an add (even and
+  // odd parts) and an FMA, and the diagonal coefficient times w; the fluxes'
+  // side pairs (2h-term sums, their diagonals and scalings) and the Gauss
+  // interpolation
   const int h = p / 2, odd = p & 1, nint = (h - 1) + odd;
   const double nid = (double)(p - 2) * (p - 2);
   const int orders = (coef[0] ? 1 : 0) + (coef[2] ? 1 : 0) + (coef[3] ? 1 : 0) + (coef[4] ? 1 : 0);
   double per = 4.0 * p * h + (double)nint * nint * orders * 8.0 * (h + odd) +
-               nid * 2.0 * (orders + (coef[5] ? 1 : 0));
-  if (kFlux) per += 2.0 * p * 2.0 * (2.0 * (h + odd)) + 4.0 * q * 2.0 * p;
+               nid * (3.0 * orders + 1.0);
+  if (kFlux) per += 2.0 * p * (4.0 * (h + odd) + 8.0) + 4.0 * q * 2.0 * p;
   const double in_bytes = kFromY ? nid * sizeof(R) : (double)p * p * 8.0;
   prof::Scope sc(name, st, (double)nl * nrhs * per,
                  (double)nl * (nrhs * (in_bytes + nid * sizeof(R) + (kFlux ? 32.0 * q : 0.0)) +
