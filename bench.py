@@ -333,8 +333,11 @@ def alu_peak_tflops(name, sm_mhz):
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the same kernel's launch in the same workload step; a kernel
-# changed since its capture has no entry.
-TRAFFIC_PER_LAUNCH = {}
+# changed since its capture has no entry.  leaf_resflux<f64>: captured on
+# 64 x 64 leaves with 64 right-hand sides (848.7 MB per launch, 3238 bytes per
+# leaf and right-hand side) and scaled by the 16 times as many units of a
+# 256 x 256 launch.
+TRAFFIC_PER_LAUNCH = {("helmholtz256", "leaf_resflux<f64>"): 848.7e6 * 16}
 
 
 def roofline_of(stats, t_total_ms, sm_mhz, workload=None):
