@@ -326,7 +326,8 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
     }
     GemmDesc<R>* dg = stg.push(gd, st);
     gemm_batched<R>(dg, nl, ni, nq, R(1), R(0), st, "gemm_yref<f32>",
-                    2.0 * nl * (double)ni * ni * nq, (double)nl * ni * (ni + 2.0 * nq) * sizeof(R));
+                    2.0 * nl * (double)ni * ni * nq, (double)nl * ni * (ni + 2.0 * nq) * sizeof(R),
+                    ni);
     ck(cudaGetLastError());
   }
   T0.alloc((size_t)nl * nq * nq * sizeof(R), st);
@@ -537,7 +538,7 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   if (!swf.empty()) {  // S = W [-T31^a | T32^b], FP32
     GemmDesc<R>* dg = stg.push(swf, st);
     gemm_batched<R>(dg, (int)swf.size(), swf_m, swf_n, R(1), R(0), st, "gemm_s<f32>", swf_flops,
-                    swf_bytes);
+                    swf_bytes, swf_m);
     ck(cudaGetLastError());
   }
   // FP64 products large enough go to the tensor cores (exact BF16 splitting);
@@ -563,15 +564,16 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   }
   if (!gsimt.empty()) {
     double fl = 0, by = 0;
-    int mx = 0;
+    int mx = 0, mk = 0;
     for (const auto& gg : gsimt) {
       fl += 2.0 * gg.M * (double)gg.N * gg.K;
       by += sizeof(R) * (2.0 * gg.M * (double)gg.K + 2.0 * gg.M * (double)gg.N);
       mx = std::max(mx, std::max(gg.M, gg.N));
+      mk = std::max(mk, gg.K);
     }
     GemmDesc<R>* dg = stg.push(gsimt, st);
     gemm_batched<R>(dg, (int)gsimt.size(), mx, mx, R(1), R(1), st,
-                    sizeof(R) == 8 ? "gemm_schur<f64>" : "gemm_schur<f32>", fl, by);
+                    sizeof(R) == 8 ? "gemm_schur<f64>" : "gemm_schur<f32>", fl, by, mk);
     ck(cudaGetLastError());
   }
   if (!goz.empty()) {
@@ -1133,18 +1135,18 @@ void leaf_correction_rhs(hps_handle_s& H, const CallPtrs& cp, int nrhs) {
                           H.leaf_off.as<int64_t>(), H.plan.ext_total, H.hpool.as<double>(), st);
       gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f,
                           0.0f, st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
-                          (double)G.nl * G.ni * G.ni * sizeof(float));
+                          (double)G.nl * G.ni * G.ni * sizeof(float), G.ni);
       gemm_batched<float>(static_cast<GemmDesc<float, float, double>*>(G.gemm_fz), G.nl, G.nq,
                           nrhs, 1.0f, 1.0f, st, "gemm_fluxz<f32>",
                           2.0 * G.nl * (double)G.nq * G.ni * nrhs,
-                          (double)G.nl * nrhs * (G.ni * 4.0 + G.nq * 16.0));
+                          (double)G.nl * nrhs * (G.ni * 4.0 + G.nq * 16.0), G.ni);
       continue;
     }
     leaf_residual<float>(G.coefp, G.l0, G.nl, G.p, H.hsc.as<double2>(), G.dD->as<double>(),
                          cp.wptr, cp.wrs, nrhs, G.rleaf->as<float>(), st);
     gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f, 0.0f,
                         st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
-                        (double)G.nl * G.ni * G.ni * sizeof(float));
+                        (double)G.nl * G.ni * G.ni * sizeof(float), G.ni);
     leaf_flux<float>(cp.wptr, cp.wrs, G.zleaf->as<float>(), G.l0, G.nl, G.p, G.q, nrhs,
                      H.hsc.as<double2>(), G.dD->as<double>(), G.dPc2g->as<double>(),
                      H.leaf_off.as<int64_t>(), H.plan.ext_total, H.hpool.as<double>(), st);

@@ -68,8 +68,11 @@ struct Tile {
   static constexpr int NT = NTN * NTM;
   static constexpr int LA = BM * BK / NT;  // A elements per thread and K tile
   static constexpr int LB = BK * BN / NT;  // B elements per thread and K tile
-  static constexpr int BNP = BN + 1;  // padded row of the B stage: the transposed
-                                      // store of a column hits distinct banks
+  // FP32 tiles of 4k x 4k per thread read their A and B values as float4
+  static constexpr bool kVec = sizeof(R) == 4 && TM % 4 == 0 && TN % 4 == 0;
+  // padded row of the B stage: the transposed store of a column hits distinct
+  // banks (a multiple of 4 for the vector reads)
+  static constexpr int BNP = kVec ? BN + 4 : BN + 1;
   static constexpr int STAGE = BK * BM + BK * BNP;
   static constexpr int SMEM = 2 * STAGE * (int)sizeof(R);
   static_assert(BM * BK % NT == 0 && BK * BN % NT == 0, "tile loads must divide evenly");
@@ -164,10 +167,29 @@ struct Tile {
 #pragma unroll 4
       for (int k = 0; k < (warp_live ? BK : 0); ++k) {
         R a[TM], b[TN];
+        if constexpr (kVec) {
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[k * BM + r0 + i];
+          for (int i = 0; i < TM; i += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(As + k * BM + r0 + i);
+            a[i] = v.x;
+            a[i + 1] = v.y;
+            a[i + 2] = v.z;
+            a[i + 3] = v.w;
+          }
 #pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[k * BNP + c0 + j];
+          for (int j = 0; j < TN; j += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(Bs + k * BNP + c0 + j);
+            b[j] = v.x;
+            b[j + 1] = v.y;
+            b[j + 2] = v.z;
+            b[j + 3] = v.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < TM; ++i) a[i] = As[k * BM + r0 + i];
+#pragma unroll
+          for (int j = 0; j < TN; ++j) b[j] = Bs[k * BNP + c0 + j];
+        }
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -184,10 +206,13 @@ struct Tile {
       const int gj = n0 + c0 + j;
       if (gj >= N) continue;
       TC* cp = C + gi0 + (size_t)gj * ldc;
-      if (TM == 4 && (sizeof(TC) == 4 || sizeof(TC) == 8) && gi0 + 4 <= M &&
+      if (TM % 4 == 0 && (sizeof(TC) == 4 || sizeof(TC) == 8) && gi0 + TM <= M &&
           (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
-        R v[4] = {acc[0][j], acc[1][j], acc[2][j], acc[3][j]};
-        store4(cp, v, alpha, beta);
+#pragma unroll
+        for (int i = 0; i < TM; i += 4) {
+          R v[4] = {acc[i][j], acc[i + 1][j], acc[i + 2][j], acc[i + 3][j]};
+          store4(cp + i, v, alpha, beta);
+        }
         continue;
       }
 #pragma unroll
@@ -206,6 +231,12 @@ template <typename R>
 using TileSq = Tile<R, 64, 64, 16, 4, 4>;
 template <typename R>
 using TileNarrow = Tile<R, 128, 16, 16, 4, 4>;
+// FP32 products with K >= kWideK and M >= kWideM: 8 x 8 outputs per thread
+// read with float4, half the shared-memory reads per FMA of the 4 x 4 tile
+// (whose two LDS per FMA pair cap it near half the FFMA rate); shorter
+// products would leave most of its 128 rows idle
+using TileWideF = Tile<float, 128, 64, 16, 8, 8>;
+constexpr int kWideK = 64, kWideM = 96;
 
 // ------------------------------------------------------------ explicit GEMMs
 template <typename R, class TL, typename TA, typename TB, typename TC>
@@ -294,9 +325,17 @@ void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int 
   if (max_N <= 16)
     launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name,
                                   flops, bytes, ws, ws_elems);
-  else
+  else if constexpr (sizeof(R) == 4) {
+    if (max_K >= kWideK && max_M >= kWideM)
+      launch_gemm<R, TileWideF>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name, flops,
+                                bytes, ws, ws_elems);
+    else
+      launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name,
+                                flops, bytes, ws, ws_elems);
+  } else {
     launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name, flops,
                               bytes, ws, ws_elems);
+  }
 }
 
 // ------------------------------------------------------------ LU: the panel
