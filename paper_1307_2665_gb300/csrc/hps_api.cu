@@ -309,8 +309,11 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
     // in FP64 carries only the rounding of T itself.
     R* Rb = Aii.as<R>();
     dY = Rb + (size_t)nl * ni * nq;
-    leaf_y_residual<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(),
-                       G.dPg2c->as<double>(), G.Y->as<R>(), G.ys, Rb, st);
+    if (!leaf_y_residual_tc<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(),
+                               G.dPg2c->as<double>(), G.Y->as<R>(), G.ys, Rb,
+                               H.status.as<int>(), st))
+      leaf_y_residual<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(),
+                         G.dPg2c->as<double>(), G.Y->as<R>(), G.ys, Rb, st);
     ck(cudaGetLastError());
     std::vector<GemmDesc<R>> gd(nl);
     for (int j = 0; j < nl; ++j) {
@@ -1130,9 +1133,14 @@ void leaf_correction_rhs(hps_handle_s& H, const CallPtrs& cp, int nrhs) {
     if (G.gemm_fz) {
       // no mixed term: r and the fluxes of w in one FP64 pass, z = A_ii^{-1} r,
       // then h += F_i z (FP32 products, FP64 sums)
-      leaf_resflux<float>(G.coefp, G.l0, G.nl, G.p, G.q, H.hsc.as<double2>(), G.dD->as<double>(),
-                          G.dPc2g->as<double>(), cp.wptr, cp.wrs, nrhs, G.rleaf->as<float>(),
-                          H.leaf_off.as<int64_t>(), H.plan.ext_total, H.hpool.as<double>(), st);
+      if (!leaf_resflux_tc<float>(G.coefp, G.l0, G.nl, G.p, G.q, H.hsc.as<double2>(),
+                                  G.dD->as<double>(), G.dPc2g->as<double>(), cp.wptr, cp.wrs,
+                                  nrhs, G.rleaf->as<float>(), H.leaf_off.as<int64_t>(),
+                                  H.plan.ext_total, H.hpool.as<double>(), H.status.as<int>(), st))
+        leaf_resflux<float>(G.coefp, G.l0, G.nl, G.p, G.q, H.hsc.as<double2>(),
+                            G.dD->as<double>(), G.dPc2g->as<double>(), cp.wptr, cp.wrs, nrhs,
+                            G.rleaf->as<float>(), H.leaf_off.as<int64_t>(), H.plan.ext_total,
+                            H.hpool.as<double>(), st);
       gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f,
                           0.0f, st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
                           (double)G.nl * G.ni * G.ni * sizeof(float), G.ni);
@@ -1341,6 +1349,16 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
     aa_update(cp.cols, cp.col_of, ncol, cp.nchunks, rb->F.as<double>(), rb->dWlast.as<double>(),
               rb->G.as<double>(), cp.nu, nslots, rb->coef.as<double>(), st);
     ck(cudaGetLastError());
+  }
+  {
+    // the residual's tensor-core kernel reports a wait that gave up here
+    int dev_status = 0;
+    ck(cudaMemcpyAsync(&dev_status, H.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ck(cudaStreamSynchronize(st));
+    if (dev_status < 0) {
+      g_last_error = "tensor-core residual: a wait for the tensor cores gave up";
+      throw CudaError{cudaErrorLaunchTimeout};
+    }
   }
   int iters = 0;
   double worst = 0.0;

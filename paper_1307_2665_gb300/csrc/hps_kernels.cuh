@@ -157,6 +157,19 @@ void leaf_resflux(const double* const* coef, int l0, int nl, int p, int q, const
                   const double* d_D, const double* d_Pc2g, double* const* wptr,
                   const int64_t* wrs, int nrhs, R* rbuf, const int64_t* leaf_off,
                   int64_t ext_total, double* hp, cudaStream_t st);
+// The same two passes with the derivative products on the tensor cores (exact
+// digit products, hps_residtc.cu), for p = 16, q <= 16 and operators without
+// the mixed and first-order terms; false (nothing launched) for any other
+// shape.  A tensor-core wait that gives up sets *status to -1.
+template <typename R>
+bool leaf_resflux_tc(const double* const* coef, int l0, int nl, int p, int q, const double2* hsc,
+                     const double* d_D, const double* d_Pc2g, double* const* wptr,
+                     const int64_t* wrs, int nrhs, R* rbuf, const int64_t* leaf_off,
+                     int64_t ext_total, double* hp, int* status, cudaStream_t st);
+template <typename R>
+bool leaf_y_residual_tc(const double* const* coef, int l0, int nl, int p, int q,
+                        const double2* hsc, const double* d_D, const double* d_Pg2c, const R* Y,
+                        int64_t ys, R* rbuf, int* status, cudaStream_t st);
 template <typename R>
 void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int nl, int p, int q,
                int nrhs, const double2* hsc, const double* d_D, const double* d_Pc2g,
