@@ -47,6 +47,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "hps_kernels.cuh"
 #include "hps_prof.hpp"
@@ -71,6 +72,8 @@ constexpr int kRDiag = 8;              // diagonals d = 2 .. 9
 constexpr int kRCols = 2 * kRDiag * kRP;  // TMEM columns: x and y accumulators
 constexpr int kRWp = kRP + 1;          // padded row pitch of the FP64 tiles (doubles)
 constexpr int kRGs = kRP * kRWp;       // one grid
+constexpr int kRFlB = 4;               // blocks per interpolation of the side derivatives
+constexpr int kRFl = kRFlB * kRG * 4;  // lines per interpolation: 128 = M
 constexpr int kASliceB = 128 * kRP * 2;  // bytes of one A digit slice (4 KB)
 constexpr int kBSliceB = kRP * kRP * 2;  // bytes of one B digit slice (512 B)
 constexpr long kRSpin = 1L << 20;      // bound of every wait (iterations)
@@ -200,18 +203,58 @@ __device__ __forceinline__ double u_to_double(int A1, int A2, int A3, int A4, in
   return __longlong_as_double((long long)b);
 }
 
+// A float as a double by integer instructions (normal numbers and zeros; the
+// conversion instruction for the rest).
+__device__ __forceinline__ double f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) {
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)(u & 0x80000000u) << 32);
+    return (double)f;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ex + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// A double rounded to the nearest float by integer instructions (the
+// conversion instruction for zeros below the float range, infinities, NaN).
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ff) - 1023;
+  if ((b << 1) == 0ULL) return __uint_as_float(sign);
+  if (E < -126 || E == 1024) return (float)x;
+  if (E > 127) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long mant = b & 0xfffffffffffffULL;
+  uint32_t m = (uint32_t)(mant >> 29);
+  const uint32_t rem = (uint32_t)mant & 0x1fffffffu;
+  m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  return __uint_as_float(sign | (((uint32_t)(E + 127) << 23) + m));  // a carry raises E
+}
+template <typename R>
+__device__ __forceinline__ R to_r(double x) {
+  if constexpr (sizeof(R) == 4)
+    return d2f(x);
+  else
+    return x;
+}
+
 // Eight outputs of one TMEM lane: columns c0 .. c0 + 7 of the eight diagonal
 // accumulators starting at column tb, as doubles scaled by 2^(e + f_n + 2 - 72).
 __device__ __forceinline__ void drain8(uint32_t tb, int c0, int e, const int* fn, double* out) {
   int A[4][8];
 #pragma unroll
-  for (int pd = 0; pd < kRDiag / 2; ++pd) {  // diagonals 2 pd + 2 and 2 pd + 3
-    uint32_t ve[8], vo[8];
-    tc::ld8(tb + (uint32_t)(2 * pd * kRP + c0), ve);
-    tc::ld8(tb + (uint32_t)((2 * pd + 1) * kRP + c0), vo);
+  for (int h = 0; h < 2; ++h) {  // diagonals 4 h + 2 .. 4 h + 5, one wait
+    uint32_t v[4][8];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) tc::ld8(tb + (uint32_t)((4 * h + t) * kRP + c0), v[t]);
     tc::wait_ld();
 #pragma unroll
-    for (int n = 0; n < 8; ++n) A[pd][n] = pair_acc(acc_bits(ve[n]), acc_bits(vo[n]));
+    for (int n = 0; n < 8; ++n) {
+      A[2 * h][n] = pair_acc(acc_bits(v[0][n]), acc_bits(v[1][n]));
+      A[2 * h + 1][n] = pair_acc(acc_bits(v[2][n]), acc_bits(v[3][n]));
+    }
   }
 #pragma unroll
   for (int n = 0; n < 8; ++n)
@@ -223,17 +266,20 @@ __device__ __forceinline__ void drain8(uint32_t tb, int c0, int e, const int* fn
 // ------------------------------------------------------------------ kernel
 // One CTA per leaf (two per SM), blocks of 8 grids (right-hand sides).  Per
 // block:
-//   1. warp g reads grid g into shared memory (FP64) and finds e_g;
+//   1. warp g moves grid g (loaded one block ahead) into shared memory and
+//      finds e_g;
 //   2. each thread writes the digits of 8 values of one row of the x and of
 //      the y operand;
 //   3. thread 0 issues the 70 products and commits them to an mbarrier;
 //   4. every warp drains 8 columns of its TMEM lane quadrant, first of the y
 //      accumulators (Y and the side derivatives d/dy to shared memory), then
 //      of the x accumulators, forming r = k11 X + k22 Y + k0 w at once;
-//   5. the Gauss interpolation of the fluxes (stored to hp) and the coalesced
-//      store of r.
-// After the products are complete the operand buffer holds Y, the side
-// derivatives and r.
+//   5. the coalesced store of r.
+// kFlux: the side derivatives of 4 blocks (32 grids x 4 sides = 128 lines of
+// 16 values) are interpolated to the Gauss points as one more digit product
+// (M = 128 lines, N = 16 rows of Pc2g, K = 16), which every warp drains.
+// After the products are complete the operand buffer holds Y and r, then the
+// digits of the lines.
 template <typename R, bool kFromY, bool kFlux>
 __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
     CoefPtrs cp, int l0, int q, const double2* __restrict__ hsc, const double* __restrict__ gD,
@@ -242,20 +288,23 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
     int64_t ys, const int64_t* __restrict__ leaf_off, int64_t ext_total, double* __restrict__ hp,
     int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smraw[];
-  unsigned char* As = smraw;                                     // x, y: 7 digit slices each
-  unsigned char* Bs = As + 2 * kRSA * kASliceB;                  // 8 digit slices
-  double* W = reinterpret_cast<double*>(Bs + kRSB * kBSliceB);   // 8 grids of 16 x 17
-  double* Kc = W + kRG * kRGs;                                   // k11, k22, k0: 16 x 17 each
-  double* Pm = Kc + 3 * kRGs;  // Pc2g (q rows of pitch 17) | Pg2c (16 x q)
+  unsigned char* As = smraw;                     // x, y: 7 digit slices each
+  unsigned char* Bs = As + 2 * kRSA * kASliceB;  // 8 digit slices of the table
+  unsigned char* Bp = Bs + kRSB * kBSliceB;      // kFlux: 8 digit slices of Pc2g
+  double* W = reinterpret_cast<double*>(Bp + (kFlux ? kRSB * kBSliceB : 0));  // 8 grids, 16 x 17
+  double* Kc = W + kRG * kRGs;                   // k11, k22, k0: 16 x 17 each
+  double* Fq = Kc + 3 * kRGs;                    // kFlux: 128 lines of pitch 17
+  double* Pm = Fq + (kFlux ? kRFl * kRWp : 0);   // kFromY: Pg2c (16 x q)
   // aliases of the operand buffer, live from the end of the products to the
-  // next block's digits
-  double* Ys = reinterpret_cast<double*>(As);                    // 8 grids of 16 x 17
-  double* Fs = Ys + kRG * kRGs;                                  // 8 grids x 4 sides x 16
-  R* Rs = reinterpret_cast<R*>(Fs + kRG * 4 * kRP);              // 8 grids x 196
+  // next digits written there
+  double* Ys = reinterpret_cast<double*>(As);    // 8 grids of 16 x 17
+  R* Rs = reinterpret_cast<R*>(Ys + kRG * kRGs);  // 8 grids x 196
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
   __shared__ int eg[kRG];
   __shared__ int fn[kRP];
+  __shared__ int fq[kRP];   // kFlux: exponents of the rows of Pc2g
+  __shared__ int el[kRFl];  // kFlux: exponents of the 128 lines
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int jl = blockIdx.x, l = l0 + jl;  // group-local and global leaf
   const double sx = hsc[l].x, sy = hsc[l].y;
@@ -274,6 +323,17 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
     if (n == 0 || n == kRP - 1) return gD[n * kRP + k];
     return gD[kRPP + n * kRP + k];  // D^2 follows D
   };
+  // kFlux: row n of Pc2g (q x 16), zero rows after it
+  auto prow = [&](int n, int k) -> double { return n < q ? gPm[n * kRP + k] : 0.0; };
+  auto row_exp = [&](int n, bool pc) {
+    uint32_t hm = 0;
+    for (int k = 0; k < kRP; ++k)
+      hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(pc ? prow(n, k)
+                                                                         : brow(n, k)) >>
+                              32) &
+                       0x7fffffffu);
+    return exp_bound(hm);
+  };
   for (int e = tid; e < kRPP; e += kRThreads) {
     const size_t g = (size_t)jl * kRPP + e;
     const int t = (e >> 4) * kRWp + (e & 15);
@@ -281,27 +341,23 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
     Kc[kRGs + t] = cp.c[2] ? cp.c[2][g] * sy * sy : 0.0;
     Kc[2 * kRGs + t] = cp.c[5] ? -cp.c[5][g] : 0.0;
   }
-  for (int e = tid; e < kRP * q; e += kRThreads) {
-    if constexpr (kFlux)
-      Pm[(e >> 4) * kRWp + (e & 15)] = gPm[e];
-    else
-      Pm[e] = gPm[e];
-  }
-  if (tid < kRP) {
-    uint32_t hm = 0;
-    for (int k = 0; k < kRP; ++k)
-      hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(brow(tid, k)) >> 32) &
-                       0x7fffffffu);
-    fn[tid] = exp_bound(hm);
-  }
+  if constexpr (kFromY)
+    for (int e = tid; e < kRP * q; e += kRThreads) Pm[e] = gPm[e];
+  if (tid < kRP) fn[tid] = row_exp(tid, false);
+  if constexpr (kFlux)
+    if (tid >= 32 && tid < 32 + kRP) fq[tid - 32] = row_exp(tid - 32, true);
   __syncthreads();
-  // digits of the table: thread (n, half) writes 8 entries of row n per slice
-  if (tid < 2 * kRP) {
-    const int n = tid >> 1, half = tid & 1;
+  // digits of the tables: thread (n, half) writes 8 entries of row n per slice
+  if (tid < 2 * kRP || (kFlux && tid >= 64 && tid < 64 + 2 * kRP)) {
+    const bool pc = tid >= 64;
+    const int n = (tid & 63) >> 1, half = tid & 1;
     unsigned long long G[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) G[j] = fixed_point<62, kRSB>(brow(n, half * 8 + j), fn[n]);
-    const uint32_t base = tc::smem_u32(Bs + op_off(n, half * 8) * 2);
+    for (int j = 0; j < 8; ++j) {
+      const int k = half * 8 + j;
+      G[j] = fixed_point<62, kRSB>(pc ? prow(n, k) : brow(n, k), pc ? fq[n] : fn[n]);
+    }
+    const uint32_t base = tc::smem_u32((pc ? Bp : Bs) + op_off(n, half * 8) * 2);
 #pragma unroll
     for (int t = 1; t <= kRSB; ++t) store_slice<kRSB>(base + (t - 1) * kBSliceB, G, t);
   }
@@ -314,35 +370,64 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
   const int rg = row >> 4, ri = row & 15;
   const int c0 = 8 * (warp >> 2);          // the 8 columns this warp drains
   const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  // the values of grid `warp` of a block held by this lane (nodes lane + 32 j),
+  // loaded one block ahead so that the loads run during the previous block
+  using PreT = typename std::conditional<kFromY, R, double>::type;
+  PreT pre[kRPP / 32];
+  auto fetch = [&](int rb0) {
+    const int g = rb0 + warp;
+#pragma unroll
+    for (int j = 0; j < kRPP / 32; ++j) {
+      const int node = lane + 32 * j, a = node >> 4, b = node & 15;
+      PreT v = PreT(0);
+      if (g < nrhs) {
+        if constexpr (kFromY) {
+          if (a > 0 && a < kRP - 1 && b > 0 && b < kRP - 1)
+            v = Ysrc[(size_t)jl * ys + (a - 1) * (kRP - 2) + (b - 1) + (size_t)g * kRNi];
+        } else {
+          v = wl[(size_t)g * wstride + node];
+        }
+      }
+      pre[j] = v;
+    }
+  };
+  // one commit per product batch; waits take the parity of the next phase
+  uint32_t phase = 0;
+  auto products_done = [&]() -> bool {
+    const bool ok = tc::mbar_wait(&bar, phase, kRSpin);
+    if (__syncthreads_or(!ok)) return false;
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return true;
+  };
+  fetch(0);
   bool fail = false;
   int blk = 0;
   for (int r0 = 0; r0 < nrhs; r0 += kRG, ++blk) {
     const int nb = min(kRG, nrhs - r0);
     // ---- 1. grid `warp` into shared memory, its exponent
     {
-      const int gi = warp;
+      const int gi = warp, g = r0 + gi;
       uint32_t hm = 0;
 #pragma unroll
       for (int j = 0; j < kRPP / 32; ++j) {
         const int node = lane + 32 * j, a = node >> 4, b = node & 15;
-        double v = 0.0;
-        if (gi < nb) {
-          if constexpr (kFromY) {
-            const int g = r0 + gi;
-            if (a > 0 && a < kRP - 1 && b > 0 && b < kRP - 1) {
-              v = (double)Ysrc[(size_t)jl * ys + (a - 1) * (kRP - 2) + (b - 1) + (size_t)g * kRNi];
-            } else {  // column g is Gauss node k of side s: L1's entry at this node
-              const int s = g / q, k = g % q;
-              int jj = -1;
-              if (s == 0 && a == 0) jj = b;
-              if (s == 2 && a == kRP - 1) jj = b;
-              if (s == 1 && b == kRP - 1) jj = a;
-              if (s == 3 && b == 0) jj = a;
-              if (jj >= 0) v = ((jj == 0 || jj == kRP - 1) ? 0.5 : 1.0) * Pm[jj * q + k];
-            }
-          } else {
-            v = wl[(size_t)(r0 + gi) * wstride + node];
+        double v;
+        if constexpr (kFromY) {
+          if (a > 0 && a < kRP - 1 && b > 0 && b < kRP - 1) {
+            v = sizeof(R) == 4 ? f2d((float)pre[j]) : (double)pre[j];
+          } else {  // column g is Gauss node k of side s: L1's entry at this node
+            v = 0.0;
+            const int s = g / q, k = g % q;
+            int jj = -1;
+            if (s == 0 && a == 0) jj = b;
+            if (s == 2 && a == kRP - 1) jj = b;
+            if (s == 1 && b == kRP - 1) jj = a;
+            if (s == 3 && b == 0) jj = a;
+            if (jj >= 0 && gi < nb) v = ((jj == 0 || jj == kRP - 1) ? 0.5 : 1.0) * Pm[jj * q + k];
           }
+        } else {
+          v = pre[j];
         }
         W[gi * kRGs + a * kRWp + b] = v;
         hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(v) >> 32) & 0x7fffffffu);
@@ -350,6 +435,7 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
       hm = __reduce_max_sync(0xffffffffu, hm);
       if (lane == 0) eg[gi] = exp_bound(hm);
     }
+    fetch(r0 + kRG);  // the next block's values, in flight during this block
     __syncthreads();
     // ---- 2. digits of the x operand (row (g, a), K = b) and of the y operand
     // (row (g, b), K = a): thread (row, half) writes 8 values per slice
@@ -392,12 +478,11 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
         }
       tc::commit(&bar);
     }
-    const bool ok = tc::mbar_wait(&bar, (uint32_t)(blk & 1), kRSpin);
-    if (__syncthreads_or(!ok)) {
+    if (!products_done()) {
       fail = true;
       break;
     }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int slot = blk & (kRFlB - 1);  // kFlux: this block's lines in Fq
     // ---- 4a. y: this lane is column b = ri of grid rg; outputs n = c0 .. c0 + 7
     // are Y(n, b) (n = 1 .. 14), d/dy at row 0 (n = 0) and at row 15 (n = 15)
     {
@@ -410,9 +495,10 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
           if (n >= 1 && n <= kRP - 2) Ys[rg * kRGs + n * kRWp + ri] = out[j];
         }
       }
-      if constexpr (kFlux) {
-        if (c0 == 0) Fs[(rg * 4 + 0) * kRP + ri] = sy * out[0];  // S
-        else Fs[(rg * 4 + 2) * kRP + ri] = sy * out[7];          // N
+      if constexpr (kFlux) {  // lines S (0) and N (2) of grid rg
+        double* F = Fq + (slot * kRG * 4 + rg * 4) * kRWp + ri;
+        if (c0 == 0) F[0] = out[0];
+        else F[2 * kRWp] = out[7];
       }
     }
     __syncthreads();
@@ -434,36 +520,93 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
             double r = Kr[2 * kRGs + n] * Wr[n];
             r = fma(Kr[kRGs + n], Yr[n], r);
             r = fma(Kr[n], out[j], r);
-            rr[n] = (R)r;
+            rr[n] = to_r<R>(r);
           }
         }
       }
-      if constexpr (kFlux) {
-        if (c0 == 0) Fs[(rg * 4 + 3) * kRP + ri] = sx * out[0];  // W
-        else Fs[(rg * 4 + 1) * kRP + ri] = sx * out[7];          // E
+      if constexpr (kFlux) {  // lines E (1) and W (3) of grid rg
+        double* F = Fq + (slot * kRG * 4 + rg * 4) * kRWp + ri;
+        if (c0 == 0) F[3 * kRWp] = out[0];
+        else F[kRWp] = out[7];
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    // ---- 5. fluxes at the Gauss points (sides S, E, N, W), r of the block
+    // ---- 5. r of the block, coalesced (grids r0 .. r0 + nb - 1 are contiguous)
+    {
+      R* rdst = rbuf + (size_t)jl * kRNi * nrhs + (size_t)r0 * kRNi;
+      for (int e = tid; e < nb * kRNi; e += kRThreads) rdst[e] = Rs[e];
+    }
+    // ---- kFlux, every 4 blocks and after the last: the lines at the Gauss
+    // points, (L4 L3 w)(s, k) = scale_s sum_j Pc2g[k][j] line_s[j]
     if constexpr (kFlux) {
-      for (int e = tid; e < nb * 4 * q; e += kRThreads) {
-        const int gi = e / (4 * q), gq = e % (4 * q), s = gq / q, k = gq % q;
-        const double* F = Fs + (gi * 4 + s) * kRP;
-        const double* P = Pm + k * kRWp;
-        double acc = 0.0;
+      if (slot == kRFlB - 1 || r0 + kRG >= nrhs) {
+        __syncthreads();  // r has left the operand buffer
+        {
+          const int line = tid >> 1, half = tid & 1;
+          const double* src = Fq + line * kRWp + half * 8;
+          double v[8];
+          uint32_t hm = 0;
 #pragma unroll
-        for (int j = 0; j < kRP; ++j) acc = fma(P[j], F[j], acc);
-        hp[(size_t)(r0 + gi) * ext_total + off + gq] = acc;
+          for (int j = 0; j < 8; ++j) {
+            v[j] = src[j];
+            hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(v[j]) >> 32) &
+                             0x7fffffffu);
+          }
+          hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));
+          const int e = exp_bound(hm);
+          if (half == 0) el[line] = e;
+          unsigned long long G[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) G[j] = fixed_point<56, kRSA>(v[j], e);
+          const uint32_t base = tc::smem_u32(As + op_off(line, half * 8) * 2);
+#pragma unroll
+          for (int s = 1; s <= kRSA; ++s) store_slice<kRSA>(base + (s - 1) * kASliceB, G, s);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bp);
+          constexpr uint32_t idesc = tc::idesc_bf16(128, kRP);
+          for (int d = 2; d <= kRDiag + 1; ++d) {
+            uint32_t acc = 0;
+            for (int s = max(1, d - kRSB); s <= min(kRSA, d - 1); ++s) {
+              const uint64_t da = tc::desc_kmajor(a0 + (uint32_t)((s - 1) * kASliceB), 128, 256);
+              const uint64_t db =
+                  tc::desc_kmajor(b0 + (uint32_t)((d - s - 1) * kBSliceB), 128, 256);
+              tc::mma_bf16(tmem + (uint32_t)((d - 2) * kRP), da, db, idesc, acc);
+              acc = 1;
+            }
+          }
+          tc::commit(&bar);
+        }
+        if (!products_done()) {
+          fail = true;
+          break;
+        }
+        {
+          // lane = line (block slot, grid, side); outputs: Gauss points c0 .. c0 + 7
+          double out[8];
+          drain8(tmem + tlane, c0, el[row], fq, out);
+          const int sl = row >> 5, g = (row >> 2) & 7, s = row & 3;
+          const int grid = r0 - slot * kRG + sl * kRG + g;
+          if (grid < nrhs) {
+            const double sc = (s & 1) ? sx : sy;
+            double* dst = hp + (size_t)grid * ext_total + off + s * q;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (c0 + j < q) dst[c0 + j] = sc * out[j];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       }
     }
-    R* rdst = rbuf + (size_t)jl * kRNi * nrhs + (size_t)r0 * kRNi;
-    for (int e = tid; e < nb * kRNi; e += kRThreads) rdst[e] = Rs[e];
   }
   if (fail && tid == 0) {
-    // the products of the block that gave up may still be in flight: let them
-    // finish (bounded) before the tensor memory is released
-    tc::mbar_wait(&bar, (uint32_t)(blk & 1), kRSpin);
+    // the products that gave up may still be in flight: let them finish
+    // (bounded) before the tensor memory is released
+    tc::mbar_wait(&bar, phase, kRSpin);
     if (status) atomicCAS(status, 0, -1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -475,8 +618,9 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
 // ------------------------------------------------------------------ host
 template <typename R, bool kFlux>
 size_t resid_tc_smem(int q) {
-  return (size_t)2 * kRSA * kASliceB + (size_t)kRSB * kBSliceB +
-         sizeof(double) * ((size_t)kRG * kRGs + 3 * kRGs + (kFlux ? (size_t)q * kRWp : (size_t)kRP * q));
+  return (size_t)2 * kRSA * kASliceB + (size_t)(kFlux ? 2 : 1) * kRSB * kBSliceB +
+         sizeof(double) * ((size_t)kRG * kRGs + 3 * kRGs +
+                           (kFlux ? (size_t)kRFl * kRWp : (size_t)kRP * q));
 }
 
 // The operator and leaf shape the kernel takes: p = 16, q <= 16, no mixed or
@@ -491,9 +635,8 @@ void launch_resid_tc(const double* const* coef, int l0, int nl, int q, const dou
                      const int64_t* wrs, int nrhs, R* rbuf, const R* Y, int64_t ys,
                      const int64_t* leaf_off, int64_t ext_total, double* hp, int* status,
                      const char* name, cudaStream_t st) {
-  static_assert((size_t)kRG * kRGs * 8 + kRG * 4 * kRP * 8 + kRG * kRNi * sizeof(R) <=
-                    (size_t)2 * kRSA * kASliceB,
-                "Y, the side derivatives and r fit in the operand buffer");
+  static_assert((size_t)kRG * kRGs * 8 + kRG * kRNi * sizeof(R) <= (size_t)2 * kRSA * kASliceB,
+                "Y and r fit in the operand buffer");
   if (nl <= 0 || nrhs <= 0) return;
   CoefPtrs cp;
   for (int k = 0; k < 6; ++k) cp.c[k] = coef[k];
