@@ -20,8 +20,8 @@ CSRC = PKG / "csrc"
 OUT_DIR = PKG / "_lib"
 LIB = OUT_DIR / "libhps.so"
 SOURCES = ["hps_host.cpp", "hps_prof.cpp", "hps_linalg.cu", "hps_leaf.cu", "hps_merge.cu",
-           "hps_refine.cu", "hps_ozaki.cu", "hps_residtc.cu", "hps_post.cu", "hps_api.cu",
-           "hps_serve.cpp"]
+           "hps_refine.cu", "hps_ozaki.cu", "hps_residtc.cu", "hps_gemmtc.cu", "hps_post.cu",
+           "hps_api.cu", "hps_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(ROOT / "include")]
 

@@ -330,7 +330,7 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
     GemmDesc<R>* dg = stg.push(gd, st);
     gemm_batched<R>(dg, nl, ni, nq, R(1), R(0), st, "gemm_yref<f32>",
                     2.0 * nl * (double)ni * ni * nq, (double)nl * ni * (ni + 2.0 * nq) * sizeof(R),
-                    ni);
+                    ni, nullptr, 0, H.status.as<int>());
     ck(cudaGetLastError());
   }
   T0.alloc((size_t)nl * nq * nq * sizeof(R), st);
@@ -541,7 +541,7 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
   if (!swf.empty()) {  // S = W [-T31^a | T32^b], FP32
     GemmDesc<R>* dg = stg.push(swf, st);
     gemm_batched<R>(dg, (int)swf.size(), swf_m, swf_n, R(1), R(0), st, "gemm_s<f32>", swf_flops,
-                    swf_bytes, swf_m);
+                    swf_bytes, swf_m, nullptr, 0, H.status.as<int>());
     ck(cudaGetLastError());
   }
   // FP64 products large enough go to the tensor cores (exact BF16 splitting);
@@ -576,7 +576,8 @@ void build_level(hps_handle_s& H, LevelGroup& L, Stager& stg, std::vector<TRef>&
     }
     GemmDesc<R>* dg = stg.push(gsimt, st);
     gemm_batched<R>(dg, (int)gsimt.size(), mx, mx, R(1), R(1), st,
-                    sizeof(R) == 8 ? "gemm_schur<f64>" : "gemm_schur<f32>", fl, by, mk);
+                    sizeof(R) == 8 ? "gemm_schur<f64>" : "gemm_schur<f32>", fl, by, mk, nullptr,
+                    0, H.status.as<int>());
     ck(cudaGetLastError());
   }
   if (!goz.empty()) {
@@ -1078,7 +1079,7 @@ void down_level(hps_handle_s& H, LevelGroup& L, int nrhs, bool with_z) {
   R* ws = split_ws<R>(H, &wse);
   gemm_batched<R>(static_cast<GemmDesc<R, double, double>*>(L.gemm_down), nm, L.max_m, nrhs, R(1),
                   with_z ? R(1) : R(0), st, sizeof(R) == 8 ? "gemm_solve<f64>" : "gemm_solve<f32>",
-                  L.down_flops1 * nrhs, L.down_bytes, L.max_ne, ws, wse);
+                  L.down_flops1 * nrhs, L.down_bytes, L.max_ne, ws, wse, H.status.as<int>());
   solve_child_scatter(L.scatter, nm, L.max_nanb, H.u3.as<double>(), H.u3_total,
                       H.uext.as<double>(), H.plan.ext_total, nrhs, st);
 }
@@ -1143,18 +1144,21 @@ void leaf_correction_rhs(hps_handle_s& H, const CallPtrs& cp, int nrhs) {
                             H.hpool.as<double>(), st);
       gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f,
                           0.0f, st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
-                          (double)G.nl * G.ni * G.ni * sizeof(float), G.ni);
+                          (double)G.nl * G.ni * G.ni * sizeof(float), G.ni, nullptr, 0,
+                          H.status.as<int>());
       gemm_batched<float>(static_cast<GemmDesc<float, float, double>*>(G.gemm_fz), G.nl, G.nq,
                           nrhs, 1.0f, 1.0f, st, "gemm_fluxz<f32>",
                           2.0 * G.nl * (double)G.nq * G.ni * nrhs,
-                          (double)G.nl * nrhs * (G.ni * 4.0 + G.nq * 16.0), G.ni);
+                          (double)G.nl * nrhs * (G.ni * 4.0 + G.nq * 16.0), G.ni, nullptr, 0,
+                          H.status.as<int>());
       continue;
     }
     leaf_residual<float>(G.coefp, G.l0, G.nl, G.p, H.hsc.as<double2>(), G.dD->as<double>(),
                          cp.wptr, cp.wrs, nrhs, G.rleaf->as<float>(), st);
     gemm_batched<float>(static_cast<GemmDesc<float>*>(G.gemm_leaf), G.nl, G.ni, nrhs, 1.0f, 0.0f,
                         st, "gemm_leafinv<f32>", 2.0 * G.nl * (double)G.ni * G.ni * nrhs,
-                        (double)G.nl * G.ni * G.ni * sizeof(float), G.ni);
+                        (double)G.nl * G.ni * G.ni * sizeof(float), G.ni, nullptr, 0,
+                        H.status.as<int>());
     leaf_flux<float>(cp.wptr, cp.wrs, G.zleaf->as<float>(), G.l0, G.nl, G.p, G.q, nrhs,
                      H.hsc.as<double2>(), G.dD->as<double>(), G.dPc2g->as<double>(),
                      H.leaf_off.as<int64_t>(), H.plan.ext_total, H.hpool.as<double>(), st);
@@ -1178,14 +1182,14 @@ void up_level(hps_handle_s& H, LevelGroup& L, int nrhs) {
   }
   gemm_batched<R>(static_cast<GemmDesc<R>*>(L.gemm_w), nm, L.max_m, nrhs, R(1), R(0), st,
                   sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flw, 0.0, L.max_m, ws,
-                  wse);
+                  wse, H.status.as<int>());
   // parents' flux offsets: [h1^a; h2^b] copied for every merge (a root's copy
   // is never read and costs little), the product only where a parent reads it
   merge_hpar(L.body, nm, L.max_ne, H.hpool.as<double>(), pl.ext_total, nrhs, st);
   if (L.n_hpar == 0) return;
   gemm_batched<R>(static_cast<GemmDesc<R, R, double>*>(L.gemm_hpar), L.n_hpar, L.max_ne, nrhs, R(1),
                   R(1), st, sizeof(R) == 8 ? "gemm_body<f64>" : "gemm_body<f32>", flc, 0.0,
-                  L.max_m, ws, wse);
+                  L.max_m, ws, wse, H.status.as<int>());
 }
 
 // Least-squares weights of one column: minimise ||F - sum_s g_s dF_s|| over
@@ -1246,6 +1250,18 @@ struct ColState {
   std::vector<double> A, b;                    // Gram matrix and right-hand side by slot
 };
 
+// The tensor-core kernels of a mixed solve (FP32 products, FP64 residual)
+// report a wait that gave up in the status word: read it (synchronises).
+void check_tc_status(hps_handle_s& H) {
+  int dev_status = 0;
+  ck(cudaMemcpyAsync(&dev_status, H.status.p, sizeof(int), cudaMemcpyDeviceToHost, H.stream));
+  ck(cudaStreamSynchronize(H.stream));
+  if (dev_status < 0) {
+    g_last_error = "tensor-core kernel: a wait for the tensor cores gave up";
+    throw CudaError{cudaErrorLaunchTimeout};
+  }
+}
+
 int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
               hps_solve_info* info) {
   cudaStream_t st = H.stream;
@@ -1254,7 +1270,11 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
   downward(H, nrhs, false);
   leaf_out(H, cp.wptr, cp.wrs, nrhs, false);
   ck(cudaGetLastError());
-  if (!H.mixed || H.opt.max_refine == 0) return HPS_OK;
+  if (!H.mixed) return HPS_OK;
+  if (H.opt.max_refine == 0) {
+    check_tc_status(H);
+    return HPS_OK;
+  }
   // ---- iterative refinement against the FP64 residual, Anderson-accelerated
   // per column (problem, right-hand side); columns finish independently
   const int m = H.opt.refine_depth;
@@ -1350,16 +1370,7 @@ int solve_all(hps_handle_s& H, const CallPtrs& cp, RefineBufs* rb, int nrhs,
               rb->G.as<double>(), cp.nu, nslots, rb->coef.as<double>(), st);
     ck(cudaGetLastError());
   }
-  {
-    // the residual's tensor-core kernel reports a wait that gave up here
-    int dev_status = 0;
-    ck(cudaMemcpyAsync(&dev_status, H.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    ck(cudaStreamSynchronize(st));
-    if (dev_status < 0) {
-      g_last_error = "tensor-core residual: a wait for the tensor cores gave up";
-      throw CudaError{cudaErrorLaunchTimeout};
-    }
-  }
+  check_tc_status(H);
   int iters = 0;
   double worst = 0.0;
   bool ok = true;

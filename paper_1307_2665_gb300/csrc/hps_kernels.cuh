@@ -112,10 +112,23 @@ constexpr int kSplitK = 128;
 inline size_t split_ws_elems(int nd, int max_M, int max_N, int max_K) {
   return max_K > kSplitK ? (size_t)nd * ((max_K + kSplitK - 1) / kSplitK) * max_M * max_N : 0;
 }
+// With a status word, FP32 products (A and B in FP32) with M >= 96 and K >= 32
+// run on the tensor cores (gemm_tc32), the others on the FP32 tile kernels;
+// the choice (and the tensor-core tile width) depends on each product's own
+// shape only, never on the other products of the launch.  Without a status
+// word all run on the tile kernels.
+__host__ __device__ constexpr bool gemm_on_tc(int M, int K) { return M >= 96 && K >= 32; }
 template <typename R, typename TA, typename TB, typename TC>
 void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
                   R beta, cudaStream_t st, const char* name, double flops, double bytes,
-                  int max_K = 0, R* ws = nullptr, size_t ws_elems = 0);
+                  int max_K = 0, R* ws = nullptr, size_t ws_elems = 0, int* status = nullptr);
+// C = beta C + alpha A B in FP32 accuracy on the tensor cores (hps_gemmtc.cu):
+// every FP32 operand split exactly into three BF16 terms, six BF16 products
+// per K step accumulated in FP32.  A wait that gives up sets *status to -1.
+// Products of the list for which gemm_on_tc holds; the others are skipped.
+template <typename TB, typename TC>
+void gemm_tc32(const GemmDesc<float, TB, TC>* d_desc, int ndesc, int max_M, int max_N,
+               float alpha, float beta, int* status, cudaStream_t st);
 
 // ---- leaf kernels (hps_leaf.cu)
 // Leaf kernels run on a group of leaves with one (p, q): group-local leaf j is

@@ -16,6 +16,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
+#include <type_traits>
+#include <unordered_map>
 #include <cstdint>
 #include <cstdio>
 
@@ -237,17 +241,32 @@ using TileNarrow = Tile<R, 128, 16, 16, 4, 4>;
 // products would leave most of its 128 rows idle
 using TileWideF = Tile<float, 128, 64, 16, 8, 8>;
 constexpr int kWideK = 64, kWideM = 96;
+// The profiler name of a product on the tensor cores: the name with "_tc"
+// before its type suffix ("gemm_body<f32>" -> "gemm_body_tc<f32>").
+const char* tc_name(const char* name) {
+  static std::mutex mu;
+  static std::unordered_map<std::string, std::string> names;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = names.find(name);
+  if (it == names.end()) {
+    std::string n(name);
+    const size_t lt = n.find('<');
+    n = lt == std::string::npos ? n + "_tc" : n.substr(0, lt) + "_tc" + n.substr(lt);
+    it = names.emplace(std::string(name), n).first;
+  }
+  return it->second.c_str();
+}
 
 // ------------------------------------------------------------ explicit GEMMs
 template <typename R, class TL, typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<TA, TB, TC>* __restrict__ d,
-                                                 int tpm, int tpn, R alpha, R beta) {
+                                                 int tpm, int tpn, R alpha, R beta, int skip_tc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int per = tpm * tpn;
   const GemmDesc<TA, TB, TC> g = d[blockIdx.x / per];
   const int tile = blockIdx.x % per;
   const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
-  if (m0 >= g.M || n0 >= g.N) return;
+  if (m0 >= g.M || n0 >= g.N || (skip_tc && gemm_on_tc(g.M, g.K))) return;
   TL::run(g.M, g.N, g.K, alpha, g.A, g.lda, g.B, g.ldb, beta, g.C, g.ldc, m0, n0,
           reinterpret_cast<R*>(smraw));
 }
@@ -258,7 +277,8 @@ __global__ void __launch_bounds__(TL::NT) k_gemm(const GemmDesc<TA, TB, TC>* __r
 template <typename R, class TL, typename TA, typename TB, typename TC>
 __global__ void __launch_bounds__(TL::NT) k_gemm_split(const GemmDesc<TA, TB, TC>* __restrict__ d,
                                                        int tpm, int tpn, int splits, int kc,
-                                                       R* __restrict__ ws, int wsM, int wsN) {
+                                                       R* __restrict__ ws, int wsM, int wsN,
+                                                       int skip_tc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int per = tpm * tpn * splits;
   const int di = blockIdx.x / per;
@@ -267,7 +287,7 @@ __global__ void __launch_bounds__(TL::NT) k_gemm_split(const GemmDesc<TA, TB, TC
   const int sp = rem / (tpm * tpn), tile = rem % (tpm * tpn);
   const int m0 = (tile % tpm) * TL::BM, n0 = (tile / tpm) * TL::BN;
   const int k0 = sp * kc;
-  if (m0 >= g.M || n0 >= g.N || k0 >= g.K) return;
+  if (m0 >= g.M || n0 >= g.N || k0 >= g.K || (skip_tc && gemm_on_tc(g.M, g.K))) return;
   const int kn = min(kc, g.K - k0);
   R* wp = ws + ((size_t)di * splits + sp) * wsM * wsN;
   TL::run(g.M, g.N, kn, R(1), g.A + (size_t)k0 * g.lda, g.lda, g.B + k0, g.ldb, R(0), wp, wsM, m0,
@@ -277,9 +297,10 @@ __global__ void __launch_bounds__(TL::NT) k_gemm_split(const GemmDesc<TA, TB, TC
 template <typename R, typename TA, typename TB, typename TC>
 __global__ void k_gemm_split_reduce(const GemmDesc<TA, TB, TC>* __restrict__ d, int splits, int kc,
                                     const R* __restrict__ ws, int wsM, int wsN, int chunks,
-                                    R alpha, R beta) {
+                                    R alpha, R beta, int skip_tc) {
   const int di = blockIdx.x / chunks;
   const GemmDesc<TA, TB, TC> g = d[di];
+  if (skip_tc && gemm_on_tc(g.M, g.K)) return;
   const int ns = min(splits, (g.K + kc - 1) / kc);
   const int64_t n = (int64_t)g.M * g.N;
   for (int64_t e = (int64_t)(blockIdx.x % chunks) * blockDim.x + threadIdx.x; e < n;
@@ -298,7 +319,7 @@ __global__ void k_gemm_split_reduce(const GemmDesc<TA, TB, TC>* __restrict__ d, 
 template <typename R, class TL, typename TA, typename TB, typename TC>
 static void launch_gemm(const GemmDesc<TA, TB, TC>* d, int nd, int max_M, int max_N, int max_K,
                         R alpha, R beta, cudaStream_t st, const char* name, double flops,
-                        double bytes, R* ws, size_t ws_elems) {
+                        double bytes, R* ws, size_t ws_elems, int skip_tc) {
   int tpm = (max_M + TL::BM - 1) / TL::BM, tpn = (max_N + TL::BN - 1) / TL::BN;
   if (nd <= 0 || tpm <= 0 || tpn <= 0) return;
   long long tiles = (long long)nd * tpm * tpn;
@@ -307,34 +328,53 @@ static void launch_gemm(const GemmDesc<TA, TB, TC>* d, int nd, int max_M, int ma
   // its own K, never on the other products of the launch
   const int splits = (ws && max_K > kSplitK) ? (max_K + kSplitK - 1) / kSplitK : 1;
   if (splits < 2 || (size_t)nd * splits * max_M * max_N > ws_elems) {
-    k_gemm<R, TL, TA, TB, TC><<<(unsigned)tiles, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta);
+    k_gemm<R, TL, TA, TB, TC><<<(unsigned)tiles, TL::NT, TL::SMEM, st>>>(d, tpm, tpn, alpha, beta,
+                                                                       skip_tc);
     return;
   }
   const int kc = kSplitK;
   k_gemm_split<R, TL, TA, TB, TC><<<(unsigned)(tiles * splits), TL::NT, TL::SMEM, st>>>(
-      d, tpm, tpn, splits, kc, ws, max_M, max_N);
+      d, tpm, tpn, splits, kc, ws, max_M, max_N, skip_tc);
   int chunks = (int)std::min<long long>(((long long)max_M * max_N + 255) / 256, 256);
   k_gemm_split_reduce<R, TA, TB, TC><<<(unsigned)((long long)nd * chunks), 256, 0, st>>>(
-      d, splits, kc, ws, max_M, max_N, chunks, alpha, beta);
+      d, splits, kc, ws, max_M, max_N, chunks, alpha, beta, skip_tc);
 }
 
 template <typename R, typename TA, typename TB, typename TC>
 void gemm_batched(const GemmDesc<TA, TB, TC>* d_desc, int ndesc, int max_M, int max_N, R alpha,
                   R beta, cudaStream_t st, const char* name, double flops, double bytes,
-                  int max_K, R* ws, size_t ws_elems) {
+                  int max_K, R* ws, size_t ws_elems, int* status) {
+  int skip_tc = 0;
+  // (FP64 B operands, converted per element as they are loaded, stay on the
+  // tile kernels: measured faster there)
+  if constexpr (std::is_same<R, float>::value && std::is_same<TA, float>::value &&
+                std::is_same<TB, float>::value) {
+    if (status && ndesc > 0 && gemm_on_tc(max_M, max_K)) {
+      // the products gemm_on_tc takes; the tile kernels below run the others
+      // (only the launch's maxima are known here, so they always launch; the
+      // profiler counts the flops and bytes under the tensor-core entry)
+      {
+        prof::Scope sc(tc_name(name), st, flops, bytes);
+        gemm_tc32<TB, TC>(d_desc, ndesc, max_M, max_N, alpha, beta, status, st);
+      }
+      skip_tc = 1;
+      flops = 0.0;
+      bytes = 0.0;
+    }
+  }
   if (max_N <= 16)
     launch_gemm<R, TileNarrow<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name,
-                                  flops, bytes, ws, ws_elems);
+                                  flops, bytes, ws, ws_elems, skip_tc);
   else if constexpr (sizeof(R) == 4) {
     if (max_K >= kWideK && max_M >= kWideM)
       launch_gemm<R, TileWideF>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name, flops,
-                                bytes, ws, ws_elems);
+                                bytes, ws, ws_elems, skip_tc);
     else
       launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name,
-                                flops, bytes, ws, ws_elems);
+                                flops, bytes, ws, ws_elems, skip_tc);
   } else {
     launch_gemm<R, TileSq<R>>(d_desc, ndesc, max_M, max_N, max_K, alpha, beta, st, name, flops,
-                              bytes, ws, ws_elems);
+                              bytes, ws, ws_elems, skip_tc);
   }
 }
 
@@ -1311,7 +1351,7 @@ template void lu_solve_batched<float>(const LuDesc<float>*, int, int, int, int, 
 #define HPS_INST_GEMM(R, TA, TB, TC)                                                            \
   template void gemm_batched<R, TA, TB, TC>(const GemmDesc<TA, TB, TC>*, int, int, int, R, R,   \
                                             cudaStream_t, const char*, double, double, int, R*, \
-                                            size_t);
+                                            size_t, int*);
 HPS_INST_GEMM(double, double, double, double)
 HPS_INST_GEMM(float, float, float, float)
 HPS_INST_GEMM(float, float, double, double)
