@@ -81,40 +81,28 @@ struct Tile {
   static constexpr int SMEM = 2 * STAGE * (int)sizeof(R);
   static_assert(BM * BK % NT == 0 && BK * BN % NT == 0, "tile loads must divide evenly");
 
-  template <typename TC>
-  __device__ static void store4(TC* cp, const R* v, R alpha, R beta) {
-    // TM = 4 consecutive rows of one column
-    if (sizeof(TC) == 8) {
-      double2* q = reinterpret_cast<double2*>(cp);
-      double2 lo = make_double2(0.0, 0.0), hi = lo;
-      if (beta != R(0)) {
-        lo = q[0];
-        hi = q[1];
-        lo.x = fma((double)alpha, (double)v[0], (double)beta * lo.x);
-        lo.y = fma((double)alpha, (double)v[1], (double)beta * lo.y);
-        hi.x = fma((double)alpha, (double)v[2], (double)beta * hi.x);
-        hi.y = fma((double)alpha, (double)v[3], (double)beta * hi.y);
-      } else {
-        lo = make_double2((double)(alpha * v[0]), (double)(alpha * v[1]));
-        hi = make_double2((double)(alpha * v[2]), (double)(alpha * v[3]));
-      }
-      q[0] = lo;
-      q[1] = hi;
-    } else {
-      float4* q = reinterpret_cast<float4*>(cp);
-      float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (beta != R(0)) {
-        c = *q;
-        c.x = fmaf((float)alpha, (float)v[0], (float)beta * c.x);
-        c.y = fmaf((float)alpha, (float)v[1], (float)beta * c.y);
-        c.z = fmaf((float)alpha, (float)v[2], (float)beta * c.z);
-        c.w = fmaf((float)alpha, (float)v[3], (float)beta * c.w);
-      } else {
-        c = make_float4((float)(alpha * v[0]), (float)(alpha * v[1]), (float)(alpha * v[2]),
-                        (float)(alpha * v[3]));
-      }
-      *q = c;
-    }
+  // 4 consecutive elements of one column (16-byte aligned)
+  __device__ static void load4(const float* cp, float* v) {
+    const float4 q = *reinterpret_cast<const float4*>(cp);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  }
+  __device__ static void load4(const double* cp, double* v) {
+    const double2 lo = reinterpret_cast<const double2*>(cp)[0];
+    const double2 hi = reinterpret_cast<const double2*>(cp)[1];
+    v[0] = lo.x;
+    v[1] = lo.y;
+    v[2] = hi.x;
+    v[3] = hi.y;
+  }
+  __device__ static void save4(float* cp, const float* v) {
+    *reinterpret_cast<float4*>(cp) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  __device__ static void save4(double* cp, const double* v) {
+    reinterpret_cast<double2*>(cp)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(cp)[1] = make_double2(v[2], v[3]);
   }
 
   template <typename TA, typename TB, typename TC>
@@ -205,27 +193,55 @@ struct Tile {
     }
     const int gi0 = m0 + r0;
     if (gi0 >= M) return;
+    // the C values of kJB columns are all loaded before any of them is stored:
+    // for all the compiler knows the stores alias the loads, which would
+    // otherwise cost one memory round trip per column (kJB caps the values
+    // held at 128 bytes per thread)
+    constexpr int kJB0 = 128 / (TM * (int)sizeof(TC));
+    constexpr int kJB = kJB0 < 1 ? 1 : (kJB0 > TN ? TN : kJB0);
+    static_assert(TN % kJB == 0, "column batches divide the tile");
+    const bool rows_in = gi0 + TM <= M;
+    auto vec_ok = [&](const TC* cp) {
+      return TM % 4 == 0 && rows_in && (reinterpret_cast<uintptr_t>(cp) & 15) == 0;
+    };
 #pragma unroll
-    for (int j = 0; j < TN; ++j) {
-      const int gj = n0 + c0 + j;
-      if (gj >= N) continue;
-      TC* cp = C + gi0 + (size_t)gj * ldc;
-      if (TM % 4 == 0 && (sizeof(TC) == 4 || sizeof(TC) == 8) && gi0 + TM <= M &&
-          (reinterpret_cast<uintptr_t>(cp) & 15) == 0) {
+    for (int j0 = 0; j0 < TN; j0 += kJB) {
+      TC cv[kJB][TM];
+      if (beta != R(0)) {
 #pragma unroll
-        for (int i = 0; i < TM; i += 4) {
-          R v[4] = {acc[i][j], acc[i + 1][j], acc[i + 2][j], acc[i + 3][j]};
-          store4(cp + i, v, alpha, beta);
+        for (int jj = 0; jj < kJB; ++jj) {
+          const int gj = n0 + c0 + j0 + jj;
+          const TC* cp = C + gi0 + (size_t)gj * ldc;
+          if (gj < N && vec_ok(cp)) {
+#pragma unroll
+            for (int i = 0; i < TM; i += 4) load4(cp + i, &cv[jj][i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < TM; ++i) cv[jj][i] = (gj < N && gi0 + i < M) ? cp[i] : TC(0);
+          }
         }
-        continue;
       }
 #pragma unroll
-      for (int i = 0; i < TM; ++i) {
-        if (gi0 + i >= M) break;
-        if (beta == R(0))
-          cp[i] = (TC)(alpha * acc[i][j]);
-        else  // accumulate in the wider of the two types
-          cp[i] = (TC)fma((TC)alpha, (TC)acc[i][j], (TC)beta * cp[i]);
+      for (int jj = 0; jj < kJB; ++jj) {
+        const int j = j0 + jj, gj = n0 + c0 + j;
+        if (gj >= N) continue;
+        TC* cp = C + gi0 + (size_t)gj * ldc;
+        TC out[TM];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          if (beta == R(0))
+            out[i] = (TC)(alpha * acc[i][j]);
+          else  // accumulate in the wider of the two types
+            out[i] = (TC)fma((TC)alpha, (TC)acc[i][j], (TC)beta * cv[jj][i]);
+        }
+        if (vec_ok(cp)) {
+#pragma unroll
+          for (int i = 0; i < TM; i += 4) save4(cp + i, &out[i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < TM; ++i)
+            if (gi0 + i < M) cp[i] = out[i];
+        }
       }
     }
   }
