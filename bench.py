@@ -333,11 +333,11 @@ def alu_peak_tflops(name, sm_mhz):
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the same kernel's launch in the same workload step; a kernel
-# changed since its capture has no entry.  leaf_resflux<f64>: captured on
-# 64 x 64 leaves with 64 right-hand sides (848.7 MB per launch, 3238 bytes per
+# changed since its capture has no entry.  leaf_resflux_tc<f64>: captured on
+# 64 x 64 leaves with 64 right-hand sides (850.7 MB per launch, 3245 bytes per
 # leaf and right-hand side) and scaled by the 16 times as many units of a
 # 256 x 256 launch.
-TRAFFIC_PER_LAUNCH = {("helmholtz256", "leaf_resflux<f64>"): 848.7e6 * 16}
+TRAFFIC_PER_LAUNCH = {("helmholtz256", "leaf_resflux_tc<f64>"): 850.7e6 * 16}
 
 
 def roofline_of(stats, t_total_ms, sm_mhz, workload=None):
@@ -350,7 +350,10 @@ def roofline_of(stats, t_total_ms, sm_mhz, workload=None):
             "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get((workload, name)),
             "peak_source": f"{'FP64 DFMA' if per == FP64_DFMA_PER_SM_CLK else 'FP32 FFMA'}: "
                            f"{N_SM} SMs x {per}/clk x 2 flop x {sm_mhz:.0f} MHz (max SM clock; "
-                           f"per-clock rate measured on a GB300 by an FMA throughput probe)",
+                           f"per-clock rate measured on a GB300 by an FMA throughput probe)"
+                           + ("; achieved counts the operation's FP64 flops, whose products "
+                              "run as exact BF16 digit products on the tensor cores, so it "
+                              "can exceed the FP64 pipe's peak" if "_tc<f64>" in name else ""),
             "flops_per_launch": per_launch_flops, "launches": st["launches"],
             "ms_per_launch": per_launch_s * 1e3, "share_of_step": st["ms"] / max(t_total_ms, 1e-9)}
 

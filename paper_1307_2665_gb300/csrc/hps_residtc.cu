@@ -644,10 +644,13 @@ void launch_resid_tc(const double* const* coef, int l0, int nl, int q, const dou
   const void* kern = reinterpret_cast<const void*>(&k_leaf_resid_tc<R, kFromY, kFlux>);
   // the ceiling covers q <= 16 (a launch asking for more fails its launch check)
   if (!opt_in_smem(kern, (int)resid_tc_smem<R, kFlux>(kRP))) return;
-  // FP64 flops per grid left on the FP64 pipe: the combination (3 per interior
-  // node) and the Gauss interpolation of the fluxes (4 q sums of 16 terms);
-  // bytes: the grid, r, the fluxes, and the leaf's coefficients
-  const double per = 3.0 * 2.0 * kRNi + (kFlux ? 4.0 * q * 2.0 * kRP : 0.0);
+  // the operation's FP64 flops per grid (what the FP64 pipe would execute):
+  // X and Y at the interior nodes (16-term sums), the combination (3 per
+  // node), the side derivatives (4 x 16 sums of 16 terms) and their Gauss
+  // interpolation (4 q sums of 16 terms); bytes: the grid, r, the fluxes, and
+  // the leaf's coefficients
+  const double per = 2.0 * (2.0 * kRNi * kRP + 3.0 * kRNi +
+                            (kFlux ? 4.0 * kRP * kRP + 4.0 * q * kRP : 0.0));
   const double in_bytes = kFromY ? (double)kRNi * sizeof(R) : (double)kRPP * 8.0;
   prof::Scope sc(name, st, (double)nl * nrhs * per,
                  (double)nl * (nrhs * (in_bytes + kRNi * sizeof(R) + (kFlux ? 32.0 * q : 0.0)) +
