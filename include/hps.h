@@ -233,6 +233,35 @@ int hps_interpolate(hps_handle h, const double* u, int nrhs, const double* xy, i
 int hps_dgemm_tc(int M, int N, int K, double alpha, const double* A, int lda, const double* B,
                  int ldb, double beta, double* C, int ldc);
 
+/* C = alpha A B + beta C for FP32 device matrices (column-major, leading
+ * dimensions lda >= M, ldb >= K, ldc >= M) through the engine the mixed mode
+ * uses for its FP32 products (leaf inverse times residual, Schur complements
+ * of the lower merges, Section 4 eq. merge in FP32): with M >= 96 and K >= 32
+ * on the tensor cores, every FP32 value split exactly into three BF16 terms
+ * and six BF16 products per K step accumulated in FP32 (the error of an FP32
+ * GEMM); smaller products on the FP32 tile kernels.  Synchronous on the
+ * current device.  Exposed for testing and measurement. */
+int hps_sgemm_tc(int M, int N, int K, float alpha, const float* A, int lda, const float* B,
+                 int ldb, float beta, float* C, int ldc);
+
+/* One pass of the mixed mode's FP64 residual kernel on raw leaves (Section
+ * 3.1's collocation operator A = -c11 d_xx - c22 d_yy + c with the Section 3.2
+ * leaf maps): for every leaf l and right-hand side k,
+ *   r[(l nrhs + k) (p-2)^2 + i] = -(A w)_i at the interior Chebyshev nodes
+ *     (i = (a-1)(p-2) + (b-1), node (a, b) = a p + b, a along y, b along x),
+ *   flux[(k nleaves + l) 4q + g] = (L4 L3 w)_g, the side fluxes at the q
+ *     Gauss points of the sides S, E, N, W (d/dy on S and N, d/dx on E and W),
+ * from w[(k nleaves + l) p^2 + node] and the coefficient samples c11, c22, c
+ * (nleaves x p^2 each, leaf-major; null = absent) on leaves of size hx x hy.
+ * All arrays are device memory.  tensor_cores = 1: the tensor-core kernel
+ * (exact BF16 digit products; p = 16, q <= 16, else HPS_EINVAL); 0: the
+ * FP64-pipe kernel (even and odd parts of the grid lines).  A grid holding an
+ * infinity or NaN gives NaN at all of its outputs in the tensor-core kernel.
+ * Synchronous.  Exposed for testing and measurement. */
+int hps_leaf_residual(int p, int q, int nleaves, double hx, double hy, const double* c11,
+                      const double* c22, const double* c, const double* w, int nrhs, double* r,
+                      double* flux, int tensor_cores);
+
 /* Release the solve workspace a handle caches between solves (exterior-value
  * pools, refinement buffers, staging); the next solve allocates it again.
  * Must not overlap a solve on the same handle. */

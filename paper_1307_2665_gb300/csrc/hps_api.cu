@@ -1844,6 +1844,113 @@ int hps_dgemm_tc(int M, int N, int K, double alpha, const double* A, int lda, co
   }
 }
 
+int hps_sgemm_tc(int M, int N, int K, float alpha, const float* A, int lda, const float* B,
+                 int ldb, float beta, float* C, int ldc) {
+  if (M < 1 || N < 1 || K < 1 || lda < M || ldb < K || ldc < M || !A || !B || !C)
+    return HPS_EINVAL;
+  g_last_error.clear();
+  try {
+    cudaStream_t st = nullptr;
+    ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int rc = HPS_OK;
+    {
+      GemmDesc<float> h{A, B, C, M, N, K, lda, ldb, ldc};
+      PoolBuf dd, stt;
+      dd.alloc(sizeof(h), st);
+      stt.alloc(sizeof(int), st);
+      ck(cudaMemcpyAsync(dd.p, &h, sizeof(h), cudaMemcpyHostToDevice, st));
+      ck(cudaMemsetAsync(stt.p, 0, sizeof(int), st));
+      gemm_batched<float>(dd.as<GemmDesc<float>>(), 1, M, N, alpha, beta, st, "sgemm<f32>",
+                          2.0 * M * (double)N * K, 4.0 * ((double)M * K + (double)K * N + M * N),
+                          K, nullptr, 0, stt.as<int>());
+      ck(cudaGetLastError());
+      int hst = 0;
+      ck(cudaMemcpyAsync(&hst, stt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      if (hst != 0) {
+        g_last_error = "tensor-core GEMM: a wait gave up";
+        rc = HPS_EDEVICE;
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  }
+}
+
+int hps_leaf_residual(int p, int q, int nleaves, double hx, double hy, const double* c11,
+                      const double* c22, const double* c, const double* w, int nrhs, double* r,
+                      double* flux, int tensor_cores) {
+  if (p < 3 || p > 64 || q < 1 || q > p || nleaves < 1 || nrhs < 1 || !(hx > 0) || !(hy > 0) ||
+      !w || !r || !flux || (tensor_cores != 0 && tensor_cores != 1))
+    return HPS_EINVAL;
+  const double* coef[6] = {c11, nullptr, c22, nullptr, nullptr, c};
+  g_last_error.clear();
+  try {
+    cudaStream_t st = nullptr;
+    ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int rc = HPS_OK;
+    {
+      const Consts k = make_consts(p, q);
+      const int pp = p * p;
+      std::vector<double> dtab(2 * (size_t)pp);
+      std::copy(k.D.begin(), k.D.end(), dtab.begin());
+      std::copy(k.D2.begin(), k.D2.end(), dtab.begin() + pp);
+      std::vector<double2> hsc(nleaves, make_double2(2.0 / hx, 2.0 / hy));
+      std::vector<const double*> wp(nleaves);
+      std::vector<int64_t> wr(nleaves, (int64_t)nleaves * pp), off(nleaves);
+      for (int l = 0; l < nleaves; ++l) {
+        wp[l] = w + (size_t)l * pp;
+        off[l] = (int64_t)l * 4 * q;
+      }
+      PoolBuf dD, dP, dh, dw, dwr, doff, stt;
+      auto up = [&](PoolBuf& b, const void* src, size_t bytes) {
+        b.alloc(bytes, st);
+        ck(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
+      };
+      up(dD, dtab.data(), dtab.size() * sizeof(double));
+      up(dP, k.Pc2g.data(), k.Pc2g.size() * sizeof(double));
+      up(dh, hsc.data(), hsc.size() * sizeof(double2));
+      up(dw, wp.data(), wp.size() * sizeof(double*));
+      up(dwr, wr.data(), wr.size() * sizeof(int64_t));
+      up(doff, off.data(), off.size() * sizeof(int64_t));
+      stt.alloc(sizeof(int), st);
+      ck(cudaMemsetAsync(stt.p, 0, sizeof(int), st));
+      double* const* wptr = reinterpret_cast<double* const*>(dw.p);
+      const int64_t ext_total = (int64_t)nleaves * 4 * q;
+      if (tensor_cores) {
+        if (!leaf_resflux_tc<double>(coef, 0, nleaves, p, q, dh.as<double2>(), dD.as<double>(),
+                                     dP.as<double>(), wptr, dwr.as<int64_t>(), nrhs, r,
+                                     doff.as<int64_t>(), ext_total, flux, stt.as<int>(), st)) {
+          g_last_error = "hps_leaf_residual: the tensor-core kernel takes p = 16, q <= 16";
+          rc = HPS_EINVAL;
+        }
+      } else {
+        leaf_resflux<double>(coef, 0, nleaves, p, q, dh.as<double2>(), dD.as<double>(),
+                             dP.as<double>(), wptr, dwr.as<int64_t>(), nrhs, r,
+                             doff.as<int64_t>(), ext_total, flux, st);
+      }
+      ck(cudaGetLastError());
+      int hst = 0;
+      ck(cudaMemcpyAsync(&hst, stt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      if (hst != 0) {
+        g_last_error = "tensor-core residual: a wait gave up";
+        rc = HPS_EDEVICE;
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  }
+}
+
 int hps_estimate_bytes(const hps_problem* probs, int nprob, const hps_options* opt_in, int nrhs,
                        int64_t* build_peak, int64_t* resident, int64_t* solve) {
   if (!probs || nprob < 1 || nrhs < 0) return HPS_EINVAL;
