@@ -44,34 +44,9 @@ constexpr int kGThreads = 256;
 constexpr int kGSub = kGM * 16 * 2;  // bytes of one A sub-tile: 128 rows x 16 k (BF16)
 constexpr long kGSpin = 1L << 22;  // bound of every wait (iterations)
 
-// Offset (elements) of operand element (row r, k) of a 16-wide K sub-tile in
-// the K-major no-swizzle layout: core matrices of 8 rows x 8 k (128 bytes),
-// LBO 128 B (the two K cores), SBO 256 B (row groups).
-__device__ __forceinline__ int g_off(int r, int k) {
-  return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
-}
-
-// The exact three-term BF16 split of 8 floats, packed as three 16-byte rows.
-__device__ __forceinline__ void split8(const float* x, uint32_t (*w)[4]) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float a = x[2 * j], b = x[2 * j + 1];
-    const __nv_bfloat162 h1 = __floats2bfloat162_rn(a, b);
-    const float ra = a - __low2float(h1), rb = b - __high2float(h1);
-    const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra, rb);
-    const float sa = ra - __low2float(h2), sb = rb - __high2float(h2);
-    const __nv_bfloat162 h3 = __floats2bfloat162_rn(sa, sb);
-    w[0][j] = *reinterpret_cast<const uint32_t*>(&h1);
-    w[1][j] = *reinterpret_cast<const uint32_t*>(&h2);
-    w[2][j] = *reinterpret_cast<const uint32_t*>(&h3);
-  }
-}
-
-__device__ __forceinline__ void st16(uint32_t saddr, const uint32_t* w) {
-  asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(saddr), "r"(w[0]), "r"(w[1]),
-               "r"(w[2]), "r"(w[3])
-               : "memory");
-}
+using tc::g_off;
+using tc::split8;
+using tc::st16;
 
 template <int BN>
 struct GTile {

@@ -177,39 +177,44 @@ void solve_root_scatter(const RootDesc* d, int nprob, int max_nbnd, int nrhs, do
                                                                       ext_total);
 }
 
-// children's exterior values from the parent's and u3 = S u_parent
-__global__ void k_child_scatter(const SolveScatterDesc* __restrict__ d, int chunks,
+// children's exterior values from the parent's and u3 = S u_parent.  A thread
+// owns one exterior entry of a child (its source read once from the map) and
+// copies it for every right-hand side, eight loads before eight stores (the
+// source and destination are disjoint parts of the pools, which the compiler
+// cannot know: one memory round trip per value otherwise).
+__global__ void k_child_scatter(const SolveScatterDesc* __restrict__ d, int bpd,
                                 const double* __restrict__ u3, int64_t u3_total,
                                 double* __restrict__ uext, int64_t ext_total, int nrhs) {
-  const SolveScatterDesc g = d[blockIdx.x / chunks];
-  const int chunk = blockIdx.x % chunks;
-  const int64_t n = (int64_t)(g.na + g.nb) * nrhs;
-  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)chunks * blockDim.x) {
-    int64_t r = e / (g.na + g.nb);
-    int i = (int)(e % (g.na + g.nb));
-    const double* up = uext + r * ext_total + g.par_off;
-    const double* u3r = u3 + r * u3_total + g.u3_off;
-    if (i < g.na) {
-      int c = g.cmap_a[i];
-      uext[r * ext_total + g.a_off + i] = c >= 0 ? up[c] : u3r[-c - 1];
-    } else {
-      i -= g.na;
-      int c = g.cmap_b[i];
-      uext[r * ext_total + g.b_off + i] = c >= 0 ? up[c] : u3r[-c - 1];
-    }
+  const SolveScatterDesc g = d[blockIdx.x / bpd];
+  const int i = (blockIdx.x % bpd) * blockDim.x + threadIdx.x;
+  if (i >= g.na + g.nb) return;
+  const bool in_a = i < g.na;
+  const int c = in_a ? g.cmap_a[i] : g.cmap_b[i - g.na];
+  const int64_t dst = in_a ? g.a_off + i : g.b_off + (i - g.na);
+  const double* src = c >= 0 ? uext + g.par_off + c : u3 + g.u3_off + (-c - 1);
+  const int64_t ss = c >= 0 ? ext_total : u3_total;
+  double* out = uext + dst;
+  constexpr int kB = 8;
+  int r0 = 0;
+  for (; r0 + kB <= nrhs; r0 += kB) {
+    double v[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) v[j] = src[(size_t)(r0 + j) * ss];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) out[(size_t)(r0 + j) * ext_total] = v[j];
   }
+  for (; r0 < nrhs; ++r0) out[(size_t)r0 * ext_total] = src[(size_t)r0 * ss];
 }
 
 void solve_child_scatter(const SolveScatterDesc* d_desc, int ndesc, int max_n, const double* u3,
                          int64_t u3_total, double* uext, int64_t ext_total, int nrhs,
                          cudaStream_t st) {
-  if (ndesc <= 0) return;
-  int64_t work = (int64_t)max_n * nrhs;
-  int chunks = (int)std::min<int64_t>((work + 255) / 256, 64);
+  if (ndesc <= 0 || max_n <= 0) return;
+  const int threads = max_n >= 256 ? 256 : ((max_n + 31) / 32) * 32;
+  const int bpd = (max_n + threads - 1) / threads;
   prof::Scope sc("child_scatter", st, 0.0, 2.0 * (double)ndesc * max_n * nrhs * 8.0);
-  k_child_scatter<<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(
-      d_desc, chunks, u3, u3_total, uext, ext_total, nrhs);
+  k_child_scatter<<<(unsigned)((int64_t)ndesc * bpd), threads, 0, st>>>(
+      d_desc, bpd, u3, u3_total, uext, ext_total, nrhs);
 }
 
 template void merge_gather<double>(const MergeDesc<double>*, int, int64_t, cudaStream_t, double);

@@ -1,6 +1,7 @@
 // Small helpers for kernels that issue 5th-generation tensor-core MMAs
 // (tcgen05) from shared-memory operands written by the CTA itself.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -93,6 +94,37 @@ __device__ __forceinline__ void ld2(uint32_t taddr, uint32_t* v) {
 
 __device__ __forceinline__ void wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Offset (elements) of operand element (row r, k) of a 16-wide K sub-tile in
+// the K-major no-swizzle layout: core matrices of 8 rows x 8 k (128 bytes),
+// LBO 128 B (the two K cores), SBO 256 B (row groups).
+__device__ __forceinline__ int g_off(int r, int k) {
+  return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// The exact three-term BF16 split of 8 floats (x1 = bf16(x), x2 = bf16(x - x1),
+// x3 = bf16(x - x1 - x2), rounding to nearest: the remainders are exact in
+// FP32 and the three terms carry all 24 bits), packed as three 16-byte rows.
+__device__ __forceinline__ void split8(const float* x, uint32_t (*w)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float a = x[2 * j], b = x[2 * j + 1];
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(a, b);
+    const float ra = a - __low2float(h1), rb = b - __high2float(h1);
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(ra, rb);
+    const float sa = ra - __low2float(h2), sb = rb - __high2float(h2);
+    const __nv_bfloat162 h3 = __floats2bfloat162_rn(sa, sb);
+    w[0][j] = *reinterpret_cast<const uint32_t*>(&h1);
+    w[1][j] = *reinterpret_cast<const uint32_t*>(&h2);
+    w[2][j] = *reinterpret_cast<const uint32_t*>(&h3);
+  }
+}
+
+__device__ __forceinline__ void st16(uint32_t saddr, const uint32_t* w) {
+  asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(saddr), "r"(w[0]), "r"(w[1]),
+               "r"(w[2]), "r"(w[3])
+               : "memory");
 }
 
 }  // namespace tc
