@@ -77,80 +77,115 @@ void merge_gather(const MergeDesc<R>* d_desc, int ndesc, int64_t max_work, cudaS
 }
 
 // ------------------------------------------------------ body-load upward pass
+// The body-load kernels below give a thread one entry of a merge and loop over
+// the right-hand sides, eight loads before eight stores (the pools' source and
+// destination parts are disjoint, which the compiler cannot know: one memory
+// round trip per value otherwise); blocks of up to 256 threads per merge.
+constexpr int kBodyBatch = 8;
+static void body_grid(int nd, int max_n, int* threads, int* bpd) {
+  *threads = max_n >= 256 ? 256 : std::max(32, ((max_n + 31) / 32) * 32);
+  *bpd = (max_n + *threads - 1) / *threads;
+  (void)nd;
+}
+
 // Right-hand side of a merge's interface equation for the correction:
 // (T33^a - T33^b) z = h3^b - h3^a, the flux offsets of the two children at J3.
 template <typename R>
-__global__ void k_merge_rhs(const BodyDesc* __restrict__ d, int chunks,
+__global__ void k_merge_rhs(const BodyDesc* __restrict__ d, int bpd,
                             const double* __restrict__ hp, int64_t ext_total, int nrhs,
                             R* __restrict__ zlev) {
-  const BodyDesc g = d[blockIdx.x / chunks];
-  const int chunk = blockIdx.x % chunks;
-  const int64_t n = (int64_t)g.m * nrhs;
-  R* z = zlev + g.z_off * nrhs;
-  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)chunks * blockDim.x) {
-    const int64_t i = e % g.m, r = e / g.m;
-    const double* h = hp + r * ext_total;
-    z[i + r * g.m] = (R)(h[g.b_off + g.j3b + i] - h[g.a_off + g.j3a + i]);
+  const BodyDesc g = d[blockIdx.x / bpd];
+  const int i = (blockIdx.x % bpd) * blockDim.x + threadIdx.x;
+  if (i >= g.m) return;
+  const double* hb = hp + g.b_off + g.j3b + i;
+  const double* ha = hp + g.a_off + g.j3a + i;
+  R* z = zlev + g.z_off * nrhs + i;
+  int r0 = 0;
+  for (; r0 + kBodyBatch <= nrhs; r0 += kBodyBatch) {
+    R v[kBodyBatch];
+#pragma unroll
+    for (int j = 0; j < kBodyBatch; ++j) {
+      const size_t o = (size_t)(r0 + j) * ext_total;
+      v[j] = (R)(hb[o] - ha[o]);
+    }
+#pragma unroll
+    for (int j = 0; j < kBodyBatch; ++j) z[(size_t)(r0 + j) * g.m] = v[j];
+  }
+  for (; r0 < nrhs; ++r0) {
+    const size_t o = (size_t)r0 * ext_total;
+    z[(size_t)r0 * g.m] = (R)(hb[o] - ha[o]);
   }
 }
 
 // The parent's flux offsets before the Schur term: h^tau(k) = h^a(src) or h^b(src).
-__global__ void k_merge_hpar(const BodyDesc* __restrict__ d, int chunks, double* __restrict__ hp,
+__global__ void k_merge_hpar(const BodyDesc* __restrict__ d, int bpd, double* __restrict__ hp,
                              int64_t ext_total, int nrhs) {
-  const BodyDesc g = d[blockIdx.x / chunks];
-  const int chunk = blockIdx.x % chunks;
-  const int64_t n = (int64_t)g.ne * nrhs;
-  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)chunks * blockDim.x) {
-    const int64_t k = e % g.ne, r = e / g.ne;
-    double* h = hp + r * ext_total;
-    const int s = g.src[k];
-    h[g.par_off + k] = s >= 0 ? h[g.a_off + s] : h[g.b_off + (-s - 1)];
+  const BodyDesc g = d[blockIdx.x / bpd];
+  const int k = (blockIdx.x % bpd) * blockDim.x + threadIdx.x;
+  if (k >= g.ne) return;
+  const int s = g.src[k];
+  const double* src = hp + (s >= 0 ? g.a_off + s : g.b_off + (-s - 1));
+  double* dst = hp + g.par_off + k;
+  int r0 = 0;
+  for (; r0 + kBodyBatch <= nrhs; r0 += kBodyBatch) {
+    double v[kBodyBatch];
+#pragma unroll
+    for (int j = 0; j < kBodyBatch; ++j) v[j] = src[(size_t)(r0 + j) * ext_total];
+#pragma unroll
+    for (int j = 0; j < kBodyBatch; ++j) dst[(size_t)(r0 + j) * ext_total] = v[j];
   }
+  for (; r0 < nrhs; ++r0) dst[(size_t)r0 * ext_total] = src[(size_t)r0 * ext_total];
 }
 
 // u3 := z (the particular part of the interface values), before u3 += S u_parent.
 template <typename R>
-__global__ void k_z_to_u3(const BodyDesc* __restrict__ d, int chunks, const R* __restrict__ zlev,
+__global__ void k_z_to_u3(const BodyDesc* __restrict__ d, int bpd, const R* __restrict__ zlev,
                           double* __restrict__ u3, int64_t u3_total, int nrhs) {
-  const BodyDesc g = d[blockIdx.x / chunks];
-  const int chunk = blockIdx.x % chunks;
-  const int64_t n = (int64_t)g.m * nrhs;
-  const R* z = zlev + g.z_off * nrhs;
-  for (int64_t e = (int64_t)chunk * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)chunks * blockDim.x) {
-    const int64_t i = e % g.m, r = e / g.m;
-    u3[r * u3_total + g.u3_off + i] = (double)z[i + r * g.m];
+  const BodyDesc g = d[blockIdx.x / bpd];
+  const int i = (blockIdx.x % bpd) * blockDim.x + threadIdx.x;
+  if (i >= g.m) return;
+  const R* z = zlev + g.z_off * nrhs + i;
+  double* u = u3 + g.u3_off + i;
+  int r0 = 0;
+  for (; r0 + kBodyBatch <= nrhs; r0 += kBodyBatch) {
+    double v[kBodyBatch];
+#pragma unroll
+    for (int j = 0; j < kBodyBatch; ++j) v[j] = (double)z[(size_t)(r0 + j) * g.m];
+#pragma unroll
+    for (int j = 0; j < kBodyBatch; ++j) u[(size_t)(r0 + j) * u3_total] = v[j];
   }
+  for (; r0 < nrhs; ++r0) u[(size_t)r0 * u3_total] = (double)z[(size_t)r0 * g.m];
 }
-
-static int body_chunks(int64_t work) { return (int)std::min<int64_t>((work + 255) / 256, 64); }
 
 template <typename R>
 void merge_rhs(const BodyDesc* d, int nd, int max_m, const double* hp, int64_t ext_total,
                int nrhs, R* zlev, cudaStream_t st) {
-  if (nd <= 0) return;
-  int ch = body_chunks((int64_t)max_m * nrhs);
+  if (nd <= 0 || max_m <= 0) return;
+  int threads, bpd;
+  body_grid(nd, max_m, &threads, &bpd);
   prof::Scope sc("merge_rhs", st, 0.0, (double)nd * max_m * nrhs * (16.0 + sizeof(R)));
-  k_merge_rhs<R><<<(unsigned)((int64_t)nd * ch), 256, 0, st>>>(d, ch, hp, ext_total, nrhs, zlev);
+  k_merge_rhs<R><<<(unsigned)((int64_t)nd * bpd), threads, 0, st>>>(d, bpd, hp, ext_total, nrhs,
+                                                                    zlev);
 }
 
 void merge_hpar(const BodyDesc* d, int nd, int max_ne, double* hp, int64_t ext_total, int nrhs,
                 cudaStream_t st) {
-  if (nd <= 0) return;
-  int ch = body_chunks((int64_t)max_ne * nrhs);
+  if (nd <= 0 || max_ne <= 0) return;
+  int threads, bpd;
+  body_grid(nd, max_ne, &threads, &bpd);
   prof::Scope sc("merge_hpar", st, 0.0, (double)nd * max_ne * nrhs * 16.0);
-  k_merge_hpar<<<(unsigned)((int64_t)nd * ch), 256, 0, st>>>(d, ch, hp, ext_total, nrhs);
+  k_merge_hpar<<<(unsigned)((int64_t)nd * bpd), threads, 0, st>>>(d, bpd, hp, ext_total, nrhs);
 }
 
 template <typename R>
 void z_to_u3(const BodyDesc* d, int nd, int max_m, const R* zlev, double* u3, int64_t u3_total,
              int nrhs, cudaStream_t st) {
-  if (nd <= 0) return;
-  int ch = body_chunks((int64_t)max_m * nrhs);
+  if (nd <= 0 || max_m <= 0) return;
+  int threads, bpd;
+  body_grid(nd, max_m, &threads, &bpd);
   prof::Scope sc("z_to_u3", st, 0.0, (double)nd * max_m * nrhs * (8.0 + sizeof(R)));
-  k_z_to_u3<R><<<(unsigned)((int64_t)nd * ch), 256, 0, st>>>(d, ch, zlev, u3, u3_total, nrhs);
+  k_z_to_u3<R><<<(unsigned)((int64_t)nd * bpd), threads, 0, st>>>(d, bpd, zlev, u3, u3_total,
+                                                                  nrhs);
 }
 
 // ----------------------------------------------------------- downward pass
