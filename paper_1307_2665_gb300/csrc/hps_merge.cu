@@ -22,38 +22,41 @@ __device__ __forceinline__ double tload(const void* p, int f64, int64_t i) {
   return f64 ? static_cast<const double*>(p)[i] : (double)static_cast<const float*>(p)[i];
 }
 
-template <typename R>
+// I: the index type, 32-bit whenever every merge of the launch has fewer than
+// 2^31 entries to write (integer division and modulo by m and ne per entry
+// cost several times as much in 64 bits).
+template <typename R, typename I>
 __global__ void __launch_bounds__(256) k_merge_gather(const MergeDesc<R>* __restrict__ d,
                                                       int chunks, int64_t per_chunk) {
   const MergeDesc<R> g = d[blockIdx.x / chunks];
   const int chunk = blockIdx.x % chunks;
-  const int64_t m = g.m, ne = g.ne;
-  const int64_t nA = m * m, nS = m * ne, nC = ne * m, nT = g.Tp ? ne * ne : 0;
-  const int64_t nW = g.W ? m * m : 0;
-  const int64_t total = nA + nS + nC + nT + nW;
-  const int64_t beg = (int64_t)chunk * per_chunk;
-  const int64_t end = min(total, beg + per_chunk);
+  const I m = g.m, ne = g.ne;
+  const I nA = m * m, nS = m * ne, nC = ne * m, nT = g.Tp ? ne * ne : 0;
+  const I nW = g.W ? m * m : 0;
+  const I total = nA + nS + nC + nT + nW;
+  const I beg = (I)(chunk * per_chunk);
+  const I end = min(total, (I)(beg + per_chunk));
   const int64_t na = g.na, nb = g.nb;
-  for (int64_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+  for (I e = beg + (I)threadIdx.x; e < end; e += (I)blockDim.x) {
     if (e < nA) {
-      int64_t i = e % m, j = e / m;
+      I i = e % m, j = e / m;
       g.Aw[e] = (R)(tload(g.Ta, g.ta64, (g.j3a + i) + (g.j3a + j) * na) -
                     tload(g.Tb, g.tb64, (g.j3b + i) + (g.j3b + j) * nb));
     } else if (e < nA + nS) {
-      int64_t x = e - nA, i = x % m, k = x / m;
+      I x = e - nA, i = x % m, k = x / m;
       int s = g.src[k];
       g.S[x] = s >= 0 ? (R)(-tload(g.Ta, g.ta64, (g.j3a + i) + (int64_t)s * na))
                       : (R)tload(g.Tb, g.tb64, (g.j3b + i) + (int64_t)(-s - 1) * nb);
     } else if (e < nA + nS + nC) {
-      int64_t x = e - nA - nS, k = x % ne, i = x / ne;
+      I x = e - nA - nS, k = x % ne, i = x / ne;
       int s = g.src[k];
       g.Cw[x] = s >= 0 ? (R)tload(g.Ta, g.ta64, s + (g.j3a + i) * na)
                        : (R)tload(g.Tb, g.tb64, (int64_t)(-s - 1) + (g.j3b + i) * nb);
     } else if (e >= nA + nS + nC + nT) {
-      int64_t x = e - nA - nS - nC - nT;
+      I x = e - nA - nS - nC - nT;
       g.W[x] = (x % m == x / m) ? R(1) : R(0);
     } else {
-      int64_t x = e - nA - nS - nC, k = x % ne, k2 = x / ne;
+      I x = e - nA - nS - nC, k = x % ne, k2 = x / ne;
       int s = g.src[k], s2 = g.src[k2];
       R v = R(0);
       if (s >= 0 && s2 >= 0)
@@ -72,8 +75,12 @@ void merge_gather(const MergeDesc<R>* d_desc, int ndesc, int64_t max_work, cudaS
   const int64_t per_chunk = 256 * 16;
   int chunks = (int)((max_work + per_chunk - 1) / per_chunk);
   prof::Scope sc(sizeof(R) == 8 ? "merge_gather<f64>" : "merge_gather<f32>", st, 0.0, bytes);
-  k_merge_gather<R><<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(d_desc, chunks,
-                                                                        per_chunk);
+  if (max_work < ((int64_t)1 << 31) - per_chunk)
+    k_merge_gather<R, int><<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(d_desc, chunks,
+                                                                               per_chunk);
+  else
+    k_merge_gather<R, int64_t><<<(unsigned)((int64_t)ndesc * chunks), 256, 0, st>>>(
+        d_desc, chunks, per_chunk);
 }
 
 // ------------------------------------------------------ body-load upward pass
