@@ -1115,11 +1115,19 @@ struct RefineBufs {
 void leaf_out(hps_handle_s& H, double* const* wptr, const int64_t* wrs, int nrhs,
               bool correction) {
   for (auto& G : H.lg) {
-    if (H.mixed)
+    if (H.mixed) {
+      // the FP64 side values on the tensor cores first, into the residual
+      // buffer (free here: the leaf correction has consumed it)
+      double* bv = G.rleaf->as<double>();
+      if (G.rleaf->bytes < (size_t)nrhs * G.nl * 4 * G.p * sizeof(double) ||
+          !leaf_bnd_interp_tc(H.uext.as<double>(), H.leaf_off.as<int64_t>(), G.l0, G.nl,
+                              H.plan.ext_total, G.p, G.q, nrhs, G.dPg2c->as<double>(), bv,
+                              H.status.as<int>(), H.stream))
+        bv = nullptr;
       leaf_post<float>(G.Y->as<float>(), G.ys, G.l0, H.uext.as<double>(), H.leaf_off.as<int64_t>(),
                        H.plan.ext_total, G.nl, G.p, G.q, nrhs, G.dPg2c->as<double>(), wptr, wrs,
-                       H.stream, correction ? G.zleaf->as<float>() : nullptr);
-    else
+                       H.stream, correction ? G.zleaf->as<float>() : nullptr, 0, bv);
+    } else
       leaf_post<double>(G.Y->as<double>(), G.ys, G.l0, H.uext.as<double>(),
                         H.leaf_off.as<int64_t>(), H.plan.ext_total, G.nl, G.p, G.q, nrhs,
                         G.dPg2c->as<double>(), wptr, wrs, H.stream);

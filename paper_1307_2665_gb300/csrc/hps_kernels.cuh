@@ -151,7 +151,7 @@ template <typename R>
 void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
                double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z = nullptr,
-               int accumulate = 0);
+               int accumulate = 0, const double* bndv = nullptr);
 template <typename R>
 void leaf_residual(const double* const* coef, int l0, int nl, int p, const double2* hsc,
                    const double* d_D, double* const* wptr, const int64_t* wrs, int nrhs, R* rbuf,
@@ -179,6 +179,12 @@ bool leaf_resflux_tc(const double* const* coef, int l0, int nl, int p, int q, co
                      const double* d_D, const double* d_Pc2g, double* const* wptr,
                      const int64_t* wrs, int nrhs, R* rbuf, const int64_t* leaf_off,
                      int64_t ext_total, double* hp, int* status, cudaStream_t st);
+// The FP64 boundary rows L1 u_e of every leaf and right-hand side on the tensor
+// cores: out[((r*nleaves + l)*4 + side)*p + j] = sum_k Pg2c[j][k] u_e[side*q + k]
+// (p = 16 and q <= 16 only; false otherwise).
+bool leaf_bnd_interp_tc(const double* uext, const int64_t* leaf_ext_off, int l0, int nleaves,
+                        int64_t ext_total, int p, int q, int nrhs, const double* d_Pg2c,
+                        double* out, int* status, cudaStream_t st);
 template <typename R>
 bool leaf_y_residual_tc(const double* const* coef, int l0, int nl, int p, int q,
                         const double2* hsc, const double* d_D, const double* d_Pg2c, const R* Y,

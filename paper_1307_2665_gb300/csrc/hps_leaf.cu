@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "hps_kernels.cuh"
 #include "hps_prof.hpp"
@@ -309,7 +310,9 @@ void leaf_dtn(R* Y, int64_t ys, int l0, int nleaves, int p, int q, const double2
 // sides' values (Section 3.2, Step 1).
 // u[(r*nl + l)*pp + node] receives w_full (accumulate = 0) or has it added in
 // FP64 (accumulate = 1).  z (optional) holds per leaf ni x nrhs interior values
-// (ld ni).
+// (ld ni).  bndv (optional) holds the side values already formed, per
+// right-hand side, leaf and side the p values L1 u_e ((r*nl + l)*4 + side)*p;
+// the kernel then reads them instead of forming them.
 template <typename R, int RC>
 __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int64_t ys, int l0,
                                                    const double* __restrict__ uext,
@@ -318,7 +321,8 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
                                                    const double* __restrict__ gPg2c,
                                                    const R* __restrict__ z, int accumulate,
                                                    double* const* __restrict__ wptr,
-                                                   const int64_t* __restrict__ wrs) {
+                                                   const int64_t* __restrict__ wrs,
+                                                   const double* __restrict__ bndv) {
   extern __shared__ __align__(16) double smd[];
   const int pp = p * p, pi = p - 2, ni = pi * pi, nq = 4 * q;
   double* Pg = smd;                               // p x q
@@ -343,11 +347,18 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
     }
     __syncthreads();
     // side values: bnd[(sd*p + j)*RC + rr] = sum_k Pg[j][k] u_e[sd*q + k]
-    for (int e = threadIdx.x; e < 4 * p * RC; e += blockDim.x) {
-      const int rr = e % RC, j = (e / RC) % p, sd = e / (RC * p);
-      double v = 0.0;
-      for (int k = 0; k < q; ++k) v = fma(Pg[j * q + k], ued[(sd * q + k) * RC + rr], v);
-      bnd[e] = v;
+    if (bndv) {
+      for (int e = threadIdx.x; e < 4 * p * RC; e += blockDim.x) {
+        const int rr = e / (4 * p), s = e % (4 * p);
+        if (rr < nr) bnd[s * RC + rr] = bndv[((size_t)(r0 + rr) * gridDim.x + l) * 4 * p + s];
+      }
+    } else {
+      for (int e = threadIdx.x; e < 4 * p * RC; e += blockDim.x) {
+        const int rr = e % RC, j = (e / RC) % p, sd = e / (RC * p);
+        double v = 0.0;
+        for (int k = 0; k < q; ++k) v = fma(Pg[j * q + k], ued[(sd * q + k) * RC + rr], v);
+        bnd[e] = v;
+      }
     }
     __syncthreads();
     // interior nodes: Y u_e (+ z) in the precision of Y.  Interior and
@@ -415,12 +426,189 @@ __global__ void __launch_bounds__(256) k_leaf_post(const R* __restrict__ Y, int6
   }
 }
 
+// Exact FP32 -> FP64 by integer instructions (the FP64 pipe, which also
+// converts, is the GPU's slowest); zeros, subnormals, infinities and NaNs
+// take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f), e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) {
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)f;
+  }
+  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)),
+                          (int)(b << 29));
+}
+
+// The post-process of a mixed solve at p = 16 (196 interior nodes = 28 x 7)
+// with the boundary rows already formed (bndv, layout as for k_leaf_post):
+// one leaf per block of 256 threads, its right-hand sides in chunks of 64.
+// Y and the chunk's z (FP32) come into shared memory by asynchronous copies
+// while the block stages u_e and writes the boundary nodes; then warp w forms
+// the right-hand sides 8w .. 8w + 7 of the chunk, lane i < 28 the interior rows
+// i, i + 28, ..., i + 168, each the same sequential FP32 FMA chain over the 4q
+// exterior values as k_leaf_post (so the same bits), plus z.
+constexpr int kPostP = 16, kPostNi = 196, kPostRows = 7, kPostLanes = 28;
+constexpr int kPostRc = 64, kPostUs = kPostRc + 4;  // chunk width, row stride of Us
+constexpr int kPostThreads = 256;
+constexpr int kPostUe = kPostRc * 64 / kPostThreads;                      // u_e per thread
+constexpr int kPostBn = (kPostRc * 4 * (kPostP - 1) + kPostThreads - 1) / kPostThreads;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// Boundary node t (0 .. 4(p-1)-1) of a leaf: its node index and the side
+// values (side * p + point) it takes, s2 >= 0 at a corner (the mean).
+__device__ __forceinline__ void post_bnd_node(int t, int& node, int& s1, int& s2) {
+  constexpr int p = kPostP;
+  int a, b;
+  s2 = -1;
+  if (t < p) {
+    a = 0, b = t, s1 = b;                       // S
+  } else if (t < 2 * p) {
+    a = p - 1, b = t - p, s1 = 2 * p + b;       // N
+  } else if (t < 3 * p - 2) {
+    a = t - 2 * p + 1, b = 0, s1 = 3 * p + a;   // W
+  } else {
+    a = t - 3 * p + 3, b = p - 1, s1 = p + a;   // E
+  }
+  if (a == 0 && b == 0) s2 = 3 * p;              // S and W
+  if (a == 0 && b == p - 1) s2 = p;              // S and E
+  if (a == p - 1 && b == 0) s2 = 3 * p + p - 1;  // N and W
+  if (a == p - 1 && b == p - 1) s2 = p + p - 1;  // N and E
+  node = a * p + b;
+}
+
+__global__ void __launch_bounds__(kPostThreads, 2) k_leaf_post_tiled(
+    const float* __restrict__ Y, int64_t ys, int l0, const double* __restrict__ uext,
+    const int64_t* __restrict__ leaf_off, int64_t ext_total, int nq, int nrhs,
+    const float* __restrict__ z, double* const* __restrict__ wptr,
+    const int64_t* __restrict__ wrs, const double* __restrict__ bndv) {
+  extern __shared__ __align__(16) float smf[];
+  constexpr int p = kPostP, ni = kPostNi, nb = 4 * (p - 1);
+  float* Ys = smf;                 // ni x nq, column g at g*ni
+  float* Us = Ys + ni * nq;        // nq x kPostUs: the chunk's u_e in FP32
+  float* Zs = Us + nq * kPostUs;   // ni x kPostRc: the chunk's z
+  const int l = blockIdx.x, nl = gridDim.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t off = leaf_off[l0 + l];
+  double* const wl = wptr[l0 + l];
+  const int64_t wstride = wrs[l0 + l];
+  {
+    const float* src = Y + (size_t)l * ys;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Ys);
+    for (int e = tid; e < ni * nq / 4; e += kPostThreads) cp_async16(dst + 16u * e, src + 4 * e);
+  }
+  const float* zl = z ? z + (size_t)l * ni * nrhs : nullptr;
+  for (int r0 = 0; r0 < nrhs; r0 += kPostRc) {
+    const int nr = min(kPostRc, nrhs - r0);
+    if (r0) __syncthreads();  // the previous chunk's reads of Us and Zs are done
+    if (zl) {
+      const float* src = zl + (size_t)r0 * ni;
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(Zs);
+      for (int e = tid; e < nr * ni / 4; e += kPostThreads) cp_async16(dst + 16u * e, src + 4 * e);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    {  // u_e of the chunk: every load in flight before the first store
+      double v[kPostUe];
+#pragma unroll
+      for (int i = 0; i < kPostUe; ++i) {
+        const int e = tid + kPostThreads * i, g = e % nq, rr = e / nq;
+        v[i] = (rr < nr) ? uext[(size_t)(r0 + rr) * ext_total + off + g] : 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < kPostUe; ++i) {
+        const int e = tid + kPostThreads * i, g = e % nq, rr = e / nq;
+        if (rr < kPostRc) Us[g * kPostUs + rr] = (float)v[i];
+      }
+    }
+    // boundary nodes, in batches of 8: loads first, then the means and stores
+#pragma unroll
+    for (int i0 = 0; i0 < kPostBn; i0 += 8) {
+      double v1[8], v2[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = tid + kPostThreads * (i0 + i), rr = e / nb;
+        int node, s1, s2;
+        post_bnd_node(e % nb, node, s1, s2);
+        v1[i] = v2[i] = 0.0;
+        if (i0 + i < kPostBn && rr < nr) {
+          const double* bv = bndv + ((size_t)(r0 + rr) * nl + l) * 4 * p;
+          v1[i] = bv[s1];
+          if (s2 >= 0) v2[i] = bv[s2];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = tid + kPostThreads * (i0 + i), rr = e / nb;
+        int node, s1, s2;
+        post_bnd_node(e % nb, node, s1, s2);
+        if (i0 + i < kPostBn && rr < nr)
+          wl[(size_t)(r0 + rr) * wstride + node] = s2 < 0 ? v1[i] : 0.5 * (v1[i] + v2[i]);
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    if (lane < kPostLanes && 8 * warp < nr) {
+      float acc[kPostRows][8];
+#pragma unroll
+      for (int j = 0; j < kPostRows; ++j)
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) acc[j][rr] = 0.0f;
+#pragma unroll 2
+      for (int g = 0; g < nq; ++g) {
+        const float4 ua = *reinterpret_cast<const float4*>(Us + g * kPostUs + 8 * warp);
+        const float4 ub = *reinterpret_cast<const float4*>(Us + g * kPostUs + 8 * warp + 4);
+        const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+        for (int j = 0; j < kPostRows; ++j) {
+          const float y = Ys[g * ni + lane + kPostLanes * j];
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) acc[j][rr] = fmaf(y, u[rr], acc[j][rr]);
+        }
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const int rc = 8 * warp + rr;
+        if (rc < nr) {
+          double* up = wl + (size_t)(r0 + rc) * wstride;
+#pragma unroll
+          for (int j = 0; j < kPostRows; ++j) {
+            const int ri = lane + kPostLanes * j;
+            float v = acc[j][rr];
+            if (zl) v += Zs[ri + rc * ni];
+            up[(ri / (p - 2) + 1) * p + ri % (p - 2) + 1] = f2d_exact(v);
+          }
+        }
+      }
+    }
+  }
+}
+
 template <typename R>
 void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t* leaf_ext_off,
                int64_t ext_total, int nleaves, int p, int q, int nrhs, const double* d_Pg2c,
                double* const* wptr, const int64_t* wrs, cudaStream_t st, const R* z,
-               int accumulate) {
+               int accumulate, const double* bndv) {
   if (nleaves <= 0 || nrhs <= 0) return;
+  if constexpr (std::is_same<R, float>::value) {
+    if (bndv && !accumulate && p == kPostP && 4 * q <= 64 && ys % 4 == 0 &&
+        reinterpret_cast<uintptr_t>(Y) % 16 == 0 && reinterpret_cast<uintptr_t>(z) % 16 == 0) {
+      const int nq = 4 * q;
+      const size_t smem = ((size_t)nq * (kPostNi + kPostUs) + (size_t)kPostNi * kPostRc) *
+                          sizeof(float);
+      if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_post_tiled), 200 * 1024))
+        return;  // reported by the caller's launch check
+      const double ni = kPostNi;
+      prof::Scope sc("leaf_post<f32>", st, (double)nleaves * nrhs * 2.0 * ni * nq,
+                     (double)nleaves * (ni * nq * sizeof(R) +
+                                        nrhs * (nq + 4.0 * p + (double)p * p) * 8.0 +
+                                        (z ? nrhs * ni * sizeof(R) : 0.0)));
+      k_leaf_post_tiled<<<nleaves, kPostThreads, smem, st>>>(Y, ys, l0, uext, leaf_ext_off, ext_total, nq,
+                                                     nrhs, z, wptr, wrs, bndv);
+      return;
+    }
+  }
   // right-hand sides per block: the smallest power of two covering nrhs, at most
   // 16 (padded columns would still run their FMAs; per column the arithmetic
   // does not depend on the block width)
@@ -436,12 +624,13 @@ void leaf_post(const R* Y, int64_t ys, int l0, const double* uext, const int64_t
     return;  // reported by the caller's launch check
   const double ni = (double)(p - 2) * (p - 2), nq = 4.0 * q;
   prof::Scope sc(tname<R>("leaf_post<f64>", "leaf_post<f32>"), st,
-                 (double)nleaves * nrhs * (2.0 * ni * nq + 2.0 * (4.0 * p) * q),
+                 (double)nleaves * nrhs * (2.0 * ni * nq + (bndv ? 0.0 : 2.0 * (4.0 * p) * q)),
                  (double)nleaves * (ni * nq * sizeof(R) +
-                                    nrhs * (nq + (double)p * p * (accumulate ? 2 : 1)) * 8.0));
+                                    nrhs * (nq + (bndv ? 4.0 * p : 0.0) +
+                                            (double)p * p * (accumulate ? 2 : 1)) * 8.0));
 #define HPS_LEAF_POST(RC)                                                                     \
   k_leaf_post<R, RC><<<nleaves, 256, smem, st>>>(Y, ys, l0, uext, leaf_ext_off, ext_total, p, q, \
-                                                 nrhs, d_Pg2c, z, accumulate, wptr, wrs)
+                                                 nrhs, d_Pg2c, z, accumulate, wptr, wrs, bndv)
   switch (rc) {
     case 1: HPS_LEAF_POST(1); break;
     case 2: HPS_LEAF_POST(2); break;
@@ -1169,7 +1358,7 @@ void leaf_flux(double* const* wptr, const int64_t* wrs, const R* z, int l0, int 
                             const double*, const double*, R*, cudaStream_t, const R*, int64_t); \
   template void leaf_post<R>(const R*, int64_t, int, const double*, const int64_t*, int64_t, int, \
                              int, int, int, const double*, double* const*, const int64_t*,      \
-                             cudaStream_t, const R*, int);                                      \
+                             cudaStream_t, const R*, int, const double*);                       \
   template void leaf_residual<R>(const double* const*, int, int, int, const double2*,           \
                                  const double*, double* const*, const int64_t*, int, R*,        \
                                  cudaStream_t);                                                 \

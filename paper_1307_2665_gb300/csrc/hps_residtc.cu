@@ -615,6 +615,159 @@ __global__ void __launch_bounds__(kRThreads, 2) k_leaf_resid_tc(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRCols));
 }
 
+// ---------------------------------------------- leaf boundary rows, L1 u_e
+// The boundary rows of a mixed solve's leaf values (Section 3.2, Step 1: each
+// side's q Gauss values interpolated to its p Chebyshev points), which must
+// be FP64 values in the range of L1 and identical in both leaves of a side:
+// each (right-hand side, leaf, side) line is rounded to a 56-bit fixed point
+// relative to its own largest exponent (so its result depends on the line
+// alone) and interpolated as one exact digit product, 128 lines per tcgen05
+// product against the digits of Pg2c (p x q, zero past q), drained by every
+// warp into correctly rounded doubles.  Line id = (r nl + l) 4 + side;
+// out[id p + j] = (Pg2c u_e(line))_j.  A persistent grid: CTA c takes rounds
+// c, c + gridDim.x, ...
+constexpr int kICols = kRDiag * kRP;  // TMEM columns: 8 diagonals x 16 points
+
+__global__ void __launch_bounds__(kRThreads, 3) k_bnd_interp_tc(
+    const double* __restrict__ uext, const int64_t* __restrict__ leaf_off, int l0, int nl,
+    int64_t ext_total, int q, int nrhs, const double* __restrict__ gPg2c,
+    double* __restrict__ out, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  unsigned char* As = smraw;                 // 7 digit slices: 128 lines
+  unsigned char* Bp = As + kRSA * kASliceB;  // 8 digit slices of Pg2c
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int fq[kRP];  // exponents of the rows of Pg2c
+  __shared__ int el[128];  // exponents of the lines
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t nlines = (int64_t)nrhs * nl * 4;
+  const int64_t rounds = (nlines + 127) / 128;
+  if ((int64_t)blockIdx.x >= rounds) return;  // uniform: before any allocation
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc::smem_u32(&tmem_base)),
+                 "r"(kICols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // row j of Pg2c (p x q), zero past q
+  auto prow = [&](int j, int k) -> double { return k < q ? gPg2c[j * q + k] : 0.0; };
+  if (tid < kRP) {
+    uint32_t hm = 0;
+    for (int k = 0; k < kRP; ++k)
+      hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(prow(tid, k)) >> 32) &
+                       0x7fffffffu);
+    fq[tid] = exp_bound(hm);
+  }
+  __syncthreads();
+  if (tid < 2 * kRP) {  // digits of Pg2c: thread (j, half), 8 entries of row j per slice
+    const int j = tid >> 1, half = tid & 1;
+    unsigned long long G[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) G[i] = fixed_point<62, kRSB>(prow(j, half * 8 + i), fq[j]);
+    const uint32_t base = tc::smem_u32(Bp + op_off(j, half * 8) * 2);
+#pragma unroll
+    for (int t = 1; t <= kRSB; ++t) store_slice<kRSB>(base + (t - 1) * kBSliceB, G, t);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int row = 32 * (warp & 3) + lane;  // TMEM lane = line of the round
+  const int c0 = 8 * (warp >> 2);          // the Chebyshev points this warp drains
+  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  bool fail = false;
+  uint32_t phase = 0;
+  // Gauss values half*8 .. +7 of line tid/2 of round rd (zero past q and
+  // past the last line), loaded one round ahead
+  double v[8];
+  auto fetch = [&](int64_t rd) {
+    const int half = tid & 1;
+    const int64_t id = rd * 128 + (tid >> 1);
+    const double* src = nullptr;
+    if (rd < rounds && id < nlines) {
+      const int side = (int)(id & 3);
+      const int64_t rl = id >> 2;
+      const int l = (int)(rl % nl), r = (int)(rl / nl);
+      src = uext + (size_t)r * ext_total + leaf_off[l0 + l] + side * q;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = half * 8 + i;
+      v[i] = (src && k < q) ? src[k] : 0.0;
+    }
+  };
+  fetch(blockIdx.x);
+  for (int64_t rd = blockIdx.x; rd < rounds; rd += gridDim.x) {
+    __syncthreads();  // the previous round's products read As: complete (waited)
+    // ---- thread (line, half) holds Gauss values half*8 .. +7 of its line
+    {
+      const int line = tid >> 1, half = tid & 1;
+      uint32_t hm = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        hm = max(hm, (uint32_t)((unsigned long long)__double_as_longlong(v[i]) >> 32) &
+                         0x7fffffffu);
+      hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, 1));
+      const int e = exp_bound(hm);
+      if (half == 0) el[line] = e;
+      unsigned long long G[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) G[i] = fixed_point<56, kRSA>(v[i], e);
+      const uint32_t base = tc::smem_u32(As + op_off(line, half * 8) * 2);
+#pragma unroll
+      for (int s = 1; s <= kRSA; ++s) store_slice<kRSA>(base + (s - 1) * kASliceB, G, s);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bp);
+      constexpr uint32_t idesc = tc::idesc_bf16(128, kRP);
+      for (int d = 2; d <= kRDiag + 1; ++d) {
+        uint32_t acc = 0;
+        for (int s = max(1, d - kRSB); s <= min(kRSA, d - 1); ++s) {
+          const uint64_t da = tc::desc_kmajor(a0 + (uint32_t)((s - 1) * kASliceB), 128, 256);
+          const uint64_t db = tc::desc_kmajor(b0 + (uint32_t)((d - s - 1) * kBSliceB), 128, 256);
+          tc::mma_bf16(tmem + (uint32_t)((d - 2) * kRP), da, db, idesc, acc);
+          acc = 1;
+        }
+      }
+      tc::commit(&bar);
+    }
+    fetch(rd + gridDim.x);  // in flight while the products run and drain
+    {
+      const bool ok = tc::mbar_wait(&bar, phase, kRSpin);
+      if (__syncthreads_or(!ok)) {
+        fail = true;
+        break;
+      }
+      phase ^= 1u;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {
+      double o[8];
+      drain8(tmem + tlane, c0, el[row], fq, o);
+      const int64_t id = rd * 128 + row;
+      if (id < nlines) {
+        double2* dst = reinterpret_cast<double2*>(out + id * kRP + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_double2(o[2 * i], o[2 * i + 1]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  if (fail && tid == 0) {
+    tc::mbar_wait(&bar, phase, kRSpin);  // the products that gave up finish first
+    if (status) atomicCAS(status, 0, -1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kICols));
+}
+
 // ------------------------------------------------------------------ host
 template <typename R, bool kFlux>
 size_t resid_tc_smem(int q) {
@@ -660,6 +813,24 @@ void launch_resid_tc(const double* const* coef, int l0, int nl, int q, const dou
 }
 
 }  // namespace
+
+bool leaf_bnd_interp_tc(const double* uext, const int64_t* leaf_ext_off, int l0, int nleaves,
+                        int64_t ext_total, int p, int q, int nrhs, const double* d_Pg2c,
+                        double* out, int* status, cudaStream_t st) {
+  if (p != kRP || q < 1 || q > kRP || !status) return false;
+  if (nleaves <= 0 || nrhs <= 0) return true;
+  const int64_t lines = (int64_t)nrhs * nleaves * 4, rounds = (lines + 127) / 128;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(rounds, (int64_t)std::max(nsm, 1) * 3);
+  const size_t smem = (size_t)kRSA * kASliceB + (size_t)kRSB * kBSliceB;
+  prof::Scope sc("leaf_bnd_tc<f64>", st, (double)lines * kRP * q * 2.0,
+                 (double)lines * (q + kRP) * 8.0);
+  k_bnd_interp_tc<<<grid, kRThreads, smem, st>>>(uext, leaf_ext_off, l0, nleaves, ext_total, q,
+                                                  nrhs, d_Pg2c, out, status);
+  return true;
+}
 
 template <typename R>
 bool leaf_resflux_tc(const double* const* coef, int l0, int nl, int p, int q, const double2* hsc,
