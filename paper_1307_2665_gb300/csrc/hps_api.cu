@@ -39,6 +39,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hps.h"
@@ -271,8 +272,11 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
   const Plan& pl = H.plan;
   cudaStream_t st = H.stream;
   const int ni = G.ni, nq = G.nq, nl = G.nl;
-  // mixed mode also solves for A_ii^{-1} (identity columns after -A_ie L1)
+  // mixed mode also forms A_ii^{-1} (columns nq .. nq+ni-1 of Y): at p = 16 by
+  // Gauss-Jordan in registers, Y's first nq columns then by one product;
+  // otherwise by the LU with identity right-hand sides after -A_ie L1
   const int nrhs_leaf = nq + (H.mixed ? ni : 0);
+  const bool gj = std::is_same<R, float>::value && H.mixed && ni == kLeafGjN;
   // mixed mode: one correction of Y against its FP64 residual before T is
   // formed; the residual and the correction reuse the factors' memory
   const bool yref = H.mixed && H.opt.leaf_refine > 0;
@@ -285,7 +289,7 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
   piv.alloc((size_t)nl * ni * sizeof(int), st);
   const double2* hsc = H.hsc.as<double2>();
   leaf_assemble<R>(G.coefp, G.l0, nl, G.p, G.q, hsc, G.dD->as<double>(), G.dPg2c->as<double>(),
-                   Aii.as<R>(), G.Y->as<R>(), G.ys, H.mixed ? 1 : 0, st);
+                   Aii.as<R>(), G.Y->as<R>(), G.ys, (H.mixed && !gj) ? 1 : 0, st);
   ck(cudaGetLastError());
   std::vector<LuDesc<R>> ld(nl);
   for (int j = 0; j < nl; ++j) {
@@ -299,7 +303,34 @@ void build_leaves(hps_handle_s& H, LeafGroup& G, Stager& stg, std::vector<TRef>&
     ld[j].box = pl.leaf_box[G.l0 + j];
   }
   LuDesc<R>* dl = stg.push(ld, st);
-  lu_solve_batched<R>(dl, nl, ni, nrhs_leaf, kLuFactor, H.status.as<int>(), st, nullptr, nullptr);
+  if constexpr (std::is_same<R, float>::value) {
+    if (gj) {
+      // A_ii^{-1} into Y's last ni columns (the right-hand sides -A_ie L1 moved
+      // into A_ii's memory), then Y = A_ii^{-1} (-A_ie L1)
+      if (!leaf_gj_inverse(dl, nl, ni, nq, H.status.as<int>(), st))
+        throw CudaError{cudaErrorInvalidValue};
+      std::vector<GemmDesc<float>> gy(nl);
+      for (int j = 0; j < nl; ++j) {
+        gy[j].A = G.Y->as<float>() + (size_t)j * G.ys + (size_t)ni * nq;
+        gy[j].B = Aii.as<float>() + (size_t)j * ni * ni;
+        gy[j].C = G.Y->as<float>() + (size_t)j * G.ys;
+        gy[j].M = ni;
+        gy[j].N = nq;
+        gy[j].K = ni;
+        gy[j].lda = ni;
+        gy[j].ldb = ni;
+        gy[j].ldc = ni;
+      }
+      GemmDesc<float>* dgy = stg.push(gy, st);
+      gemm_batched<float>(dgy, nl, ni, nq, 1.0f, 0.0f, st, "gemm_leafy<f32>",
+                          2.0 * nl * (double)ni * ni * nq,
+                          (double)nl * ni * (ni + 2.0 * nq) * sizeof(float), ni, nullptr, 0,
+                          H.status.as<int>());
+    }
+  }
+  if (!gj)
+    lu_solve_batched<R>(dl, nl, ni, nrhs_leaf, kLuFactor, H.status.as<int>(), st, nullptr,
+                        nullptr);
   ck(cudaGetLastError());
   R* dY = nullptr;
   if (yref) {

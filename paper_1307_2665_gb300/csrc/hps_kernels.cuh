@@ -77,6 +77,13 @@ struct BodyDesc {
 // h_m / h_nrhs: host copies of each descriptor's m and nrhs (launch accounting
 // only; null means every descriptor has the maximum sizes).
 constexpr int kLuFactor = 0, kLuFactorKeep = 1, kLuSolveOnly = 2;
+constexpr int kLeafGjN = 196;  // the order leaf_gj_inverse takes (p = 16)
+// A^{-1} of n x n FP32 leaf systems (n = kLeafGjN only; false otherwise) by
+// Gauss-Jordan elimination, one CTA per matrix: per descriptor A (ld n) is
+// read and then overwritten by B's first nq columns; B's columns nq .. nq+n-1
+// (ld n) receive A^{-1}.  Bad pivots as for the LU.
+bool leaf_gj_inverse(const LuDesc<float>* d_desc, int nd, int n, int nq, int* status,
+                     cudaStream_t st);
 template <typename R>
 void lu_solve_batched(const LuDesc<R>* d_desc, int ndesc, int max_m, int max_nrhs, int mode,
                       int* d_status, cudaStream_t st, const int* h_m, const int* h_nrhs);

@@ -987,6 +987,170 @@ __global__ void __launch_bounds__(TL::NT) k_backsub_update(const LuDesc<R>* __re
           D.B + rlo, D.ldb, m0, n0, reinterpret_cast<R*>(smraw));
 }
 
+// ------------------------------------------------ leaf inverse, Gauss-Jordan
+// The leaf systems of a mixed build at p = 16 (n = 196 interior nodes): A^{-1}
+// by Gauss-Jordan elimination with partial pivoting (the inverse of Section
+// 3.1's A_ii, from which the solution operator Y = A_ii^{-1} (-A_ie L1) and the
+// refinement's interior corrections follow by products), the whole matrix in
+// registers: one CTA per leaf, thread (tr, tc) of 28 x 28 holding rows
+// tr + 28a and columns tc + 28b (a, b < 7); 16 more threads make the last warp
+// whole and hold nothing.  Rows are never interchanged: step k takes as pivot
+// row p_k the largest |entry| of column k among the rows not yet used (ties:
+// the lower row), scales row p_k by 1/pivot (its column-k entry becoming
+// 1/pivot) and subtracts multiples of it from every other row (their column-k
+// entries becoming -entry/pivot), one FMA per entry.  After n steps entry
+// (i, k) of the array is A^{-1}(s(i), p_k), s(i) the step at which row i was
+// pivot; the inverse is written un-permuted through shared memory.
+// Per descriptor: A (n x n, ld n) is read and then receives a copy of B's
+// first nq columns (ld n); B's columns nq .. nq + n - 1 receive A^{-1}.  A zero
+// or non-finite pivot records box+1 in *status (first error wins) and the
+// elimination goes on with a zero reciprocal, as the LU's does.
+constexpr int kGjN = kLeafGjN, kGjT = 28, kGjR = 7, kGjOwners = kGjT * kGjT, kGjThreads = 800;
+
+// Pivot order: |v| (its bit pattern), then the sign, then the lower row; a
+// row not yet used always has a non-zero key.
+__device__ __forceinline__ unsigned long long gj_key(float v, int row) {
+  const uint32_t b = __float_as_uint(v);
+  return ((unsigned long long)(b & 0x7fffffffu) << 32) | (1u << 17) | ((b >> 31) << 16) |
+         (0xffffu - (uint32_t)row);
+}
+
+__global__ void __launch_bounds__(kGjThreads, 1)
+    k_leaf_gj_inverse(const LuDesc<float>* __restrict__ d, int nq, int* status) {
+  extern __shared__ __align__(16) float sinv[];  // n x n: the inverse, un-permuted
+  __shared__ float prow[kGjN], pcol[kGjN];
+  __shared__ unsigned long long cand[2];
+  __shared__ int rowstep[kGjN], steprow[kGjN];
+  constexpr int n = kGjN, T = kGjT, R = kGjR;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool owner = tid < kGjOwners;
+  const int tc = owner ? tid / T : -1, tr = owner ? tid - (tid / T) * T : -1;
+  for (int i = tid; i < n; i += kGjThreads) rowstep[i] = steprow[i] = 0;
+  float x[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) x[a][b] = 0.0f;
+  {
+    // the descriptor is read again where needed, not held through the steps
+    float* const A = d[blockIdx.x].A;
+    if (owner) {
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) x[a][b] = A[(tr + T * a) + (size_t)(tc + T * b) * n];
+    }
+    __syncthreads();  // every read of A precedes the copy into it
+    const float4* src = reinterpret_cast<const float4*>(d[blockIdx.x].B);
+    float4* dst = reinterpret_cast<float4*>(A);
+    for (int e = tid; e < n * nq / 4; e += kGjThreads) dst[e] = src[e];
+  }
+  uint32_t used = 0;  // bit a: row tr + 28a has been a pivot row
+#pragma unroll
+  for (int kb = 0; kb < R; ++kb) {
+#pragma unroll 1
+    for (int kc = 0; kc < T; ++kc) {
+      const int k = kb * T + kc;
+      // ---- candidates from the owners of column k (threads 28kc .. 28kc+27)
+      const int w0 = (kc * T) >> 5, w1 = (kc * T + T - 1) >> 5;
+      if (warp == w0 || warp == w1) {
+        unsigned long long key = 0;
+        if (tc == kc) {
+#pragma unroll
+          for (int a = 0; a < R; ++a)
+            if (!((used >> a) & 1u)) key = max(key, gj_key(x[a][kb], tr + T * a));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+        if (lane == 0) {
+          cand[warp - w0] = key;
+          if (w0 == w1) cand[1] = 0;
+        }
+      }
+      __syncthreads();
+      // ---- the pivot, decoded alike by every thread
+      const unsigned long long best = max(cand[0], cand[1]);
+      const int p = min(0xffff - (int)(best & 0xffffu), n - 1);  // a row not yet used
+      const float piv =
+          __uint_as_float((uint32_t)(best >> 32) | (((uint32_t)(best >> 16) & 1u) << 31));
+      const bool bad = !(piv != 0.0f) || !isfinite(piv);
+      const float rp = bad ? 0.0f : 1.0f / piv;
+      const int tp = p % T, ap = p / T;
+      if (tid == 0) {
+        steprow[k] = p;
+        rowstep[p] = k;
+        if (bad && status) atomicCAS(status, 0, d[blockIdx.x].box + 1);
+      }
+      if (tr == tp) {  // the pivot row, scaled (its column-k entry 1/pivot), then cleared
+        used |= 1u << ap;
+        switch (ap) {
+#define HPS_GJ_PROW(A)                                                      \
+  case A:                                                                   \
+    _Pragma("unroll") for (int b = 0; b < R; ++b) {                         \
+      prow[tc + T * b] = (b == kb && tc == kc) ? rp : x[A][b] * rp;         \
+      x[A][b] = 0.0f;                                                       \
+    }                                                                       \
+    break;
+          HPS_GJ_PROW(0) HPS_GJ_PROW(1) HPS_GJ_PROW(2) HPS_GJ_PROW(3) HPS_GJ_PROW(4)
+          HPS_GJ_PROW(5) HPS_GJ_PROW(6)
+#undef HPS_GJ_PROW
+        }
+      }
+      if (tc == kc) {  // the multipliers (-1 for the pivot row); column k cleared
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          pcol[tr + T * a] = (tr + T * a == p) ? -1.0f : x[a][kb];
+          x[a][kb] = 0.0f;
+        }
+      }
+      __syncthreads();
+      // ---- the update: entry -= multiplier x scaled pivot row (the pivot row,
+      // cleared, with multiplier -1 becomes the scaled row itself)
+      if (owner) {
+        float pr[R];
+#pragma unroll
+        for (int b = 0; b < R; ++b) pr[b] = prow[tc + T * b];
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          const float f = pcol[tr + T * a];
+#pragma unroll
+          for (int b = 0; b < R; ++b) x[a][b] = fmaf(-f, pr[b], x[a][b]);
+        }
+      }
+    }
+  }
+  // ---- A^{-1}(s(i), p_k) = entry (i, k), through shared memory
+  __syncthreads();
+  if (owner) {
+    int rs[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) rs[a] = rowstep[tr + T * a];
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      const int col = steprow[tc + T * b];
+#pragma unroll
+      for (int a = 0; a < R; ++a) sinv[rs[a] + col * n] = x[a][b];
+    }
+  }
+  __syncthreads();
+  {
+    const float4* src = reinterpret_cast<const float4*>(sinv);
+    float4* dst = reinterpret_cast<float4*>(d[blockIdx.x].B + (size_t)nq * n);
+    for (int e = tid; e < n * n / 4; e += kGjThreads) dst[e] = src[e];
+  }
+}
+
+bool leaf_gj_inverse(const LuDesc<float>* d_desc, int nd, int n, int nq, int* status,
+                     cudaStream_t st) {
+  if (n != kGjN || nq < 0 || nq > n) return false;
+  if (nd <= 0) return true;
+  if (!opt_in_smem(reinterpret_cast<const void*>(&k_leaf_gj_inverse), 200 * 1024)) return false;
+  prof::Scope sc("leaf_gj_inverse<f32>", st, 2.0 * nd * (double)n * n * n,
+                 (double)nd * (2.0 * n * n + 2.0 * n * nq) * sizeof(float));
+  k_leaf_gj_inverse<<<nd, kGjThreads, (size_t)n * n * sizeof(float), st>>>(d_desc, nq, status);
+  return true;
+}
+
 // ------------------------------------------------------------------ driver
 template <typename R>
 void lu_solve_batched(const LuDesc<R>* d_desc, int nd, int max_m, int max_nrhs, int mode,
