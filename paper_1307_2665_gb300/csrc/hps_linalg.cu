@@ -1001,17 +1001,18 @@ __global__ void __launch_bounds__(TL::NT) k_backsub_update(const LuDesc<R>* __re
 // entries becoming -entry/pivot), one FMA per entry.  After n steps entry
 // (i, k) of the array is A^{-1}(s(i), p_k), s(i) the step at which row i was
 // pivot; the inverse is written un-permuted through shared memory.
+// The pivot search of step k+1 runs in the warps that hold column k+1 while
+// the others still update for step k (they update that column first).
 // Per descriptor: A (n x n, ld n) is read and then receives a copy of B's
 // first nq columns (ld n); B's columns nq .. nq + n - 1 receive A^{-1}.  A zero
 // or non-finite pivot records box+1 in *status (first error wins) and the
 // elimination goes on with a zero reciprocal, as the LU's does.
 constexpr int kGjN = kLeafGjN, kGjT = 28, kGjR = 7, kGjOwners = kGjT * kGjT, kGjThreads = 800;
 
-// Pivot order: |v| (its bit pattern), then the sign, then the lower row; a
-// row not yet used always has a non-zero key.
+// Pivot order: |v| (its bit pattern), then the lower row; a row not yet used
+// always has a non-zero key.
 __device__ __forceinline__ unsigned long long gj_key(float v, int row) {
-  const uint32_t b = __float_as_uint(v);
-  return ((unsigned long long)(b & 0x7fffffffu) << 32) | (1u << 17) | ((b >> 31) << 16) |
+  return ((unsigned long long)(__float_as_uint(v) & 0x7fffffffu) << 32) | (1u << 17) |
          (0xffffu - (uint32_t)row);
 }
 
@@ -1020,6 +1021,7 @@ __global__ void __launch_bounds__(kGjThreads, 1)
   extern __shared__ __align__(16) float sinv[];  // n x n: the inverse, un-permuted
   __shared__ float prow[kGjN], pcol[kGjN];
   __shared__ unsigned long long cand[2];
+  __shared__ float crcp[2];
   __shared__ int rowstep[kGjN], steprow[kGjN];
   constexpr int n = kGjN, T = kGjT, R = kGjR;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1046,40 +1048,55 @@ __global__ void __launch_bounds__(kGjThreads, 1)
     for (int e = tid; e < n * nq / 4; e += kGjThreads) dst[e] = src[e];
   }
   uint32_t used = 0;  // bit a: row tr + 28a has been a pivot row
+  // Candidates for column (B, kcn) from its owners (threads 28kcn .. 28kcn+27,
+  // in warps w0n and w1n): per warp the largest |entry| among unused rows (as
+  // bit pattern + 1, so that an unused zero beats a used row), then the lowest
+  // row holding it; that lane publishes the 64-bit key and the reciprocal of
+  // its entry (zero for a bad pivot).
+  auto candidates = [&](auto Bc, int kcn) {
+    constexpr int B = decltype(Bc)::value;
+    const int w0n = (kcn * T) >> 5, w1n = (kcn * T + T - 1) >> 5;
+    uint32_t mk = 0;
+    int mrow = 0xffff;
+    float mv = 0.0f;
+    if (tc == kcn) {
 #pragma unroll
-  for (int kb = 0; kb < R; ++kb) {
+      for (int a = 0; a < R; ++a) {
+        const float v = x[a][B];
+        const uint32_t m = ((used >> a) & 1u) ? 0u : (__float_as_uint(v) & 0x7fffffffu) + 1u;
+        if (m > mk) mk = m, mrow = tr + T * a, mv = v;  // rows ascend with a
+      }
+    }
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, mk);
+    const uint32_t wrow = __reduce_min_sync(0xffffffffu, mk == wmax ? (uint32_t)mrow : 0xffffu);
+    if (lane == 0 && wmax == 0u) cand[warp - w0n] = 0;
+    if (wmax != 0u && mk == wmax && (uint32_t)mrow == wrow) {
+      const bool bad = !(mv != 0.0f) || !isfinite(mv);
+      cand[warp - w0n] = gj_key(mv, mrow);
+      crcp[warp - w0n] = bad ? 0.0f : 1.0f / mv;
+    }
+    if (lane == 0 && w0n == w1n) cand[1] = 0;
+  };
+  if (warp == 0) candidates(std::integral_constant<int, 0>{}, 0);  // column 0: threads 0 .. 27
+  // the steps of column block kb (columns 28kb .. 28kb+27), kb a constant
+  auto block = [&](auto KB) {
+    constexpr int kb = decltype(KB)::value;
 #pragma unroll 1
     for (int kc = 0; kc < T; ++kc) {
       const int k = kb * T + kc;
-      // ---- candidates from the owners of column k (threads 28kc .. 28kc+27)
-      const int w0 = (kc * T) >> 5, w1 = (kc * T + T - 1) >> 5;
-      if (warp == w0 || warp == w1) {
-        unsigned long long key = 0;
-        if (tc == kc) {
-#pragma unroll
-          for (int a = 0; a < R; ++a)
-            if (!((used >> a) & 1u)) key = max(key, gj_key(x[a][kb], tr + T * a));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-        if (lane == 0) {
-          cand[warp - w0] = key;
-          if (w0 == w1) cand[1] = 0;
-        }
-      }
-      __syncthreads();
+      __syncthreads();  // the candidates of column k are in
       // ---- the pivot, decoded alike by every thread
-      const unsigned long long best = max(cand[0], cand[1]);
+      const unsigned long long c0 = cand[0], c1 = cand[1];
+      const unsigned long long best = max(c0, c1);
+      const float rp = crcp[c1 > c0 ? 1 : 0];
       const int p = min(0xffff - (int)(best & 0xffffu), n - 1);  // a row not yet used
-      const float piv =
-          __uint_as_float((uint32_t)(best >> 32) | (((uint32_t)(best >> 16) & 1u) << 31));
-      const bool bad = !(piv != 0.0f) || !isfinite(piv);
-      const float rp = bad ? 0.0f : 1.0f / piv;
       const int tp = p % T, ap = p / T;
       if (tid == 0) {
         steprow[k] = p;
         rowstep[p] = k;
-        if (bad && status) atomicCAS(status, 0, d[blockIdx.x].box + 1);
+        const float piv = __uint_as_float((uint32_t)(best >> 32));  // |pivot|
+        if ((!(piv != 0.0f) || !isfinite(piv)) && status)
+          atomicCAS(status, 0, d[blockIdx.x].box + 1);
       }
       if (tr == tp) {  // the pivot row, scaled (its column-k entry 1/pivot), then cleared
         used |= 1u << ap;
@@ -1105,20 +1122,56 @@ __global__ void __launch_bounds__(kGjThreads, 1)
       }
       __syncthreads();
       // ---- the update: entry -= multiplier x scaled pivot row (the pivot row,
-      // cleared, with multiplier -1 becomes the scaled row itself)
-      if (owner) {
-        float pr[R];
+      // cleared, with multiplier -1 becomes the scaled row itself).  The warps
+      // holding column k+1 update it first and find its candidates while the
+      // other warps update.
+      auto update_col = [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        if (owner) {
+          const float pb = prow[tc + T * B];
 #pragma unroll
-        for (int b = 0; b < R; ++b) pr[b] = prow[tc + T * b];
-#pragma unroll
-        for (int a = 0; a < R; ++a) {
-          const float f = pcol[tr + T * a];
-#pragma unroll
-          for (int b = 0; b < R; ++b) x[a][b] = fmaf(-f, pr[b], x[a][b]);
+          for (int a = 0; a < R; ++a) x[a][B] = fmaf(-pcol[tr + T * a], pb, x[a][B]);
         }
+      };
+      auto update_rest = [&](auto Bc) {  // every column but B (B = R: all)
+        constexpr int B = decltype(Bc)::value;
+        if (owner) {
+          float pr[R];
+#pragma unroll
+          for (int b = 0; b < R; ++b) pr[b] = b != B ? prow[tc + T * b] : 0.0f;
+#pragma unroll
+          for (int a = 0; a < R; ++a) {
+            const float f = pcol[tr + T * a];
+#pragma unroll
+            for (int b = 0; b < R; ++b)
+              if (b != B) x[a][b] = fmaf(-f, pr[b], x[a][b]);
+          }
+        }
+      };
+      const int kcn = kc + 1 < T ? kc + 1 : 0;
+      const bool next = k + 1 < n;
+      const bool cw = next && (warp == (kcn * T) >> 5 || warp == (kcn * T + T - 1) >> 5);
+      if (!cw) {
+        update_rest(std::integral_constant<int, R>{});
+      } else if (kc + 1 < T) {
+        update_col(std::integral_constant<int, kb>{});
+        candidates(std::integral_constant<int, kb>{}, kcn);
+        update_rest(std::integral_constant<int, kb>{});
+      } else if constexpr (kb + 1 < R) {
+        update_col(std::integral_constant<int, kb + 1>{});
+        candidates(std::integral_constant<int, kb + 1>{}, kcn);
+        update_rest(std::integral_constant<int, kb + 1>{});
       }
     }
-  }
+  };
+  block(std::integral_constant<int, 0>{});
+  block(std::integral_constant<int, 1>{});
+  block(std::integral_constant<int, 2>{});
+  block(std::integral_constant<int, 3>{});
+  block(std::integral_constant<int, 4>{});
+  block(std::integral_constant<int, 5>{});
+  block(std::integral_constant<int, 6>{});
+  static_assert(kGjR == 7, "one call per column block");
   // ---- A^{-1}(s(i), p_k) = entry (i, k), through shared memory
   __syncthreads();
   if (owner) {
