@@ -992,22 +992,24 @@ __global__ void __launch_bounds__(TL::NT) k_backsub_update(const LuDesc<R>* __re
 // by Gauss-Jordan elimination with partial pivoting (the inverse of Section
 // 3.1's A_ii, from which the solution operator Y = A_ii^{-1} (-A_ie L1) and the
 // refinement's interior corrections follow by products), the whole matrix in
-// registers: one CTA per leaf, thread (tr, tc) of 28 x 28 holding rows
-// tr + 28a and columns tc + 28b (a, b < 7); 16 more threads make the last warp
-// whole and hold nothing.  Rows are never interchanged: step k takes as pivot
-// row p_k the largest |entry| of column k among the rows not yet used (ties:
-// the lower row), scales row p_k by 1/pivot (its column-k entry becoming
-// 1/pivot) and subtracts multiples of it from every other row (their column-k
-// entries becoming -entry/pivot), one FMA per entry.  After n steps entry
-// (i, k) of the array is A^{-1}(s(i), p_k), s(i) the step at which row i was
-// pivot; the inverse is written un-permuted through shared memory.
+// registers: one CTA per leaf, thread (tr, tc) of 28 x 14 holding rows
+// tr + 28a (a < 7) and columns tc + 14b (b < 14); 24 more threads make the
+// last warp whole and hold nothing.  Rows are never interchanged: step k
+// takes as pivot row p_k the largest |entry| of column k among the rows not
+// yet used (ties: the lower row), scales row p_k by 1/pivot (its column-k
+// entry becoming 1/pivot) and subtracts multiples of it from every other row
+// (their column-k entries becoming -entry/pivot), one FMA per entry.  After n
+// steps entry (i, k) of the array is A^{-1}(s(i), p_k), s(i) the step at which
+// row i was pivot; the inverse is written un-permuted through shared memory.
 // The pivot search of step k+1 runs in the warps that hold column k+1 while
 // the others still update for step k (they update that column first).
 // Per descriptor: A (n x n, ld n) is read and then receives a copy of B's
 // first nq columns (ld n); B's columns nq .. nq + n - 1 receive A^{-1}.  A zero
 // or non-finite pivot records box+1 in *status (first error wins) and the
 // elimination goes on with a zero reciprocal, as the LU's does.
-constexpr int kGjN = kLeafGjN, kGjT = 28, kGjR = 7, kGjOwners = kGjT * kGjT, kGjThreads = 800;
+constexpr int kGjN = kLeafGjN, kGjTr = 28, kGjTc = 14, kGjR = 7, kGjC = 14;
+constexpr int kGjOwners = kGjTr * kGjTc, kGjThreads = (kGjOwners + 31) / 32 * 32;
+static_assert(kGjTr * kGjR == kGjN && kGjTc * kGjC == kGjN, "the tiles cover the matrix");
 
 // Pivot order: |v| (its bit pattern), then the lower row; a row not yet used
 // always has a non-zero key.
@@ -1023,16 +1025,16 @@ __global__ void __launch_bounds__(kGjThreads, 1)
   __shared__ unsigned long long cand[2];
   __shared__ float crcp[2];
   __shared__ int rowstep[kGjN], steprow[kGjN];
-  constexpr int n = kGjN, T = kGjT, R = kGjR;
+  constexpr int n = kGjN, Tr = kGjTr, Tc = kGjTc, R = kGjR, C = kGjC;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool owner = tid < kGjOwners;
-  const int tc = owner ? tid / T : -1, tr = owner ? tid - (tid / T) * T : -1;
+  const int tc = owner ? tid / Tr : -1, tr = owner ? tid - (tid / Tr) * Tr : -1;
   for (int i = tid; i < n; i += kGjThreads) rowstep[i] = steprow[i] = 0;
-  float x[R][R];
+  float x[R][C];
 #pragma unroll
   for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < R; ++b) x[a][b] = 0.0f;
+    for (int b = 0; b < C; ++b) x[a][b] = 0.0f;
   {
     // the descriptor is read again where needed, not held through the steps
     float* const A = d[blockIdx.x].A;
@@ -1040,7 +1042,7 @@ __global__ void __launch_bounds__(kGjThreads, 1)
 #pragma unroll
       for (int a = 0; a < R; ++a)
 #pragma unroll
-        for (int b = 0; b < R; ++b) x[a][b] = A[(tr + T * a) + (size_t)(tc + T * b) * n];
+        for (int b = 0; b < C; ++b) x[a][b] = A[(tr + Tr * a) + (size_t)(tc + Tc * b) * n];
     }
     __syncthreads();  // every read of A precedes the copy into it
     const float4* src = reinterpret_cast<const float4*>(d[blockIdx.x].B);
@@ -1048,14 +1050,14 @@ __global__ void __launch_bounds__(kGjThreads, 1)
     for (int e = tid; e < n * nq / 4; e += kGjThreads) dst[e] = src[e];
   }
   uint32_t used = 0;  // bit a: row tr + 28a has been a pivot row
-  // Candidates for column (B, kcn) from its owners (threads 28kcn .. 28kcn+27,
-  // in warps w0n and w1n): per warp the largest |entry| among unused rows (as
-  // bit pattern + 1, so that an unused zero beats a used row), then the lowest
-  // row holding it; that lane publishes the 64-bit key and the reciprocal of
-  // its entry (zero for a bad pivot).
+  // Candidates for column (slot B, group kcn) from its owners (threads
+  // 28kcn .. 28kcn+27, in warps w0n and w1n): per warp the largest |entry|
+  // among unused rows (as bit pattern + 1, so that an unused zero beats a used
+  // row), then the lowest row holding it; that lane publishes the 64-bit key
+  // and the reciprocal of its entry (zero for a bad pivot).
   auto candidates = [&](auto Bc, int kcn) {
     constexpr int B = decltype(Bc)::value;
-    const int w0n = (kcn * T) >> 5, w1n = (kcn * T + T - 1) >> 5;
+    const int w0n = (kcn * Tr) >> 5, w1n = (kcn * Tr + Tr - 1) >> 5;
     uint32_t mk = 0;
     int mrow = 0xffff;
     float mv = 0.0f;
@@ -1064,7 +1066,7 @@ __global__ void __launch_bounds__(kGjThreads, 1)
       for (int a = 0; a < R; ++a) {
         const float v = x[a][B];
         const uint32_t m = ((used >> a) & 1u) ? 0u : (__float_as_uint(v) & 0x7fffffffu) + 1u;
-        if (m > mk) mk = m, mrow = tr + T * a, mv = v;  // rows ascend with a
+        if (m > mk) mk = m, mrow = tr + Tr * a, mv = v;  // rows ascend with a
       }
     }
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, mk);
@@ -1078,19 +1080,20 @@ __global__ void __launch_bounds__(kGjThreads, 1)
     if (lane == 0 && w0n == w1n) cand[1] = 0;
   };
   if (warp == 0) candidates(std::integral_constant<int, 0>{}, 0);  // column 0: threads 0 .. 27
-  // the steps of column block kb (columns 28kb .. 28kb+27), kb a constant
+  // the steps of columns 14kb .. 14kb + 13 (slot kb of groups tc = 0 .. 13),
+  // kb a constant
   auto block = [&](auto KB) {
     constexpr int kb = decltype(KB)::value;
 #pragma unroll 1
-    for (int kc = 0; kc < T; ++kc) {
-      const int k = kb * T + kc;
+    for (int kc = 0; kc < Tc; ++kc) {
+      const int k = kc + Tc * kb;  // column k = group kc, slot kb
       __syncthreads();  // the candidates of column k are in
       // ---- the pivot, decoded alike by every thread
       const unsigned long long c0 = cand[0], c1 = cand[1];
       const unsigned long long best = max(c0, c1);
       const float rp = crcp[c1 > c0 ? 1 : 0];
       const int p = min(0xffff - (int)(best & 0xffffu), n - 1);  // a row not yet used
-      const int tp = p % T, ap = p / T;
+      const int tp = p % Tr, ap = p / Tr;
       if (tid == 0) {
         steprow[k] = p;
         rowstep[p] = k;
@@ -1103,8 +1106,8 @@ __global__ void __launch_bounds__(kGjThreads, 1)
         switch (ap) {
 #define HPS_GJ_PROW(A)                                                      \
   case A:                                                                   \
-    _Pragma("unroll") for (int b = 0; b < R; ++b) {                         \
-      prow[tc + T * b] = (b == kb && tc == kc) ? rp : x[A][b] * rp;         \
+    _Pragma("unroll") for (int b = 0; b < C; ++b) {                         \
+      prow[tc + Tc * b] = (b == kb && tc == kc) ? rp : x[A][b] * rp;        \
       x[A][b] = 0.0f;                                                       \
     }                                                                       \
     break;
@@ -1116,7 +1119,7 @@ __global__ void __launch_bounds__(kGjThreads, 1)
       if (tc == kc) {  // the multipliers (-1 for the pivot row); column k cleared
 #pragma unroll
         for (int a = 0; a < R; ++a) {
-          pcol[tr + T * a] = (tr + T * a == p) ? -1.0f : x[a][kb];
+          pcol[tr + Tr * a] = (tr + Tr * a == p) ? -1.0f : x[a][kb];
           x[a][kb] = 0.0f;
         }
       }
@@ -1128,36 +1131,36 @@ __global__ void __launch_bounds__(kGjThreads, 1)
       auto update_col = [&](auto Bc) {
         constexpr int B = decltype(Bc)::value;
         if (owner) {
-          const float pb = prow[tc + T * B];
+          const float pb = prow[tc + Tc * B];
 #pragma unroll
-          for (int a = 0; a < R; ++a) x[a][B] = fmaf(-pcol[tr + T * a], pb, x[a][B]);
+          for (int a = 0; a < R; ++a) x[a][B] = fmaf(-pcol[tr + Tr * a], pb, x[a][B]);
         }
       };
-      auto update_rest = [&](auto Bc) {  // every column but B (B = R: all)
+      auto update_rest = [&](auto Bc) {  // every column slot but B (B = C: all)
         constexpr int B = decltype(Bc)::value;
         if (owner) {
-          float pr[R];
+          float f[R];
 #pragma unroll
-          for (int b = 0; b < R; ++b) pr[b] = b != B ? prow[tc + T * b] : 0.0f;
+          for (int a = 0; a < R; ++a) f[a] = pcol[tr + Tr * a];
 #pragma unroll
-          for (int a = 0; a < R; ++a) {
-            const float f = pcol[tr + T * a];
+          for (int b = 0; b < C; ++b) {
+            if (b == B) continue;
+            const float pb = prow[tc + Tc * b];
 #pragma unroll
-            for (int b = 0; b < R; ++b)
-              if (b != B) x[a][b] = fmaf(-f, pr[b], x[a][b]);
+            for (int a = 0; a < R; ++a) x[a][b] = fmaf(-f[a], pb, x[a][b]);
           }
         }
       };
-      const int kcn = kc + 1 < T ? kc + 1 : 0;
+      const int kcn = kc + 1 < Tc ? kc + 1 : 0;
       const bool next = k + 1 < n;
-      const bool cw = next && (warp == (kcn * T) >> 5 || warp == (kcn * T + T - 1) >> 5);
+      const bool cw = next && (warp == (kcn * Tr) >> 5 || warp == (kcn * Tr + Tr - 1) >> 5);
       if (!cw) {
-        update_rest(std::integral_constant<int, R>{});
-      } else if (kc + 1 < T) {
+        update_rest(std::integral_constant<int, C>{});
+      } else if (kc + 1 < Tc) {
         update_col(std::integral_constant<int, kb>{});
         candidates(std::integral_constant<int, kb>{}, kcn);
         update_rest(std::integral_constant<int, kb>{});
-      } else if constexpr (kb + 1 < R) {
+      } else if constexpr (kb + 1 < C) {
         update_col(std::integral_constant<int, kb + 1>{});
         candidates(std::integral_constant<int, kb + 1>{}, kcn);
         update_rest(std::integral_constant<int, kb + 1>{});
@@ -1171,16 +1174,23 @@ __global__ void __launch_bounds__(kGjThreads, 1)
   block(std::integral_constant<int, 4>{});
   block(std::integral_constant<int, 5>{});
   block(std::integral_constant<int, 6>{});
-  static_assert(kGjR == 7, "one call per column block");
+  block(std::integral_constant<int, 7>{});
+  block(std::integral_constant<int, 8>{});
+  block(std::integral_constant<int, 9>{});
+  block(std::integral_constant<int, 10>{});
+  block(std::integral_constant<int, 11>{});
+  block(std::integral_constant<int, 12>{});
+  block(std::integral_constant<int, 13>{});
+  static_assert(kGjC == 14, "one call per column slot");
   // ---- A^{-1}(s(i), p_k) = entry (i, k), through shared memory
   __syncthreads();
   if (owner) {
     int rs[R];
 #pragma unroll
-    for (int a = 0; a < R; ++a) rs[a] = rowstep[tr + T * a];
+    for (int a = 0; a < R; ++a) rs[a] = rowstep[tr + Tr * a];
 #pragma unroll
-    for (int b = 0; b < R; ++b) {
-      const int col = steprow[tc + T * b];
+    for (int b = 0; b < C; ++b) {
+      const int col = steprow[tc + Tc * b];
 #pragma unroll
       for (int a = 0; a < R; ++a) sinv[rs[a] + col * n] = x[a][b];
     }
