@@ -1920,6 +1920,58 @@ int hps_sgemm_tc(int M, int N, int K, float alpha, const float* A, int lda, cons
   }
 }
 
+int hps_sinv_gj(int n, int count, const float* A, float* Ainv) {
+  if (n != kLeafGjN || count < 1 || !A || !Ainv) return HPS_EINVAL;
+  const size_t nn = (size_t)n * n;
+  const char *a0 = reinterpret_cast<const char*>(A), *b0 = reinterpret_cast<const char*>(Ainv);
+  if (a0 < b0 + nn * count * sizeof(float) && b0 < a0 + nn * count * sizeof(float))
+    return HPS_EINVAL;  // overlapping
+  if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Ainv) % 16)
+    return HPS_EINVAL;  // the kernel copies by 16-byte vectors
+  g_last_error.clear();
+  try {
+    cudaStream_t st = nullptr;
+    ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int rc = HPS_OK;
+    {
+      // nq = 0: nothing is copied into A, which is only read
+      std::vector<LuDesc<float>> h(count);
+      for (int m = 0; m < count; ++m) {
+        h[m].A = const_cast<float*>(A) + nn * m;
+        h[m].ipiv = nullptr;
+        h[m].B = Ainv + nn * m;
+        h[m].m = n;
+        h[m].lda = n;
+        h[m].nrhs = n;
+        h[m].ldb = n;
+        h[m].box = m;
+      }
+      PoolBuf dd, stt;
+      dd.alloc(h.size() * sizeof(LuDesc<float>), st);
+      stt.alloc(sizeof(int), st);
+      ck(cudaMemcpyAsync(dd.p, h.data(), h.size() * sizeof(LuDesc<float>), cudaMemcpyHostToDevice,
+                         st));
+      ck(cudaMemsetAsync(stt.p, 0, sizeof(int), st));
+      if (!leaf_gj_inverse(dd.as<LuDesc<float>>(), count, n, 0, stt.as<int>(), st))
+        throw CudaError{cudaErrorInvalidValue};
+      ck(cudaGetLastError());
+      int hst = 0;
+      ck(cudaMemcpyAsync(&hst, stt.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      ck(cudaStreamSynchronize(st));
+      if (hst > 0) {
+        g_last_error = "hps_sinv_gj: zero or non-finite pivot in matrix " + std::to_string(hst - 1);
+        rc = HPS_ESINGULAR;
+      }
+    }
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return rc;
+  } catch (CudaError& e) {
+    cudaGetLastError();
+    return e.err == cudaErrorMemoryAllocation ? HPS_ENOMEM : HPS_EDEVICE;
+  }
+}
+
 int hps_leaf_residual(int p, int q, int nleaves, double hx, double hy, const double* c11,
                       const double* c22, const double* c, const double* w, int nrhs, double* r,
                       double* flux, int tensor_cores) {

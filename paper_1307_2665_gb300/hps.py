@@ -33,7 +33,7 @@ EXPORTS = ("hps_default_options", "hps_boundary_count", "hps_cheb_nodes",
            "hps_profile_enable", "hps_profile_reset", "hps_profile_read", "hps_last_error",
            "hps_solve_static", "hps_build_batch", "hps_solve_batch", "hps_batch_size",
            "hps_estimate_bytes", "hps_release_workspace", "hps_dgemm_tc", "hps_apply_dtn",
-           "hps_interpolate", "hps_sgemm_tc", "hps_leaf_residual",
+           "hps_interpolate", "hps_sgemm_tc", "hps_leaf_residual", "hps_sinv_gj",
            # include/hps_serve.h
            "hps_server_default_options", "hps_server_create", "hps_server_destroy",
            "hps_server_submit_build", "hps_server_submit_solve", "hps_server_wait",
@@ -158,6 +158,8 @@ def lib():
                                     ctypes.c_double, vp, vp, vp, vp, ctypes.c_int, vp, vp,
                                     ctypes.c_int]
     L.hps_leaf_residual.restype = ctypes.c_int
+    L.hps_sinv_gj.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp]
+    L.hps_sinv_gj.restype = ctypes.c_int
     L.hps_apply_dtn.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int]
     L.hps_apply_dtn.restype = ctypes.c_int
     L.hps_interpolate.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int64, vp, ctypes.c_int]
