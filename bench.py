@@ -336,8 +336,10 @@ def alu_peak_tflops(name, sm_mhz):
 # changed since its capture has no entry.  leaf_resflux_tc<f64>: captured on
 # 64 x 64 leaves with 64 right-hand sides (850.7 MB per launch, 3245 bytes per
 # leaf and right-hand side) and scaled by the 16 times as many units of a
-# 256 x 256 launch.
-TRAFFIC_PER_LAUNCH = {("helmholtz256", "leaf_resflux_tc<f64>"): 850.7e6 * 16}
+# 256 x 256 launch.  leaf_gj_inverse<f32>: captured on 64 x 64 leaves (4096
+# matrices, 810.5 + 758.4 MB, 383 KB per leaf), scaled the same way.
+TRAFFIC_PER_LAUNCH = {("helmholtz256", "leaf_resflux_tc<f64>"): 850.7e6 * 16,
+                      ("helmholtz256", "leaf_gj_inverse<f32>"): (810.5e6 + 758.4e6) * 16}
 
 
 def roofline_of(stats, t_total_ms, sm_mhz, workload=None):
