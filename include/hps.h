@@ -266,9 +266,10 @@ int hps_leaf_residual(int p, int q, int nleaves, double hx, double hy, const dou
  * systems A_ii (Section 3.1; the paper solves them by a dense factorisation):
  * Gauss-Jordan elimination with partial pivoting, one thread block per matrix
  * with the whole matrix in registers.  Ainv[m n^2 ..] = A[m n^2 ..]^{-1} for
- * m < count, every matrix n x n column-major; A and Ainv are device memory and
- * must not overlap; A is not modified.  Only n = 196 (the interior of a p = 16
- * leaf), else HPS_EINVAL.  A zero or non-finite pivot gives HPS_ESINGULAR
+ * m < count, every matrix n x n column-major; A and Ainv are 16-byte aligned
+ * device memory and must not overlap; A is not modified.  Only n = 196 (the
+ * interior of a p = 16 leaf); otherwise, or for overlapping or unaligned
+ * arrays, HPS_EINVAL with the reason in hps_last_error().  A zero or non-finite pivot gives HPS_ESINGULAR
  * (hps_last_error() names the first such matrix); Ainv is then written but
  * meaningless for it.  Synchronous.  Exposed for testing and measurement. */
 int hps_sinv_gj(int n, int count, const float* A, float* Ainv);

@@ -1921,14 +1921,22 @@ int hps_sgemm_tc(int M, int N, int K, float alpha, const float* A, int lda, cons
 }
 
 int hps_sinv_gj(int n, int count, const float* A, float* Ainv) {
-  if (n != kLeafGjN || count < 1 || !A || !Ainv) return HPS_EINVAL;
+  g_last_error.clear();
+  if (n != kLeafGjN || count < 1 || !A || !Ainv) {
+    g_last_error = "hps_sinv_gj: takes n = " + std::to_string(kLeafGjN) +
+                   ", count >= 1 and non-null arrays";
+    return HPS_EINVAL;
+  }
   const size_t nn = (size_t)n * n;
   const char *a0 = reinterpret_cast<const char*>(A), *b0 = reinterpret_cast<const char*>(Ainv);
-  if (a0 < b0 + nn * count * sizeof(float) && b0 < a0 + nn * count * sizeof(float))
-    return HPS_EINVAL;  // overlapping
-  if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Ainv) % 16)
-    return HPS_EINVAL;  // the kernel copies by 16-byte vectors
-  g_last_error.clear();
+  if (a0 < b0 + nn * count * sizeof(float) && b0 < a0 + nn * count * sizeof(float)) {
+    g_last_error = "hps_sinv_gj: A and Ainv overlap";
+    return HPS_EINVAL;
+  }
+  if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Ainv) % 16) {
+    g_last_error = "hps_sinv_gj: A and Ainv must be 16-byte aligned";  // 16-byte vector copies
+    return HPS_EINVAL;
+  }
   try {
     cudaStream_t st = nullptr;
     ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));

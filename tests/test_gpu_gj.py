@@ -125,3 +125,10 @@ def test_shape_limit():
     a = torch.zeros(100 * 100, dtype=torch.float32, device="cuda")
     x = torch.zeros_like(a)
     assert hps.lib().hps_sinv_gj(100, 1, a.data_ptr(), x.data_ptr()) == hps.HPS_EINVAL
+    assert b"n = 196" in hps.lib().hps_last_error()
+    b = torch.zeros(2 * N * N + 4, dtype=torch.float32, device="cuda")
+    assert hps.lib().hps_sinv_gj(N, 2, b.data_ptr(), b.data_ptr() + 4 * N * N) == hps.HPS_EINVAL
+    assert b"overlap" in hps.lib().hps_last_error()
+    y = torch.zeros(N * N, dtype=torch.float32, device="cuda")  # sized for one inverse
+    assert hps.lib().hps_sinv_gj(N, 1, b.data_ptr() + 4, y.data_ptr()) == hps.HPS_EINVAL
+    assert b"aligned" in hps.lib().hps_last_error()
